@@ -1,0 +1,172 @@
+/*
+ * Oracle: plain, slow, FP64 CPU reference for the three structured solves.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or
+ * calls this file; only the tests, the package smoke check and the benchmark's
+ * CPU-baseline leg do.  It shares no code, header, table or helper with the
+ * CUDA path.
+ *
+ * The problems (the paper's case studies, Fig. 2 caption, and the annotated
+ * input "X^T X = A" of the "Generator structure" paragraph):
+ *   (a) X_u^T X_u = A,        A symmetric positive definite, X_u upper triangular;
+ *   (b) L X_s + X_s L^T = S,  L lower triangular, S and X_s symmetric;
+ *   (c) L X + X U = C,        L lower triangular, U upper triangular.
+ * All matrices are n x n, double precision (the paper's "Preliminary
+ * performance results" paragraph).
+ *
+ * Each routine is the textbook unblocked recurrence obtained by writing the
+ * defining equation out entry by entry and solving for one unknown at a time.
+ * No blocking, no reordering, no fusion.  Storage is column-major: element
+ * (i, j) of a matrix with leading dimension ld sits at p[i + j * ld].
+ *
+ * Readings taken where the paper is silent:
+ *   - the Cholesky factor has a positive diagonal (this makes it unique);
+ *   - the Cholesky routine reads only the upper triangle of A and writes only
+ *     the upper triangle of X;
+ *   - the Lyapunov routine reads only the lower triangle of S and writes only
+ *     the lower triangle of X (X is symmetric);
+ *   - sums run left to right in plain FP64 (built with -ffp-contract=off);
+ *   - the Sylvester and Lyapunov right-hand sides carry no minus sign: the
+ *     equations are taken literally as printed.
+ *
+ * Return codes (the same convention as the library's per-instance info):
+ *   0      success;
+ *   j + 1  (Cholesky) the pivot of column j (0-based) was not positive or was NaN;
+ *   1      (Sylvester / Lyapunov) some divisor l_ii + u_jj had magnitude at or below
+ *          delta = n * DBL_EPSILON * max_i,j(|l_ii|, |u_jj|), or was NaN.
+ */
+#include <math.h>
+#include <float.h>
+#include <stddef.h>
+
+#define AT(p, ld, i, j) ((p)[(size_t)(i) + (size_t)(j) * (size_t)(ld)])
+
+/*
+ * Upper Cholesky, problem (a).  Entry (i, j), i <= j, of X^T X is
+ *   sum_{k <= i} x_ki x_kj,
+ * so for i < j:  x_ij = (a_ij - sum_{k < i} x_ki x_kj) / x_ii
+ * and           x_jj = sqrt(a_jj - sum_{k < j} x_kj^2).
+ * Columns are produced left to right; inside a column, rows top to bottom.
+ */
+int oracle_potrf_upper(int n, const double *A, int lda, double *X, int ldx)
+{
+    for (int j = 0; j < n; ++j) {
+        for (int i = 0; i < j; ++i) {
+            double s = AT(A, lda, i, j);
+            for (int k = 0; k < i; ++k)
+                s = s - AT(X, ldx, k, i) * AT(X, ldx, k, j);
+            AT(X, ldx, i, j) = s / AT(X, ldx, i, i);
+        }
+        double d = AT(A, lda, j, j);
+        for (int k = 0; k < j; ++k)
+            d = d - AT(X, ldx, k, j) * AT(X, ldx, k, j);
+        if (!(d > 0.0))
+            return j + 1;
+        AT(X, ldx, j, j) = sqrt(d);
+    }
+    return 0;
+}
+
+static double divisor_threshold(int n, double maxdiag)
+{
+    return (double)n * DBL_EPSILON * maxdiag;
+}
+
+/*
+ * Triangular Sylvester, problem (c).  Entry (i, j) of L X + X U is
+ *   sum_{k <= i} l_ik x_kj + sum_{k <= j} x_ik u_kj,
+ * so  x_ij = (c_ij - sum_{k < i} l_ik x_kj - sum_{k < j} x_ik u_kj) / (l_ii + u_jj).
+ * Rows top to bottom, columns left to right: every x on the right is known.
+ */
+int oracle_trsyl_lu(int n, const double *L, int ldl, const double *U, int ldu,
+                    const double *C, int ldc, double *X, int ldx)
+{
+    double maxdiag = 0.0;
+    for (int i = 0; i < n; ++i) {
+        if (fabs(AT(L, ldl, i, i)) > maxdiag) maxdiag = fabs(AT(L, ldl, i, i));
+        if (fabs(AT(U, ldu, i, i)) > maxdiag) maxdiag = fabs(AT(U, ldu, i, i));
+    }
+    const double delta = divisor_threshold(n, maxdiag);
+    int info = 0;
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j < n; ++j) {
+            double s = AT(C, ldc, i, j);
+            for (int k = 0; k < i; ++k)
+                s = s - AT(L, ldl, i, k) * AT(X, ldx, k, j);
+            for (int k = 0; k < j; ++k)
+                s = s - AT(X, ldx, i, k) * AT(U, ldu, k, j);
+            double d = AT(L, ldl, i, i) + AT(U, ldu, j, j);
+            if (!(fabs(d) > delta))
+                info = 1;
+            AT(X, ldx, i, j) = s / d;
+        }
+    }
+    return info;
+}
+
+/* Read element (r, c) of the symmetric X from its stored lower triangle. */
+static double sym_lower(const double *X, int ldx, int r, int c)
+{
+    return r >= c ? AT(X, ldx, r, c) : AT(X, ldx, c, r);
+}
+
+/*
+ * Triangular Lyapunov, problem (b): the Sylvester equation with U = L^T, so
+ * u_kj = l_jk.  Only i >= j is computed; an unknown x_kj with k < j is the
+ * stored x_jk (symmetry of X):
+ *   x_ij = (s_ij - sum_{k < i} l_ik x_kj - sum_{k < j} x_ik l_jk) / (l_ii + l_jj).
+ */
+int oracle_trlyap_l(int n, const double *L, int ldl, const double *S, int lds,
+                    double *X, int ldx)
+{
+    double maxdiag = 0.0;
+    for (int i = 0; i < n; ++i)
+        if (fabs(AT(L, ldl, i, i)) > maxdiag) maxdiag = fabs(AT(L, ldl, i, i));
+    const double delta = divisor_threshold(n, maxdiag);
+    int info = 0;
+    for (int i = 0; i < n; ++i) {
+        for (int j = 0; j <= i; ++j) {
+            double s = AT(S, lds, i, j);
+            for (int k = 0; k < i; ++k)
+                s = s - AT(L, ldl, i, k) * sym_lower(X, ldx, k, j);
+            for (int k = 0; k < j; ++k)
+                s = s - sym_lower(X, ldx, i, k) * AT(L, ldl, j, k);
+            double d = AT(L, ldl, i, i) + AT(L, ldl, j, j);
+            if (!(fabs(d) > delta))
+                info = 1;
+            AT(X, ldx, i, j) = s / d;
+        }
+    }
+    return info;
+}
+
+/*
+ * Batched drivers over a packed buffer: instance b has order n[b] and starts
+ * at element offset off[b] of every operand buffer; its leading dimension is
+ * n[b].  info[b] receives the routine's return code.  Loops over instances in
+ * order; thread-level parallelism, when wanted, is the caller's (the routines
+ * keep no state).
+ */
+void oracle_potrf_upper_batch(int batch, const int *n, const long long *off,
+                              const double *A, double *X, int *info)
+{
+    for (int b = 0; b < batch; ++b)
+        info[b] = oracle_potrf_upper(n[b], A + off[b], n[b], X + off[b], n[b]);
+}
+
+void oracle_trsyl_lu_batch(int batch, const int *n, const long long *off,
+                           const double *L, const double *U, const double *C,
+                           double *X, int *info)
+{
+    for (int b = 0; b < batch; ++b)
+        info[b] = oracle_trsyl_lu(n[b], L + off[b], n[b], U + off[b], n[b],
+                                  C + off[b], n[b], X + off[b], n[b]);
+}
+
+void oracle_trlyap_l_batch(int batch, const int *n, const long long *off,
+                           const double *L, const double *S, double *X, int *info)
+{
+    for (int b = 0; b < batch; ++b)
+        info[b] = oracle_trlyap_l(n[b], L + off[b], n[b], S + off[b], n[b],
+                                  X + off[b], n[b]);
+}

@@ -1,0 +1,179 @@
+"""Seeded synthetic inputs for the three structured solves.
+
+This module builds problem instances and nothing else: it holds none of the
+solvers' arithmetic and imports neither the library binding nor the oracle.
+Both sides of every parity check (the CUDA path and the CPU oracle) consume the
+same arrays produced here.
+
+Instances are packed into one flat float64 buffer per operand.  Instance ``b``
+is an ``n[b] x n[b]`` column-major matrix with leading dimension ``n[b]`` that
+starts at element offset ``off[b]``; offsets are multiples of 32 elements
+(256 bytes) so that every instance starts on a 256-byte boundary.
+
+Recipes (the paper's case studies are square double-precision matrices, Fig. 2
+caption; the distributions below stand in for its size sweep, which used no
+public dataset):
+
+* Cholesky:  X0 upper triangular with N(0,1) entries (diagonal included),
+  A = X0^T X0 + n I.  ``exact=True`` instead draws X0 with integer entries
+  (off-diagonal in [-3, 3], diagonal in [1, 4]) and A = X0^T X0, which is exact
+  in FP64, so the unique factor with positive diagonal is X0 itself.
+* Sylvester: L lower and U upper triangular, off-diagonals N(0,1)/sqrt(n),
+  diagonals uniform in [1, 2]; X0 ~ N(0,1); C = L X0 + X0 U.
+* Lyapunov:  L as above; X0 symmetric (lower triangle of G ~ N(0,1) mirrored);
+  M = L X0 and S = M + M^T, exactly symmetric.
+
+Every instance draws from its own generator seeded with ``(seed, b)``, so a
+single instance of a large batch can be regenerated on its own.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+ALIGN_ELEMS = 32
+
+
+@dataclasses.dataclass
+class Packed:
+    """A batch of square instances packed into flat float64 operand buffers."""
+
+    n: np.ndarray            # int32 [batch]
+    off: np.ndarray          # int64 [batch], element offsets
+    total: int               # elements per operand buffer
+    ops: dict                # name -> float64 [total]
+
+    @property
+    def batch(self) -> int:
+        return int(self.n.shape[0])
+
+    def view(self, name: str, b: int) -> np.ndarray:
+        """Column-major n x n view of instance b of operand ``name``."""
+        nb = int(self.n[b])
+        o = int(self.off[b])
+        return self.ops[name][o:o + nb * nb].reshape(nb, nb, order="F")
+
+
+def pack_offsets(n: np.ndarray, align: int = ALIGN_ELEMS):
+    n = np.asarray(n, dtype=np.int64)
+    sizes = ((n * n + align - 1) // align) * align
+    off = np.zeros_like(sizes)
+    if len(sizes) > 1:
+        off[1:] = np.cumsum(sizes)[:-1]
+    total = int(sizes.sum()) if len(sizes) else 0
+    return off, max(total, align)
+
+
+def sizes_fixed(batch: int, n: int) -> np.ndarray:
+    return np.full(batch, n, dtype=np.int32)
+
+
+def sizes_uniform(batch: int, lo: int, hi: int, seed: int) -> np.ndarray:
+    """n uniform over the integers lo..hi inclusive."""
+    rng = np.random.default_rng([seed, 0x5151])
+    return rng.integers(lo, hi + 1, size=batch).astype(np.int32)
+
+
+def sizes_log_uniform(batch: int, lo: int, hi: int, seed: int) -> np.ndarray:
+    """n = round(exp(U(ln lo, ln hi))), clipped to [lo, hi]."""
+    rng = np.random.default_rng([seed, 0x10a1])
+    v = np.rint(np.exp(rng.uniform(math.log(lo), math.log(hi), size=batch)))
+    return np.clip(v, lo, hi).astype(np.int32)
+
+
+def _instance_rng(seed: int, b: int) -> np.random.Generator:
+    return np.random.default_rng([seed, 7919, b])
+
+
+def _tri_factors(rng: np.random.Generator, n: int, lower: bool) -> np.ndarray:
+    m = rng.standard_normal((n, n)) / math.sqrt(n)
+    m = np.tril(m, -1) if lower else np.triu(m, 1)
+    m[np.diag_indices(n)] = rng.uniform(1.0, 2.0, size=n)
+    return m
+
+
+def cholesky_instance(n: int, seed: int, b: int, exact: bool = False):
+    rng = _instance_rng(seed, b)
+    if exact:
+        x0 = np.triu(rng.integers(-3, 4, size=(n, n)).astype(np.float64), 1)
+        x0[np.diag_indices(n)] = rng.integers(1, 5, size=n).astype(np.float64)
+        a = x0.T @ x0
+    else:
+        x0 = np.triu(rng.standard_normal((n, n)))
+        a = x0.T @ x0 + n * np.eye(n)
+        a = 0.5 * (a + a.T)
+    return a, x0
+
+
+def sylvester_instance(n: int, seed: int, b: int):
+    rng = _instance_rng(seed, b)
+    l = _tri_factors(rng, n, lower=True)
+    u = _tri_factors(rng, n, lower=False)
+    x0 = rng.standard_normal((n, n))
+    c = l @ x0 + x0 @ u
+    return l, u, c, x0
+
+
+def lyapunov_instance(n: int, seed: int, b: int):
+    rng = _instance_rng(seed, b)
+    l = _tri_factors(rng, n, lower=True)
+    g = rng.standard_normal((n, n))
+    x0 = np.tril(g) + np.tril(g, -1).T
+    m = l @ x0
+    s = m + m.T
+    return l, s, x0
+
+
+def _pack(n: np.ndarray, names, make) -> Packed:
+    n = np.asarray(n, dtype=np.int32)
+    off, total = pack_offsets(n)
+    ops = {k: np.zeros(total, dtype=np.float64) for k in names}
+    for b, nb in enumerate(n):
+        mats = make(int(nb), b)
+        o = int(off[b])
+        for k, m in zip(names, mats):
+            ops[k][o:o + nb * nb] = np.asarray(m, dtype=np.float64).ravel(order="F")
+    return Packed(n=n, off=off, total=total, ops=ops)
+
+
+def cholesky_batch(n, seed: int, exact: bool = False) -> Packed:
+    return _pack(n, ("A", "X0"), lambda nb, b: cholesky_instance(nb, seed, b, exact))
+
+
+def sylvester_batch(n, seed: int) -> Packed:
+    return _pack(n, ("L", "U", "C", "X0"), lambda nb, b: sylvester_instance(nb, seed, b))
+
+
+def lyapunov_batch(n, seed: int) -> Packed:
+    return _pack(n, ("L", "S", "X0"), lambda nb, b: lyapunov_instance(nb, seed, b))
+
+
+# The workloads measured and parity-checked by this project, by name.
+WORKLOADS = {
+    # plain FP64 upper Cholesky, 1024 instances of order 64
+    "potrf_1024x64": dict(op="potrf", sizes=lambda s: sizes_fixed(1024, 64)),
+    # FP64 triangular Sylvester, 4096 instances, n uniform in {4..128}
+    "trsyl_4096xU4-128": dict(op="trsyl", sizes=lambda s: sizes_uniform(4096, 4, 128, s)),
+    # triangular Lyapunov, 2048 instances of order 128
+    "trlyap_2048x128": dict(op="trlyap", sizes=lambda s: sizes_fixed(2048, 128)),
+    # mixed-size Cholesky, 8192 instances, n log-uniform in [8, 256]
+    "potrf_8192xLU8-256": dict(op="potrf", sizes=lambda s: sizes_log_uniform(8192, 8, 256, s)),
+}
+
+
+def make_workload(name: str, seed: int = 1234) -> Packed:
+    w = WORKLOADS[name]
+    n = w["sizes"](seed)
+    return make_batch(w["op"], n, seed)
+
+
+def make_batch(op: str, n, seed: int) -> Packed:
+    if op == "potrf":
+        return cholesky_batch(n, seed)
+    if op == "trsyl":
+        return sylvester_batch(n, seed)
+    if op == "trlyap":
+        return lyapunov_batch(n, seed)
+    raise ValueError(f"unknown op {op!r}")
