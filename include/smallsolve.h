@@ -1,0 +1,167 @@
+/*
+ * smallsolve.h -- C ABI of the batched small structured-solve library
+ * (CUDA, sm_103a).
+ *
+ * The operations are the three case studies of "Program Generation for Linear
+ * Algebra Using Multiple Layers of DSLs" (Spampinato, Fabregat-Traver,
+ * Pueschel, Bientinesi), Fig. 2 caption:
+ *   potrf_upper:  X^T X = A           A SPD, X upper triangular   (Fig. 2a)
+ *   trlyap_l:     L X + X L^T = S     L lower, S and X symmetric  (Fig. 2b)
+ *   trsyl_lu:     L X + X U = C       L lower, U upper            (Fig. 2c)
+ * all in double precision (the "Preliminary performance results" paragraph),
+ * here for many independent small instances per call.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Memory.  Every pointer argument whose name starts with d_ is a DEVICE
+ * pointer.  The caller owns all memory; the library allocates nothing on the
+ * solve path and never synchronises the stream.  Pointer arrays (d_A, d_X, ...)
+ * are device arrays of `batch` device pointers; size arrays (d_n, d_ld*) are
+ * device arrays of `batch` ints.
+ *
+ * Layout.  Instance b is column-major: element (i, j) of operand M sits at
+ * d_M[b][i + j * d_ldm[b]], 0 <= i, j < d_n[b], with d_ldm[b] >= max(1, d_n[b]).
+ *
+ * Triangles.  Only the structurally meaningful triangle of an input is read:
+ * A upper, L lower, U upper, S lower.  Only the upper triangle of the Cholesky
+ * X and the lower triangle of the Lyapunov X are written; the other strict
+ * triangle of X is left untouched.  The Sylvester X is written in full.
+ * X may alias the right-hand side (X == A, X == C or X == S per instance with
+ * the same leading dimension); it must not overlap anything else.
+ *
+ * Sizes.  0 <= d_n[b] <= max_n <= SS_MAX_N.  max_n is a host-side bound used to
+ * size the launch; an instance whose device-side n violates it is skipped and
+ * gets info = SS_INFO_BAD_SIZE.  n = 0 is an empty instance (info = 0).
+ *
+ * Modes (`mode`).  SS_MODE_FP64 computes in FP64 throughout.  The *_REFINED
+ * modes solve in low precision (the update products in TF32 or BF16 on the
+ * tensor cores with FP32 accumulation, or in FP32 on the CUDA cores; diagonal
+ * blocks, square roots and divisions stay FP64) and then apply FP64 iterative
+ * refinement until the relative correction falls below SS_REFINE_TOL or
+ * SS_REFINE_MAXIT steps ran.  The *_RAW modes stop after the low-precision
+ * solve.  Refined and raw modes need workspace (see ss_workspace_size).
+ *
+ * Configurations (`cfg`).  cfg >= 0 selects a kernel configuration by id
+ * (0 <= cfg < ss_config_count(op, mode)); cfg = SS_CFG_TABLE uses the per-size
+ * table set with ss_set_config_table (the autotuner's or the learned
+ * selector's choice), falling back to the built-in default for sizes the table
+ * leaves at -1; cfg = SS_CFG_DEFAULT uses the built-in default.
+ *
+ * Return value.  0 on success; -k if argument k (1-based) is invalid, checked
+ * on the host before anything is launched; SS_ERR_CUDA if a launch failed.
+ * Per-instance numerical outcomes go to d_info[b] (written on the stream):
+ *   0                  success;
+ *   k > 0  (potrf)     leading minor k is not positive (pivot k-1, 0-based,
+ *                      was <= 0 or NaN); columns >= k-1 of X are undefined;
+ *   1      (trsyl, trlyap) some divisor l_ii + u_jj (l_ii + l_jj) has
+ *                      magnitude <= n * DBL_EPSILON * max diagonal magnitude,
+ *                      or is NaN; X is computed anyway and may hold Inf/NaN;
+ *   n + 1  (refined modes) refinement did not reach SS_REFINE_TOL within
+ *                      SS_REFINE_MAXIT steps; X holds the last iterate;
+ *   SS_INFO_BAD_SIZE   d_n[b] < 0 or d_n[b] > max_n; X untouched;
+ *   SS_INFO_NO_WORK    the workspace was too small for this instance.
+ *
+ * Streams.  `stream` is a cudaStream_t (NULL: the legacy default stream).
+ * Every call is asynchronous with respect to the host.
+ */
+#ifndef SMALLSOLVE_H
+#define SMALLSOLVE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SS_MAX_N 4096
+
+/* operations */
+#define SS_OP_POTRF  0
+#define SS_OP_TRSYL  1
+#define SS_OP_TRLYAP 2
+
+/* modes */
+#define SS_MODE_FP64          0
+#define SS_MODE_FP32_REFINED  1
+#define SS_MODE_TF32_REFINED  2
+#define SS_MODE_BF16_REFINED  3
+#define SS_MODE_FP32_RAW      4
+#define SS_MODE_TF32_RAW      5
+#define SS_MODE_BF16_RAW      6
+#define SS_NUM_MODES          7
+
+/* configuration selectors */
+#define SS_CFG_DEFAULT (-1)
+#define SS_CFG_TABLE   (-2)
+
+/* return and info codes */
+#define SS_ERR_CUDA       (-100)
+#define SS_INFO_BAD_SIZE  (-1)
+#define SS_INFO_NO_WORK   (-2)
+
+#define SS_REFINE_MAXIT 10
+#define SS_REFINE_TOL   1e-13
+
+/*
+ * Upper Cholesky X^T X = A (Fig. 2a).  Reads the upper triangle of A, writes
+ * the upper triangle of X with a positive diagonal.
+ */
+int potrf_upper(int batch, int max_n, const int *d_n,
+                const double *const *d_A, const int *d_lda,
+                double *const *d_X, const int *d_ldx, int *d_info,
+                int mode, int cfg, void *d_work, size_t work_bytes, void *stream);
+
+/*
+ * Triangular Sylvester L X + X U = C (Fig. 2c).  Reads the lower triangle of
+ * L, the upper triangle of U and all of C; writes all of X.
+ */
+int trsyl_lu(int batch, int max_n, const int *d_n,
+             const double *const *d_L, const int *d_ldl,
+             const double *const *d_U, const int *d_ldu,
+             const double *const *d_C, const int *d_ldc,
+             double *const *d_X, const int *d_ldx, int *d_info,
+             int mode, int cfg, void *d_work, size_t work_bytes, void *stream);
+
+/*
+ * Triangular Lyapunov L X + X L^T = S (Fig. 2b).  Reads the lower triangles of
+ * L and S; writes the lower triangle of the symmetric X.
+ */
+int trlyap_l(int batch, int max_n, const int *d_n,
+             const double *const *d_L, const int *d_ldl,
+             const double *const *d_S, const int *d_lds,
+             double *const *d_X, const int *d_ldx, int *d_info,
+             int mode, int cfg, void *d_work, size_t work_bytes, void *stream);
+
+/*
+ * Workspace, in bytes, that a call of `op` with this batch, max_n and mode
+ * needs (the bound assumes every instance has order max_n).  Returns 0 and
+ * writes *bytes, or a negative argument error.
+ */
+int ss_workspace_size(int op, int batch, int max_n, int mode, size_t *bytes);
+
+/*
+ * Kernel configurations.  ss_config_count returns how many explicit
+ * configurations `op` has in `mode` (or a negative error);
+ * ss_config_describe writes the block size, threads per CTA and algorithm
+ * variant of configuration `cfg` (any pointer may be NULL).
+ */
+int ss_config_count(int op, int mode);
+int ss_config_describe(int op, int mode, int cfg, int *block, int *threads, int *variant);
+
+/*
+ * Per-size configuration table used by cfg = SS_CFG_TABLE.  cfg_by_n[k] is the
+ * configuration for instances of order n with bin(n) = k, where bin(n) =
+ * ceil(log2(max(n, 1))) (so bins 0..12 cover n up to 4096); -1 means the
+ * built-in default.  The table is host-side library state, copied; setting
+ * nbins = 0 clears it.  Calls are not thread-safe with concurrent solves.
+ */
+int ss_set_config_table(int op, int mode, int nbins, const int *cfg_by_bin);
+
+/* Library version and the number of the CUDA device the calls run on. */
+int ss_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SMALLSOLVE_H */

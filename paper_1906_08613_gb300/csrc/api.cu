@@ -1,0 +1,307 @@
+// C ABI of the library (declared in include/smallsolve.h): argument checks,
+// configuration selection, workspace layout and the launch plan of one call
+// (binning pre-pass, then one persistent solve launch per launch group).
+#include <string.h>
+
+#include <mutex>
+
+#include "ss_internal.h"
+
+namespace ss {
+
+cudaError_t launch_potrf_fp64(const Operands &o, const Sched &s, const Launch &l, cudaStream_t st);
+cudaError_t launch_syl_fp64(const Operands &o, const Sched &s, const Launch &l, cudaStream_t st, bool lyap);
+cudaError_t launch_mixed(int op, const Operands &o, const Sched &s, const Launch &l, cudaStream_t st);
+int mixed_config_count(int op, int mode);
+const Config *mixed_config_get(int op, int mode, int cfg);
+long long mixed_scratch_per_n2(int op, int mode);
+
+namespace {
+
+const Config kFp64Configs[] = {
+    {8, 64, 0}, {16, 64, 0}, {16, 128, 0}, {32, 128, 0}, {32, 256, 0},
+};
+constexpr int kNumFp64 = sizeof(kFp64Configs) / sizeof(kFp64Configs[0]);
+
+int host_bin(int n) { int k = 0; while ((1 << k) < n) ++k; return k; }
+
+bool valid_op(int op) { return op == SS_OP_POTRF || op == SS_OP_TRSYL || op == SS_OP_TRLYAP; }
+bool valid_mode(int m) { return m >= 0 && m < SS_NUM_MODES; }
+
+struct TableState {
+    std::mutex mu;
+    int table[3][SS_NUM_MODES][NUM_BINS];
+    TableState()
+    {
+        for (auto &a : table) for (auto &b : a) for (int &c : b) c = -1;
+    }
+};
+TableState &tables()
+{
+    static TableState t;
+    return t;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+int config_count(int op, int mode)
+{
+    if (mode == SS_MODE_FP64) return kNumFp64;
+    return mixed_config_count(op, mode);
+}
+
+const Config *config_get(int op, int mode, int cfg)
+{
+    if (cfg < 0 || cfg >= config_count(op, mode)) return nullptr;
+    if (mode == SS_MODE_FP64) return &kFp64Configs[cfg];
+    return mixed_config_get(op, mode, cfg);
+}
+
+// Built-in default: a single configuration chosen from the largest order.
+int config_default(int op, int mode, int max_n)
+{
+    (void)op;
+    if (mode == SS_MODE_FP64) {
+        if (max_n <= 8) return 0;
+        if (max_n <= 16) return 1;
+        if (max_n <= 32) return 2;
+        return 3;
+    }
+    return 0;
+}
+
+int sm_count()
+{
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+    if (cache[dev] == 0) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cache[dev] = v > 0 ? v : 1;
+    }
+    return cache[dev];
+}
+
+static long long scratch_per_n2(int op, int mode)
+{
+    return mode == SS_MODE_FP64 ? 0 : mixed_scratch_per_n2(op, mode);
+}
+
+// Workspace layout: [meta: META_INTS ints][perm: batch ints][scr: batch
+// int64][scratch: batch * max_n^2 * scratch_per_n2 floats], each part aligned
+// to 256 bytes.
+size_t workspace_bytes(int op, int batch, int max_n, int mode)
+{
+    size_t b = align_up(META_INTS * sizeof(int), 256);
+    b += align_up((size_t)batch * sizeof(int), 256);
+    const long long per = scratch_per_n2(op, mode);
+    if (per > 0) {
+        b += align_up((size_t)batch * sizeof(long long), 256);
+        b += align_up((size_t)batch * (size_t)max_n * (size_t)max_n * (size_t)per * sizeof(float), 256);
+    }
+    return b;
+}
+
+void carve_workspace(void *d_work, int batch, int max_n, int mode, Sched *s)
+{
+    (void)max_n;
+    char *p = static_cast<char *>(d_work);
+    s->meta = reinterpret_cast<int *>(p);
+    p += align_up(META_INTS * sizeof(int), 256);
+    s->perm = reinterpret_cast<const int *>(p);
+    p += align_up((size_t)batch * sizeof(int), 256);
+    s->scr = nullptr;
+    s->scratch = nullptr;
+    s->scratch_elems = 0;
+    (void)mode;
+}
+
+}  // namespace ss
+
+using namespace ss;
+
+namespace {
+
+// Shared driver of the three entry points.
+int run(int op, int batch, int max_n, const Operands &o, int mode, int cfg, void *d_work,
+        size_t work_bytes, void *stream, int arg_mode, int arg_work)
+{
+    if (!valid_mode(mode)) return -arg_mode;
+    const int ncfg = config_count(op, mode);
+    if (ncfg <= 0) return -arg_mode;
+    if (!(cfg == SS_CFG_DEFAULT || cfg == SS_CFG_TABLE || (cfg >= 0 && cfg < ncfg))) return -(arg_mode + 1);
+    if (batch == 0) return 0;
+    const size_t need = workspace_bytes(op, batch, max_n, mode);
+    if (d_work == nullptr) return -arg_work;
+    if (work_bytes < need) return -(arg_work + 1);
+
+    // Configuration per size bin, then launch groups = runs of equal configs.
+    int by_bin[NUM_BINS];
+    const int top = host_bin(max_n > 0 ? max_n : 1);
+    for (int k = 0; k < NUM_BINS; ++k) {
+        int c = -1;
+        if (cfg >= 0) c = cfg;
+        else if (cfg == SS_CFG_TABLE) {
+            std::lock_guard<std::mutex> g(tables().mu);
+            c = tables().table[op][mode][k];
+        }
+        if (c < 0 || c >= ncfg) c = config_default(op, mode, max_n);
+        by_bin[k] = c;
+    }
+    int group_of_bin[NUM_BINS];
+    int group_cfg[MAX_GROUPS];
+    int ngroups = 0;
+    for (int k = NUM_BINS - 1; k >= 0; --k) {
+        if (k > top) { group_of_bin[k] = -1; continue; }
+        if (ngroups > 0 && group_cfg[ngroups - 1] == by_bin[k]) {
+            group_of_bin[k] = ngroups - 1;
+        } else {
+            if (ngroups == MAX_GROUPS) return SS_ERR_CUDA;
+            group_cfg[ngroups] = by_bin[k];
+            group_of_bin[k] = ngroups++;
+        }
+    }
+
+    Sched s;
+    carve_workspace(d_work, batch, max_n, mode, &s);
+    const long long per = scratch_per_n2(op, mode);
+    if (per > 0) {
+        char *p = reinterpret_cast<char *>(const_cast<int *>(s.perm)) + align_up((size_t)batch * sizeof(int), 256);
+        s.scr = reinterpret_cast<const long long *>(p);
+        p += align_up((size_t)batch * sizeof(long long), 256);
+        s.scratch = p;
+        s.scratch_elems = (long long)((d_work == nullptr ? 0 : (static_cast<char *>(d_work) + work_bytes) - p) / sizeof(float));
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_binning(batch, max_n, o.n, o.info, s, group_of_bin, ngroups, per, st);
+    if (e != cudaSuccess) return SS_ERR_CUDA;
+    for (int g = 0; g < ngroups; ++g) {
+        Launch l{g, group_cfg[g], mode, max_n, batch};
+        if (mode == SS_MODE_FP64) {
+            if (op == SS_OP_POTRF) e = launch_potrf_fp64(o, s, l, st);
+            else e = launch_syl_fp64(o, s, l, st, op == SS_OP_TRLYAP);
+        } else {
+            e = launch_mixed(op, o, s, l, st);
+        }
+        if (e != cudaSuccess) return SS_ERR_CUDA;
+    }
+    return 0;
+}
+
+bool bad_common(int batch, int max_n) { return batch < 0 || max_n < 0 || max_n > SS_MAX_N; }
+
+}  // namespace
+
+extern "C" {
+
+int potrf_upper(int batch, int max_n, const int *d_n, const double *const *d_A, const int *d_lda,
+                double *const *d_X, const int *d_ldx, int *d_info, int mode, int cfg,
+                void *d_work, size_t work_bytes, void *stream)
+{
+    if (batch < 0) return -1;
+    if (max_n < 0 || max_n > SS_MAX_N) return -2;
+    if (batch > 0) {
+        if (!d_n) return -3;
+        if (!d_A) return -4;
+        if (!d_lda) return -5;
+        if (!d_X) return -6;
+        if (!d_ldx) return -7;
+        if (!d_info) return -8;
+    }
+    Operands o{d_n, d_A, d_lda, nullptr, nullptr, nullptr, nullptr, d_X, d_ldx, d_info};
+    return run(SS_OP_POTRF, batch, max_n, o, mode, cfg, d_work, work_bytes, stream, 9, 11);
+}
+
+int trsyl_lu(int batch, int max_n, const int *d_n, const double *const *d_L, const int *d_ldl,
+             const double *const *d_U, const int *d_ldu, const double *const *d_C, const int *d_ldc,
+             double *const *d_X, const int *d_ldx, int *d_info, int mode, int cfg, void *d_work,
+             size_t work_bytes, void *stream)
+{
+    if (batch < 0) return -1;
+    if (max_n < 0 || max_n > SS_MAX_N) return -2;
+    if (batch > 0) {
+        if (!d_n) return -3;
+        if (!d_L) return -4;
+        if (!d_ldl) return -5;
+        if (!d_U) return -6;
+        if (!d_ldu) return -7;
+        if (!d_C) return -8;
+        if (!d_ldc) return -9;
+        if (!d_X) return -10;
+        if (!d_ldx) return -11;
+        if (!d_info) return -12;
+    }
+    Operands o{d_n, d_L, d_ldl, d_U, d_ldu, d_C, d_ldc, d_X, d_ldx, d_info};
+    return run(SS_OP_TRSYL, batch, max_n, o, mode, cfg, d_work, work_bytes, stream, 13, 15);
+}
+
+int trlyap_l(int batch, int max_n, const int *d_n, const double *const *d_L, const int *d_ldl,
+             const double *const *d_S, const int *d_lds, double *const *d_X, const int *d_ldx,
+             int *d_info, int mode, int cfg, void *d_work, size_t work_bytes, void *stream)
+{
+    if (batch < 0) return -1;
+    if (max_n < 0 || max_n > SS_MAX_N) return -2;
+    if (batch > 0) {
+        if (!d_n) return -3;
+        if (!d_L) return -4;
+        if (!d_ldl) return -5;
+        if (!d_S) return -6;
+        if (!d_lds) return -7;
+        if (!d_X) return -8;
+        if (!d_ldx) return -9;
+        if (!d_info) return -10;
+    }
+    Operands o{d_n, d_L, d_ldl, nullptr, nullptr, d_S, d_lds, d_X, d_ldx, d_info};
+    return run(SS_OP_TRLYAP, batch, max_n, o, mode, cfg, d_work, work_bytes, stream, 11, 13);
+}
+
+int ss_workspace_size(int op, int batch, int max_n, int mode, size_t *bytes)
+{
+    if (!valid_op(op)) return -1;
+    if (batch < 0) return -2;
+    if (max_n < 0 || max_n > SS_MAX_N) return -3;
+    if (!valid_mode(mode)) return -4;
+    if (!bytes) return -5;
+    *bytes = workspace_bytes(op, batch, max_n, mode);
+    return 0;
+}
+
+int ss_config_count(int op, int mode)
+{
+    if (!valid_op(op)) return -1;
+    if (!valid_mode(mode)) return -2;
+    return config_count(op, mode);
+}
+
+int ss_config_describe(int op, int mode, int cfg, int *block, int *threads, int *variant)
+{
+    if (!valid_op(op)) return -1;
+    if (!valid_mode(mode)) return -2;
+    const Config *c = config_get(op, mode, cfg);
+    if (!c) return -3;
+    if (block) *block = c->block;
+    if (threads) *threads = c->threads;
+    if (variant) *variant = c->variant;
+    return 0;
+}
+
+int ss_set_config_table(int op, int mode, int nbins, const int *cfg_by_bin)
+{
+    if (!valid_op(op)) return -1;
+    if (!valid_mode(mode)) return -2;
+    if (nbins < 0 || nbins > NUM_BINS) return -3;
+    if (nbins > 0 && !cfg_by_bin) return -4;
+    const int ncfg = config_count(op, mode);
+    for (int k = 0; k < nbins; ++k)
+        if (cfg_by_bin[k] < -1 || cfg_by_bin[k] >= ncfg) return -4;
+    std::lock_guard<std::mutex> g(tables().mu);
+    for (int k = 0; k < NUM_BINS; ++k) tables().table[op][mode][k] = k < nbins ? cfg_by_bin[k] : -1;
+    return 0;
+}
+
+int ss_version(void) { return 1; }
+
+}  // extern "C"

@@ -1,0 +1,375 @@
+// Plain FP64 batched solvers: upper Cholesky (Fig. 2a), triangular Lyapunov
+// (Fig. 2b) and triangular Sylvester (Fig. 2c) of the paper.
+//
+// One CTA solves one instance at a time and pulls instances from a persistent
+// queue ordered by size, largest first.  Each instance is processed in B x B
+// blocks with the "lazy" (left-looking) loop order: a block of the result is
+// finished in one visit, after accumulating every update it needs from
+// already finished blocks, and is then written once.  The updates are the
+// GEMM/SYRK part (register-tiled, FP64 FMA); the diagonal work (square roots,
+// the divisions by x_ii and by l_ii + u_jj) is a wavefront of split dot
+// products over the block in shared memory.
+//
+// Blocked recurrences (2 x 2 partitioning of the defining equations):
+//   Cholesky   X_IJ = X_II^{-T} (A_IJ - sum_{K<I} X_KI^T X_KJ),  I < J,
+//              X_JJ = chol(A_JJ - sum_{K<J} X_KJ^T X_KJ);
+//   Sylvester  L_II X_IJ + X_IJ U_JJ = C_IJ - sum_{K<I} L_IK X_KJ - sum_{K<J} X_IK U_KJ;
+//   Lyapunov   the Sylvester recurrence with U = L^T over the blocks I >= J,
+//              reading X_KJ (K < J) as X_JK^T.
+#include "ss_device.cuh"
+#include "ss_internal.h"
+
+namespace ss {
+namespace {
+
+// Shared memory of one CTA: five tiles plus a few scalars.
+template <int B>
+constexpr size_t smem_bytes() { return (size_t)5 * Tile<B>::SZ * sizeof(double) + 2 * B * sizeof(double); }
+
+__device__ __forceinline__ double block_max_abs_diag(const double *P, long ld, int n, double *s_red)
+{
+    double m = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs(P[i + (long)i * ld]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    double r = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, s_red[w]);
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------- Sylvester
+//
+// Solve Lt Y + Y Ut = T in place for an m x nn block in sT, Lt = sL (lower
+// triangular m x m), Ut = sU (upper, nn x nn) or, with UT, the transpose of
+// the lower triangular sU.  Wavefront over anti-diagonals d = i + j; the
+// entries of one anti-diagonal are independent and each is a dot product of
+// length d split over `split` lanes.  Returns 1 if a divisor was tiny.
+template <int B, int T, bool UT>
+__device__ int syl_diag(const double *sL, const double *sU, double *sT, int m, int nn, double delta)
+{
+    constexpr int LD = Tile<B>::LD;
+    int bad = 0;
+    for (int d = 0; d <= m + nn - 2; ++d) {
+        const int ilo = max(0, d - nn + 1), ihi = min(d, m - 1);
+        const int cnt = ihi - ilo + 1;
+        const int split = pick_split<T>(cnt, d);
+        if (warp_has_work(cnt, split)) {
+            const int idx = threadIdx.x / split, part = threadIdx.x % split;
+            const bool act = idx < cnt;
+            const int i = ilo + (act ? idx : 0), j = d - i;
+            double s = 0.0;
+            if (act) {
+                for (int k = part; k < i; k += split) s = fma(sL[i + k * LD], sT[k + j * LD], s);
+                for (int k = part; k < j; k += split) {
+                    const double u = UT ? sU[j + k * LD] : sU[k + j * LD];
+                    s = fma(sT[i + k * LD], u, s);
+                }
+            }
+            s = group_sum(s, split);
+            if (act && part == 0) {
+                const double dd = sL[i + i * LD] + (UT ? sU[j + j * LD] : sU[j + j * LD]);
+                if (!(fabs(dd) > delta)) bad = 1;
+                sT[i + j * LD] = (sT[i + j * LD] - s) / dd;
+            }
+        }
+        __syncthreads();
+    }
+    return bad;
+}
+
+// One Sylvester (LYAP = false) or Lyapunov (LYAP = true, U unused) instance.
+template <int B, int T, bool LYAP>
+__device__ void syl_instance(int n, const double *L, long ldl, const double *U, long ldu,
+                             const double *C, long ldc, double *X, long ldx, int *info,
+                             double *sm)
+{
+    constexpr int LD = Tile<B>::LD, SZ = Tile<B>::SZ, E = B * B / T;
+    double *sA = sm, *sB = sm + SZ, *sT = sm + 2 * SZ, *sL = sm + 3 * SZ, *sU = sm + 4 * SZ;
+    double *s_red = sm + 5 * SZ;
+    const int nb = (n + B - 1) / B;
+
+    double md = block_max_abs_diag(L, ldl, n, s_red);
+    if (!LYAP) md = fmax(md, block_max_abs_diag(U, ldu, n, s_red));
+    const double delta = divisor_delta(n, md);
+
+    int bad = 0;
+    Slots<B, T> sl;
+    for (int I = 0; I < nb; ++I) {
+        const int mI = min(B, n - I * B);
+        const int i0 = I * B;
+        __syncthreads();
+        stage_tri<B, T>(sL, L + i0 + (long)i0 * ldl, ldl, mI, true);
+        const int jend = LYAP ? I + 1 : nb;
+        for (int J = 0; J < jend; ++J) {
+            const int nJ = min(B, n - J * B);
+            const int j0 = J * B;
+            sl.set(Shape::Full, mI, nJ);
+            double acc[E];
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                acc[r] = 0.0;
+                if (sl.ok(r)) {
+                    int rr = sl.row[r], cc = sl.col[r];
+                    // Lyapunov diagonal block: read S through its lower triangle.
+                    if (LYAP && I == J && rr < cc) { int t = rr; rr = cc; cc = t; }
+                    acc[r] = C[(i0 + rr) + (long)(j0 + cc) * ldc];
+                }
+            }
+            // sum_{K<I} L_IK X_KJ
+            for (int K = 0; K < I; ++K) {
+                const int k0 = K * B;
+                __syncthreads();
+                stage_tile<B, T>(sA, L + i0 + (long)k0 * ldl, ldl, mI, B);
+                const bool tr = LYAP && K < J;
+                if (LYAP && K == J) stage_sym_lower<B, T>(sB, X + j0 + (long)j0 * ldx, ldx, nJ);
+                else if (!tr) stage_tile<B, T>(sB, X + k0 + (long)j0 * ldx, ldx, B, nJ);
+                else          stage_tile<B, T>(sB, X + j0 + (long)k0 * ldx, ldx, nJ, B);   // X_JK
+                __syncthreads();
+                if (!tr) slot_update<B, T, false, false>(acc, sl, sA, sB, B);
+                else     slot_update<B, T, false, true>(acc, sl, sA, sB, B);
+            }
+            // sum_{K<J} X_IK U_KJ  (Lyapunov: U_KJ = L_JK^T)
+            for (int K = 0; K < J; ++K) {
+                const int k0 = K * B;
+                __syncthreads();
+                stage_tile<B, T>(sA, X + i0 + (long)k0 * ldx, ldx, mI, B);
+                if (!LYAP) stage_tile<B, T>(sB, U + k0 + (long)j0 * ldu, ldu, B, nJ);
+                else       stage_tile<B, T>(sB, L + j0 + (long)k0 * ldl, ldl, nJ, B);
+                __syncthreads();
+                if (!LYAP) slot_update<B, T, false, false>(acc, sl, sA, sB, B);
+                else       slot_update<B, T, false, true>(acc, sl, sA, sB, B);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < E; ++r)
+                if (sl.ok(r)) sT[sl.row[r] + sl.col[r] * LD] = acc[r];
+            if (!LYAP) stage_tri<B, T>(sU, U + j0 + (long)j0 * ldu, ldu, nJ, false);
+            else       stage_tri<B, T>(sU, L + j0 + (long)j0 * ldl, ldl, nJ, true);
+            __syncthreads();
+            bad |= syl_diag<B, T, LYAP>(sL, sU, sT, mI, nJ, delta);
+            // syl_diag ends with a barrier.
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                if (sl.ok(r)) {
+                    const int rr = sl.row[r], cc = sl.col[r];
+                    if (!LYAP || I != J || rr >= cc)
+                        X[(i0 + rr) + (long)(j0 + cc) * ldx] = sT[rr + cc * LD];
+                }
+            }
+        }
+    }
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) *info = bad ? 1 : 0;
+}
+
+// ----------------------------------------------------------------- Cholesky
+//
+// Factor the m x m block in sT (upper triangle) in place: X^T X = T.  Row i
+// of X needs only rows < i, so rows go one at a time and the entries of a row
+// are independent split dot products.  Returns 0 or the failing pivot + 1.
+template <int B, int T>
+__device__ int chol_diag(double *sT, int m, double *s_scal)
+{
+    constexpr int LD = Tile<B>::LD;
+    for (int i = 0; i < m; ++i) {
+        const int cnt = m - i;
+        const int split = pick_split<T>(cnt, i);
+        if (warp_has_work(cnt, split)) {
+            const int idx = threadIdx.x / split, part = threadIdx.x % split;
+            const bool act = idx < cnt;
+            const int j = i + (act ? idx : 0);
+            double s = 0.0;
+            if (act)
+                for (int k = part; k < i; k += split) s = fma(sT[k + i * LD], sT[k + j * LD], s);
+            s = group_sum(s, split);
+            if (act && part == 0) sT[i + j * LD] -= s;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const double d = sT[i + i * LD];
+            if (d > 0.0) {
+                const double p = sqrt(d);
+                sT[i + i * LD] = p;
+                s_scal[0] = 1.0 / p;
+                s_scal[1] = 0.0;
+            } else {
+                s_scal[1] = 1.0;
+            }
+        }
+        __syncthreads();
+        if (s_scal[1] != 0.0) return i + 1;
+        const double rinv = s_scal[0];
+        for (int j = i + 1 + threadIdx.x; j < m; j += T) sT[i + j * LD] *= rinv;
+        __syncthreads();
+    }
+    return 0;
+}
+
+// Solve X_II^T Y = T in place for the B x nn block in sT, X_II the upper
+// triangular factor in sD with reciprocal diagonal s_rinv.  Row i of Y needs
+// rows < i only.
+template <int B, int T>
+__device__ void chol_trsm(const double *sD, const double *s_rinv, double *sT, int m, int nn)
+{
+    constexpr int LD = Tile<B>::LD;
+    for (int i = 0; i < m; ++i) {
+        const int split = pick_split<T>(nn, i);
+        if (warp_has_work(nn, split)) {
+            const int idx = threadIdx.x / split, part = threadIdx.x % split;
+            const bool act = idx < nn;
+            const int j = act ? idx : 0;
+            double s = 0.0;
+            if (act)
+                for (int k = part; k < i; k += split) s = fma(sD[k + i * LD], sT[k + j * LD], s);
+            s = group_sum(s, split);
+            if (act && part == 0) sT[i + j * LD] = (sT[i + j * LD] - s) * s_rinv[i];
+        }
+        __syncthreads();
+    }
+}
+
+template <int B, int T>
+__device__ void potrf_instance(int n, const double *A, long lda, double *X, long ldx, int *info,
+                               double *sm)
+{
+    constexpr int LD = Tile<B>::LD, SZ = Tile<B>::SZ, E = B * B / T;
+    double *sA = sm, *sB = sm + SZ, *sT = sm + 2 * SZ, *sD = sm + 3 * SZ;
+    double *s_rinv = sm + 5 * SZ, *s_scal = s_rinv + B;
+    const int nb = (n + B - 1) / B;
+    Slots<B, T> sl;
+    for (int J = 0; J < nb; ++J) {
+        const int nJ = min(B, n - J * B);
+        const int j0 = J * B;
+        for (int I = 0; I <= J; ++I) {
+            const int i0 = I * B;
+            const bool diag = I == J;
+            const int mI = diag ? nJ : B;
+            if (diag) sl.set(Shape::Upper, nJ, nJ);
+            else      sl.set(Shape::Full, mI, nJ);
+            double acc[E];
+#pragma unroll
+            for (int r = 0; r < E; ++r)
+                acc[r] = sl.ok(r) ? A[(i0 + sl.row[r]) + (long)(j0 + sl.col[r]) * lda] : 0.0;
+            // sum_{K<I} X_KI^T X_KJ
+            for (int K = 0; K < I; ++K) {
+                const int k0 = K * B;
+                __syncthreads();
+                stage_tile<B, T>(sA, X + k0 + (long)i0 * ldx, ldx, B, mI);   // X_KI
+                stage_tile<B, T>(sB, X + k0 + (long)j0 * ldx, ldx, B, nJ);   // X_KJ
+                __syncthreads();
+                slot_update<B, T, true, false>(acc, sl, sA, sB, B);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < E; ++r)
+                if (sl.ok(r)) sT[sl.row[r] + sl.col[r] * LD] = acc[r];
+            if (!diag) {
+                stage_tri<B, T>(sD, X + i0 + (long)i0 * ldx, ldx, B, false);
+                __syncthreads();
+                for (int i = threadIdx.x; i < B; i += T) s_rinv[i] = 1.0 / sD[i + i * LD];
+                __syncthreads();
+                chol_trsm<B, T>(sD, s_rinv, sT, B, nJ);
+            } else {
+                __syncthreads();
+                const int f = chol_diag<B, T>(sT, nJ, s_scal);
+                if (f) {
+                    if (threadIdx.x == 0) *info = j0 + f;
+                    return;     // uniform: every thread saw the same pivot
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < E; ++r)
+                if (sl.ok(r)) X[(i0 + sl.row[r]) + (long)(j0 + sl.col[r]) * ldx] = sT[sl.row[r] + sl.col[r] * LD];
+        }
+    }
+    if (threadIdx.x == 0) *info = 0;
+}
+
+// --------------------------------------------------------------- kernels
+
+__device__ __forceinline__ bool next_instance(const Sched &s, int group, int *s_slot, int &b)
+{
+    const int lo = s.meta[META_RANGE + 2 * group], hi = s.meta[META_RANGE + 2 * group + 1];
+    const int w = lo + claim_slot(s.meta + META_HEAD + group, s_slot);
+    if (w >= hi) return false;
+    b = s.perm[w];
+    return true;
+}
+
+template <int B, int T>
+__global__ void __launch_bounds__(T) potrf_fp64_kernel(Operands o, Sched s, int group)
+{
+    extern __shared__ double sm[];
+    __shared__ int s_slot;
+    int b;
+    while (next_instance(s, group, &s_slot, b)) {
+        const int n = o.n[b];
+        if (n == 0) { if (threadIdx.x == 0) o.info[b] = 0; continue; }
+        potrf_instance<B, T>(n, o.A[b], o.lda[b], o.X[b], o.ldx[b], o.info + b, sm);
+    }
+}
+
+template <int B, int T, bool LYAP>
+__global__ void __launch_bounds__(T) syl_fp64_kernel(Operands o, Sched s, int group)
+{
+    extern __shared__ double sm[];
+    __shared__ int s_slot;
+    int b;
+    while (next_instance(s, group, &s_slot, b)) {
+        const int n = o.n[b];
+        if (n == 0) { if (threadIdx.x == 0) o.info[b] = 0; continue; }
+        syl_instance<B, T, LYAP>(n, o.A[b], o.lda[b], LYAP ? nullptr : o.U[b], LYAP ? 0 : o.ldu[b],
+                                 o.C[b], o.ldc[b], o.X[b], o.ldx[b], o.info + b, sm);
+    }
+}
+
+template <typename K>
+cudaError_t launch_persistent(K kernel, int threads, size_t smem, int batch, cudaStream_t st,
+                              const Operands &o, const Sched &s, int group)
+{
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    long grid = (long)per_sm * sm_count();
+    if (grid > batch) grid = batch;
+    if (grid < 1) grid = 1;
+    kernel<<<(int)grid, threads, smem, st>>>(o, s, group);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// Configuration id -> (B, T); the same table for all three ops in FP64.
+#define SS_FP64_CONFIGS(X)  X(0, 8, 64) X(1, 16, 64) X(2, 16, 128) X(3, 32, 128) X(4, 32, 256)
+
+cudaError_t launch_potrf_fp64(const Operands &o, const Sched &s, const Launch &l, cudaStream_t st)
+{
+    switch (l.cfg) {
+#define CASE(id, B, T) \
+    case id: return launch_persistent(potrf_fp64_kernel<B, T>, T, smem_bytes<B>(), l.batch, st, o, s, l.group);
+        SS_FP64_CONFIGS(CASE)
+#undef CASE
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_syl_fp64(const Operands &o, const Sched &s, const Launch &l, cudaStream_t st, bool lyap)
+{
+    switch (l.cfg) {
+#define CASE(id, B, T)                                                                                   \
+    case id:                                                                                             \
+        return lyap ? launch_persistent(syl_fp64_kernel<B, T, true>, T, smem_bytes<B>(), l.batch, st, o, s, l.group) \
+                    : launch_persistent(syl_fp64_kernel<B, T, false>, T, smem_bytes<B>(), l.batch, st, o, s, l.group);
+        SS_FP64_CONFIGS(CASE)
+#undef CASE
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace ss

@@ -1,0 +1,217 @@
+// Device building blocks shared by the solve kernels: the persistent work
+// queue, shared-memory tile staging, the register-tiled block update, and
+// split dot products.
+//
+// Tiles are B x B blocks of one instance, staged column-major in shared
+// memory with leading dimension B + 1 (odd, so a transposed read walks the
+// banks).  A CTA of T threads owns the B*B outputs of a block update with
+// element e = tid + T * r  ->  (row, col) = (e % B, e / B): each thread keeps
+// E = B*B/T accumulators for one row and E columns spaced T/B apart.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ss {
+
+template <int B>
+struct Tile {
+    static constexpr int LD = B + 1;
+    static constexpr int SZ = B * (B + 1);
+};
+
+// Claim the next slot of the persistent queue; every thread gets the value.
+__device__ __forceinline__ int claim_slot(int *head, int *s_slot)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) *s_slot = atomicAdd(head, 1);
+    __syncthreads();
+    return *s_slot;
+}
+
+// Stage a rows x cols sub-block of a column-major global matrix (leading
+// dimension ldg) into tile S, zero-filling the rest of the B x B tile.
+template <int B, int T, typename Src>
+__device__ __forceinline__ void stage_tile(double *S, const Src *G, long ldg, int rows, int cols)
+{
+    constexpr int LD = Tile<B>::LD;
+#pragma unroll 4
+    for (int e = threadIdx.x; e < B * B; e += T) {
+        const int r = e % B, c = e / B;
+        double v = 0.0;
+        if (r < rows && c < cols) v = (double)G[r + (long)c * ldg];
+        S[r + c * LD] = v;
+    }
+}
+
+// Same, but keep only the lower (lower=true) or upper triangle of the
+// sub-block (diagonal included); the other strict triangle becomes zero.
+template <int B, int T>
+__device__ __forceinline__ void stage_tri(double *S, const double *G, long ldg, int m, bool lower)
+{
+    constexpr int LD = Tile<B>::LD;
+#pragma unroll 4
+    for (int e = threadIdx.x; e < B * B; e += T) {
+        const int r = e % B, c = e / B;
+        double v = 0.0;
+        const bool keep = lower ? (r >= c) : (r <= c);
+        if (r < m && c < m && keep) v = G[r + (long)c * ldg];
+        S[r + c * LD] = v;
+    }
+}
+
+// Stage the symmetric m x m diagonal block whose lower triangle is stored in
+// G, mirroring it into the upper triangle of S; zero elsewhere.
+template <int B, int T>
+__device__ __forceinline__ void stage_sym_lower(double *S, const double *G, long ldg, int m)
+{
+    constexpr int LD = Tile<B>::LD;
+#pragma unroll 4
+    for (int e = threadIdx.x; e < B * B; e += T) {
+        const int r = e % B, c = e / B;
+        double v = 0.0;
+        if (r < m && c < m) v = r >= c ? G[r + (long)c * ldg] : G[c + (long)r * ldg];
+        S[r + c * LD] = v;
+    }
+}
+
+// Register-tiled block update  acc -= op(A) * op(Bm)  over kk terms, with
+// op(A)(row, k) = TA ? A[k + row*LD] : A[row + k*LD] and
+// op(Bm)(k, col) = TB ? Bm[col + k*LD] : Bm[k + col*LD].
+template <int B, int T, bool TA, bool TB>
+__device__ __forceinline__ void block_update(double (&acc)[B * B / T], const double *A,
+                                             const double *Bm, int kk)
+{
+    constexpr int LD = Tile<B>::LD;
+    constexpr int E = B * B / T;
+    constexpr int CS = T / B;
+    const int row = threadIdx.x % B;
+    const int col0 = threadIdx.x / B;
+#pragma unroll 2
+    for (int k = 0; k < kk; ++k) {
+        const double a = TA ? A[k + row * LD] : A[row + k * LD];
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int col = col0 + CS * r;
+            const double b = TB ? Bm[col + k * LD] : Bm[k + col * LD];
+            acc[r] = fma(-a, b, acc[r]);
+        }
+    }
+}
+
+// Sum over aligned groups of `split` lanes (a power of two <= 32).  Every lane
+// of the warp must call it.
+__device__ __forceinline__ double group_sum(double v, int split)
+{
+    for (int o = split >> 1; o > 0; o >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int pow2_floor(int x)
+{
+    return x <= 1 ? 1 : (1 << (31 - __clz(x)));
+}
+
+// Lanes per dot product when `cnt` dot products of length about `len` share T
+// threads: a power of two, at most 32, at most T/cnt, and small enough that
+// each lane still does about four terms.
+template <int T>
+__device__ __forceinline__ int pick_split(int cnt, int len)
+{
+    int s = pow2_floor(T / (cnt > 0 ? cnt : 1));
+    int byLen = pow2_floor(len / 4 > 0 ? len / 4 : 1);
+    s = s < byLen ? s : byLen;
+    return s > 32 ? 32 : s;
+}
+
+// Threshold below which a Sylvester/Lyapunov divisor counts as singular:
+// n * DBL_EPSILON * (largest diagonal magnitude).
+__device__ __forceinline__ double divisor_delta(int n, double maxdiag)
+{
+    return (double)n * 2.220446049250313e-16 * maxdiag;
+}
+
+}  // namespace ss
+
+namespace ss {
+
+// Which outputs of a block a thread owns.  Slot r of thread tid is flat index
+// e = tid + T*r over the block's valid elements, so lanes only ever hold real
+// outputs and padded rows or columns cost no arithmetic.
+enum class Shape { Full, Upper, Lower };
+
+template <int B, int T>
+struct Slots {
+    static constexpr int E = B * B / T;
+    int row[E];
+    int col[E];
+    unsigned valid;
+
+    // Column index c with c(c+1)/2 <= e < (c+1)(c+2)/2.
+    __device__ __forceinline__ static int tri_decode(int e)
+    {
+        int c = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+        while (c * (c + 1) / 2 > e) --c;
+        while ((c + 1) * (c + 2) / 2 <= e) ++c;
+        return c;
+    }
+
+    __device__ __forceinline__ void set(Shape s, int m, int nn)
+    {
+        valid = 0u;
+        const int cnt = s == Shape::Full ? m * nn : nn * (nn + 1) / 2;
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int e = threadIdx.x + T * r;
+            int rr = 0, cc = 0;
+            if (e < cnt) {
+                if (s == Shape::Full) {
+                    rr = e % m;
+                    cc = e / m;
+                } else {
+                    const int t = tri_decode(e);
+                    const int u = e - t * (t + 1) / 2;   // 0 <= u <= t
+                    if (s == Shape::Upper) { rr = u; cc = t; }
+                    else                   { rr = t; cc = u; }
+                }
+                valid |= 1u << r;
+            }
+            row[r] = rr;
+            col[r] = cc;
+        }
+    }
+    __device__ __forceinline__ bool ok(int r) const { return (valid >> r) & 1u; }
+};
+
+// acc[r] -= sum_k op(A)(row[r], k) * op(Bm)(k, col[r]) over kk terms, with
+// op(A)(i, k) = TA ? A[k + i*LD] : A[i + k*LD] and
+// op(Bm)(k, j) = TB ? Bm[j + k*LD] : Bm[k + j*LD].
+template <int B, int T, bool TA, bool TB>
+__device__ __forceinline__ void slot_update(double (&acc)[B * B / T], const Slots<B, T> &s,
+                                            const double *A, const double *Bm, int kk)
+{
+    constexpr int LD = Tile<B>::LD;
+    constexpr int E = B * B / T;
+#pragma unroll 2
+    for (int k = 0; k < kk; ++k) {
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            if (s.ok(r)) {
+                const double a = TA ? A[k + s.row[r] * LD] : A[s.row[r] + k * LD];
+                const double b = TB ? Bm[s.col[r] + k * LD] : Bm[k + s.col[r] * LD];
+                acc[r] = fma(-a, b, acc[r]);
+            }
+        }
+    }
+}
+
+// True if any lane of this warp handles one of the first `cnt` work items
+// when items are spread `split` lanes apiece (warp-uniform).
+__device__ __forceinline__ bool warp_has_work(int cnt, int split)
+{
+    const int first = (threadIdx.x & ~31) / split;
+    return first < cnt;
+}
+
+}  // namespace ss

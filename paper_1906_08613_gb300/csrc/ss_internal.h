@@ -1,0 +1,88 @@
+// Internal interfaces between the C-ABI layer (api.cu) and the kernel
+// translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "../../include/smallsolve.h"
+
+namespace ss {
+
+// Operands of one batched call, exactly as the caller passed them.
+struct Operands {
+    const int *n;
+    const double *const *A;   // potrf: A; trsyl/trlyap: L
+    const int *lda;
+    const double *const *U;   // trsyl: U
+    const int *ldu;
+    const double *const *C;   // trsyl: C; trlyap: S
+    const int *ldc;
+    double *const *X;
+    const int *ldx;
+    int *info;
+};
+
+// Device-side workspace produced by the binning pre-pass.
+//   meta[META_COUNT]          number of instances with a valid size
+//   meta[META_BIN_LO + k]     first position (in perm) of size bin k
+//   meta[META_BIN_HI + k]     one past the last position of size bin k
+//   meta[META_HEAD + g]       work-queue head of launch group g
+//   perm[w]                   instance index at position w (sizes descending)
+//   scr[w]                    element offset of position w's scratch area
+constexpr int META_COUNT = 0;
+constexpr int META_BIN_LO = 16;
+constexpr int META_BIN_HI = 32;
+constexpr int META_HEAD = 48;
+constexpr int META_RANGE = 64;     // pairs (lo, hi) per launch group, 2 * MAX_GROUPS
+constexpr int MAX_GROUPS = 16;
+constexpr int META_INTS = 128;
+constexpr int NUM_BINS = 13;       // bin(n) = ceil(log2(max(n,1))), n <= 4096
+
+struct Sched {
+    int *meta;
+    const int *perm;
+    const long long *scr;      // scratch offsets (elements), may be null
+    void *scratch;             // scratch base, may be null
+    long long scratch_elems;   // capacity in elements of the scratch element type
+};
+
+// A launch over the positions [meta[META_RANGE+2g], meta[META_RANGE+2g+1]).
+struct Launch {
+    int group;
+    int cfg;                   // index into the op's configuration table
+    int mode;
+    int max_n;
+    int batch;
+};
+
+size_t workspace_bytes(int op, int batch, int max_n, int mode);
+void carve_workspace(void *d_work, int batch, int max_n, int mode, Sched *s);
+
+// Binning pre-pass: sorts valid instances by size (descending), fills bins,
+// scratch offsets and the launch-group ranges, resets the queue heads.
+// group_of_bin[k] is the launch group of size bin k (-1: none, only for bins
+// that cannot hold instances); ngroups groups are used.
+cudaError_t launch_binning(int batch, int max_n, const int *d_n, int *d_info, const Sched &s,
+                           const int *group_of_bin, int ngroups, long long scratch_per_n2,
+                           cudaStream_t st);
+
+// Configuration tables.
+struct Config {
+    int block;
+    int threads;
+    int variant;
+};
+int config_count(int op, int mode);
+const Config *config_get(int op, int mode, int cfg);
+int config_default(int op, int mode, int max_n);
+
+// Kernel launchers (one per op).  Return cudaSuccess or the launch error.
+cudaError_t launch_potrf(const Operands &o, const Sched &s, const Launch &l, cudaStream_t st);
+cudaError_t launch_trsyl(const Operands &o, const Sched &s, const Launch &l, cudaStream_t st);
+cudaError_t launch_trlyap(const Operands &o, const Sched &s, const Launch &l, cudaStream_t st);
+
+// Number of SMs of the current device (cached per device).
+int sm_count();
+
+}  // namespace ss

@@ -1,0 +1,76 @@
+"""Device-memory plumbing for packed batches (allocation and pointer arrays).
+
+PyTorch provides device memory and streams only; the solves themselves go
+through the C ABI (``smallsolve``).  A ``DeviceBatch`` uploads a packed batch
+(see ``inputs.Packed``), builds the per-instance pointer and size arrays the
+entry points take, allocates X, info and the workspace, and calls the entry
+point for its operation.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import smallsolve as ss
+
+OPERANDS = {"potrf": ("A",), "trsyl": ("L", "U", "C"), "trlyap": ("L", "S")}
+
+
+class DeviceBatch:
+    def __init__(self, n, off, ops: dict, op: str, device="cuda", alias_rhs: bool = False,
+                 x_fill: float = 0.0, max_n: int | None = None):
+        self.op = op
+        self.device = torch.device(device)
+        n = np.ascontiguousarray(n, dtype=np.int32)
+        off = np.ascontiguousarray(off, dtype=np.int64)
+        self.batch = int(n.shape[0])
+        self.max_n = int(n.max()) if (max_n is None and self.batch) else int(max_n or 0)
+        self.n_host = n
+        self.off_host = off
+        self.d_n = torch.from_numpy(n).to(self.device)
+        self.d_ld = torch.from_numpy(np.maximum(n, 1).astype(np.int32)).to(self.device)
+        self.bufs = {k: torch.from_numpy(np.ascontiguousarray(ops[k])).to(self.device)
+                     for k in OPERANDS[op]}
+        rhs = {"potrf": "A", "trsyl": "C", "trlyap": "S"}[op]
+        total = int(next(iter(ops.values())).shape[0])
+        if alias_rhs:
+            self.X = self.bufs[rhs]
+        else:
+            self.X = torch.full((total,), x_fill, dtype=torch.float64, device=self.device)
+        offb = torch.from_numpy(off * 8).to(self.device)
+        self.ptrs = {k: (v.data_ptr() + offb).contiguous() for k, v in self.bufs.items()}
+        self.ptrs["X"] = (self.X.data_ptr() + offb).contiguous()
+        self.info = torch.full((max(self.batch, 1),), 12345, dtype=torch.int32, device=self.device)
+        self.work = None
+        self.work_bytes = 0
+
+    def ensure_work(self, mode: int) -> None:
+        need = ss.ss_workspace_size(ss.OPS[self.op], self.batch, self.max_n, mode)
+        if self.work is None or self.work_bytes < need:
+            self.work = torch.empty(max(need, 256), dtype=torch.uint8, device=self.device)
+            self.work_bytes = int(self.work.numel())
+
+    def solve(self, mode: int = ss.MODE_FP64, cfg: int = ss.CFG_DEFAULT, stream: int = 0,
+              check: bool = True) -> int:
+        self.ensure_work(mode)
+        p = self.ptrs
+        ld = self.d_ld.data_ptr()
+        w = self.work.data_ptr()
+        common = dict(mode=mode, cfg=cfg, d_work=w, work_bytes=self.work_bytes, stream=stream,
+                      check=check)
+        if self.op == "potrf":
+            return ss.potrf_upper(self.batch, self.max_n, self.d_n.data_ptr(), p["A"].data_ptr(), ld,
+                                  p["X"].data_ptr(), ld, self.info.data_ptr(), **common)
+        if self.op == "trsyl":
+            return ss.trsyl_lu(self.batch, self.max_n, self.d_n.data_ptr(), p["L"].data_ptr(), ld,
+                               p["U"].data_ptr(), ld, p["C"].data_ptr(), ld, p["X"].data_ptr(), ld,
+                               self.info.data_ptr(), **common)
+        return ss.trlyap_l(self.batch, self.max_n, self.d_n.data_ptr(), p["L"].data_ptr(), ld,
+                           p["S"].data_ptr(), ld, p["X"].data_ptr(), ld, self.info.data_ptr(),
+                           **common)
+
+    def x_host(self) -> np.ndarray:
+        return self.X.cpu().numpy()
+
+    def info_host(self) -> np.ndarray:
+        return self.info[: self.batch].cpu().numpy()

@@ -1,0 +1,143 @@
+"""Python binding of the C ABI in include/smallsolve.h (ctypes, marshalling only).
+
+Every function here converts its arguments and calls the entry point of the
+same name in libsmallsolve.so; all arithmetic runs in the library's CUDA
+kernels.  The library must have been built (``__graft_entry__.build()`` or
+``python -m paper_1906_08613_gb300.build``); if it is missing, loading fails
+with an error rather than falling back to anything else.
+
+Device pointers are passed as Python ints (e.g. ``tensor.data_ptr()``) and
+streams as the integer handle of a ``cudaStream_t`` (``torch.cuda.Stream
+.cuda_stream``; 0 is the legacy default stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libsmallsolve.so")
+
+OP_POTRF, OP_TRSYL, OP_TRLYAP = 0, 1, 2
+OPS = {"potrf": OP_POTRF, "trsyl": OP_TRSYL, "trlyap": OP_TRLYAP}
+
+MODE_FP64 = 0
+MODE_FP32_REFINED = 1
+MODE_TF32_REFINED = 2
+MODE_BF16_REFINED = 3
+MODE_FP32_RAW = 4
+MODE_TF32_RAW = 5
+MODE_BF16_RAW = 6
+MODES = {"fp64": 0, "fp32_refined": 1, "tf32_refined": 2, "bf16_refined": 3,
+         "fp32_raw": 4, "tf32_raw": 5, "bf16_raw": 6}
+
+CFG_DEFAULT = -1
+CFG_TABLE = -2
+
+ERR_CUDA = -100
+INFO_BAD_SIZE = -1
+INFO_NO_WORK = -2
+MAX_N = 4096
+NUM_BINS = 13
+REFINE_TOL = 1e-13
+REFINE_MAXIT = 10
+
+_lock = threading.Lock()
+_lib = None
+
+
+class SmallSolveError(RuntimeError):
+    pass
+
+
+def lib():
+    """Load libsmallsolve.so (once)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise SmallSolveError(
+                    f"{LIB_PATH} is missing: build the CUDA library first "
+                    "(python -c 'import __graft_entry__ as g; g.build()')")
+            L = ctypes.CDLL(LIB_PATH)
+            i, vp, sz = ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t
+            L.potrf_upper.argtypes = [i, i, vp, vp, vp, vp, vp, vp, i, i, vp, sz, vp]
+            L.trsyl_lu.argtypes = [i, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i, i, vp, sz, vp]
+            L.trlyap_l.argtypes = [i, i, vp, vp, vp, vp, vp, vp, vp, vp, i, i, vp, sz, vp]
+            for f in (L.potrf_upper, L.trsyl_lu, L.trlyap_l):
+                f.restype = i
+            L.ss_workspace_size.argtypes = [i, i, i, i, ctypes.POINTER(sz)]
+            L.ss_workspace_size.restype = i
+            L.ss_config_count.argtypes = [i, i]
+            L.ss_config_count.restype = i
+            ip = ctypes.POINTER(i)
+            L.ss_config_describe.argtypes = [i, i, i, ip, ip, ip]
+            L.ss_config_describe.restype = i
+            L.ss_set_config_table.argtypes = [i, i, i, ip]
+            L.ss_set_config_table.restype = i
+            L.ss_version.argtypes = []
+            L.ss_version.restype = i
+            _lib = L
+    return _lib
+
+
+def _check(rc: int, name: str) -> int:
+    if rc != 0:
+        raise SmallSolveError(f"{name} returned {rc}")
+    return rc
+
+
+def potrf_upper(batch, max_n, d_n, d_A, d_lda, d_X, d_ldx, d_info, mode=MODE_FP64,
+                cfg=CFG_DEFAULT, d_work=0, work_bytes=0, stream=0, check=True):
+    rc = lib().potrf_upper(batch, max_n, d_n, d_A, d_lda, d_X, d_ldx, d_info, mode, cfg,
+                           d_work or None, work_bytes, stream or None)
+    return _check(rc, "potrf_upper") if check else rc
+
+
+def trsyl_lu(batch, max_n, d_n, d_L, d_ldl, d_U, d_ldu, d_C, d_ldc, d_X, d_ldx, d_info,
+             mode=MODE_FP64, cfg=CFG_DEFAULT, d_work=0, work_bytes=0, stream=0, check=True):
+    rc = lib().trsyl_lu(batch, max_n, d_n, d_L, d_ldl, d_U, d_ldu, d_C, d_ldc, d_X, d_ldx,
+                        d_info, mode, cfg, d_work or None, work_bytes, stream or None)
+    return _check(rc, "trsyl_lu") if check else rc
+
+
+def trlyap_l(batch, max_n, d_n, d_L, d_ldl, d_S, d_lds, d_X, d_ldx, d_info, mode=MODE_FP64,
+             cfg=CFG_DEFAULT, d_work=0, work_bytes=0, stream=0, check=True):
+    rc = lib().trlyap_l(batch, max_n, d_n, d_L, d_ldl, d_S, d_lds, d_X, d_ldx, d_info, mode,
+                        cfg, d_work or None, work_bytes, stream or None)
+    return _check(rc, "trlyap_l") if check else rc
+
+
+def ss_workspace_size(op, batch, max_n, mode) -> int:
+    out = ctypes.c_size_t(0)
+    _check(lib().ss_workspace_size(op, batch, max_n, mode, ctypes.byref(out)), "ss_workspace_size")
+    return int(out.value)
+
+
+def ss_config_count(op, mode) -> int:
+    return int(lib().ss_config_count(op, mode))
+
+
+def ss_config_describe(op, mode, cfg):
+    b, t, v = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().ss_config_describe(op, mode, cfg, ctypes.byref(b), ctypes.byref(t),
+                                    ctypes.byref(v)), "ss_config_describe")
+    return int(b.value), int(t.value), int(v.value)
+
+
+def ss_set_config_table(op, mode, cfg_by_bin) -> None:
+    arr = (ctypes.c_int * max(1, len(cfg_by_bin)))(*[int(c) for c in cfg_by_bin])
+    _check(lib().ss_set_config_table(op, mode, len(cfg_by_bin), arr), "ss_set_config_table")
+
+
+def ss_version() -> int:
+    return int(lib().ss_version())
+
+
+def size_bin(n: int) -> int:
+    """bin(n) = ceil(log2(max(n, 1))), the index of the per-size config table."""
+    k = 0
+    while (1 << k) < n:
+        k += 1
+    return k

@@ -1,0 +1,72 @@
+"""The C-ABI library loads and exports every entry point that
+include/smallsolve.h declares; host-side argument checks and configuration
+queries work without a GPU (no kernel is launched here)."""
+import os
+import re
+
+import pytest
+
+from paper_1906_08613_gb300 import build as libbuild
+from paper_1906_08613_gb300 import smallsolve as ss
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                      "smallsolve.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:int|size_t|void)\s*\*?\s*(\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    libbuild.build()
+    return ss.lib()
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for required in ("potrf_upper", "trsyl_lu", "trlyap_l", "ss_workspace_size"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), f"{name} declared in smallsolve.h but not exported"
+
+
+def test_host_side_queries(lib):
+    assert ss.ss_version() >= 1
+    for op in (ss.OP_POTRF, ss.OP_TRSYL, ss.OP_TRLYAP):
+        cnt = ss.ss_config_count(op, ss.MODE_FP64)
+        assert cnt >= 1
+        for c in range(cnt):
+            b, t, v = ss.ss_config_describe(op, ss.MODE_FP64, c)
+            assert b in (8, 16, 32, 64) and t % 32 == 0 and t >= b
+        assert ss.ss_workspace_size(op, 1000, 128, ss.MODE_FP64) >= 4 * 1000
+    assert lib.ss_config_count(7, 0) < 0
+    assert lib.ss_workspace_size(0, -1, 4, 0, None) < 0
+
+
+def test_argument_errors_before_launch(lib):
+    # Each returns before any CUDA call: negative batch, size bound, null
+    # pointer arrays, invalid mode / cfg, missing or short workspace.
+    assert ss.potrf_upper(-1, 4, 1, 1, 1, 1, 1, 1, check=False) == -1
+    assert ss.potrf_upper(1, ss.MAX_N + 1, 1, 1, 1, 1, 1, 1, check=False) == -2
+    assert ss.potrf_upper(1, 4, 0, 1, 1, 1, 1, 1, check=False) == -3
+    assert ss.trsyl_lu(1, 4, 1, 1, 1, 1, 1, 0, 1, 1, 1, 1, check=False) == -8
+    assert ss.trlyap_l(1, 4, 1, 1, 1, 1, 1, 1, 1, 0, check=False) == -10
+    assert ss.potrf_upper(1, 4, 1, 1, 1, 1, 1, 1, mode=99, check=False) == -9
+    assert ss.potrf_upper(1, 4, 1, 1, 1, 1, 1, 1, cfg=999, check=False) == -10
+    assert ss.potrf_upper(1, 4, 1, 1, 1, 1, 1, 1, d_work=0, check=False) == -11
+    assert ss.potrf_upper(1, 4, 1, 1, 1, 1, 1, 1, d_work=1, work_bytes=1, check=False) == -12
+    assert ss.trsyl_lu(0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0) == 0
+
+
+def test_config_table_validation(lib):
+    with pytest.raises(ss.SmallSolveError):
+        ss.ss_set_config_table(ss.OP_TRSYL, ss.MODE_FP64, [999])
+    ss.ss_set_config_table(ss.OP_TRSYL, ss.MODE_FP64, [0, 1, -1])
+    ss.ss_set_config_table(ss.OP_TRSYL, ss.MODE_FP64, [])
