@@ -1,0 +1,409 @@
+"""Benchmark: batched small structured solves on GB300 (one JSON line).
+
+Default workload: triangular Sylvester L X + X U = C, 4096 instances with
+order n uniform in {4..128} (FP64 inputs and output), solved by the library's
+C ABI (``trsyl_lu``) in one persistent launch per configuration group.  A step
+is one batched solve of the whole workload.  Inputs are seeded synthetic data
+(see paper_1906_08613_gb300/inputs.py); the operand buffers are larger than
+the 129 MB L2, so no flush is needed between steps.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+        [--workload NAME] [--mode fp64|fp32_refined|...] [--cfg C]
+For N > 1 launch with torch.distributed.run; each rank solves its own copy of
+the workload (independent replicas, weak scaling, no collective on the data
+path).  ``--impl reference`` times the CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "batched solves/s and % roofline, mixed+learned vs plain FP64 GPU at 1e-11 error"
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07   # SMs x DFMA/clk/SM x flop/FMA x GHz = 1258.6
+GATE = 1e-11
+
+
+def flops_paper(op, n):
+    """The paper's flop counts (Fig. 2 caption): n^3/3 for Cholesky, 2 n^3
+    for Sylvester and Lyapunov."""
+    n = np.asarray(n, dtype=np.float64)
+    return float((n ** 3 / 3).sum()) if op == "potrf" else float((2 * n ** 3).sum())
+
+
+def flops_algorithmic(op, n):
+    """Multiply-add count x 2 of the solve as computed (Lyapunov exploits the
+    symmetry of X: n^3)."""
+    n = np.asarray(n, dtype=np.float64)
+    if op == "potrf":
+        return float((n ** 3 / 3).sum())
+    if op == "trsyl":
+        return float((2 * n ** 3).sum())
+    return float((n ** 3).sum())
+
+
+def bytes_algorithmic(op, n):
+    """Stored triangles / full operands read once and X written once, FP64."""
+    n = np.asarray(n, dtype=np.float64)
+    tri = n * (n + 1) / 2
+    if op == "potrf":
+        return float((8 * (tri + tri)).sum())
+    if op == "trsyl":
+        return float((8 * (tri + tri + n * n + n * n)).sum())
+    return float((8 * (tri + tri + tri)).sum())
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        import tempfile
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        dist.init_process_group(backend=backend)
+        return dist, rank, world, local
+    return None, rank, world, local
+
+
+def barrier(dist, dev):
+    import torch
+    if dist is not None:
+        dist.barrier(device_ids=[dev.index])
+    torch.cuda.synchronize(dev)
+
+
+def max_over_ranks(dist, value, dev):
+    import torch
+    if dist is None:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, value, dev):
+    import torch
+    if dist is None:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def read_traffic(kernel_prefix, workload):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, if it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    from paper_1906_08613_gb300 import build as b
+    ent = d.get(f"{workload}:{kernel_prefix}")
+    if not ent or ent.get("sources_sha") != b.sources_sha():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def cpu_oracle_rate(op, pk, seconds: float, threads: int, indices=None):
+    """Time the oracle on host threads over (a sample of) the batch, repeating
+    passes until `seconds` elapsed; returns (solves/s, solves, elapsed, out)."""
+    import oracle
+    ops = {k: v for k, v in pk.ops.items() if k != "X0"}
+    idx = np.arange(pk.batch) if indices is None else np.asarray(indices)
+    done = 0
+    out = None
+    t0 = time.perf_counter()
+    while True:
+        out, _ = oracle.solve_packed_parallel(op, pk.n, pk.off, ops, threads=threads, indices=idx)
+        done += len(idx)
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return done / el, done, el, out
+
+
+def sample_indices(pk, k, seed=7):
+    rng = np.random.default_rng(seed)
+    k = min(k, pk.batch)
+    return np.sort(rng.choice(pk.batch, size=k, replace=False))
+
+
+def run_reference(args):
+    """The oracle arm: one step = the oracle over a bounded sample of the
+    workload on all host cores."""
+    dist, rank, world, _ = (None, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), 0)
+    if rank != 0:
+        return 0
+    from paper_1906_08613_gb300 import inputs
+    import oracle
+    name = args.workload
+    op = inputs.WORKLOADS[name]["op"]
+    pk = inputs.make_workload(name, seed=args.seed)
+    threads = os.cpu_count() or 1
+    per_step = max(8, min(pk.batch, int(args.ref_sample)))
+    ops = {k: v for k, v in pk.ops.items() if k != "X0"}
+    for w in range(args.warmup):
+        oracle.solve_packed_parallel(op, pk.n, pk.off, ops, threads=threads,
+                                     indices=sample_indices(pk, per_step, seed=1000 + w))
+    times = []
+    solves = 0
+    for s in range(args.steps):
+        idx = sample_indices(pk, per_step, seed=s)
+        t0 = time.perf_counter()
+        oracle.solve_packed_parallel(op, pk.n, pk.off, ops, threads=threads, indices=idx)
+        times.append(time.perf_counter() - t0)
+        solves += len(idx)
+    total = sum(times)
+    value = solves / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": name, "op": op, "batch_per_step": per_step,
+                   "sizes": "sampled from the workload's size distribution"},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{per_step} seeded random instances of {name} per step"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="graft", choices=["graft", "reference"])
+    ap.add_argument("--workload", default="trsyl_4096xU4-128")
+    ap.add_argument("--mode", default="fp64")
+    ap.add_argument("--cfg", type=int, default=None)
+    ap.add_argument("--seed", type=int, default=1234)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-sample", type=int, default=256)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_1906_08613_gb300 import inputs, smallsolve as ss
+    from paper_1906_08613_gb300.device import DeviceBatch
+
+    dist, rank, world, local = dist_init()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    sh = stream.cuda_stream
+
+    name = args.workload
+    op = inputs.WORKLOADS[name]["op"]
+    pk = inputs.make_workload(name, seed=args.seed)
+    mode = ss.MODES[args.mode]
+    cfg = ss.CFG_DEFAULT if args.cfg is None else args.cfg
+
+    db = DeviceBatch(pk.n, pk.off, pk.ops, op, device=dev)
+    db.ensure_work(mode)
+    F = flops_paper(op, pk.n)
+    Falg = flops_algorithmic(op, pk.n)
+    Balg = bytes_algorithmic(op, pk.n)
+
+    def step():
+        db.solve(mode=mode, cfg=cfg, stream=sh)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    barrier(dist, dev)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ss.ss_profile_enable(True)
+    ss.ss_profile_read()
+    l0 = ss.ss_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier(dist, dev)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+    stream.synchronize()
+    barrier(dist, dev)
+    launches = ss.ss_launch_count() - l0
+    kern_ms, kern_calls = ss.ss_profile_read()
+    ss.ss_profile_enable(False)
+    clk = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    ms_total = max_over_ranks(dist, ms_total, dev)
+    ms_step = ms_total / args.steps
+    solves = sum_over_ranks(dist, float(pk.batch * args.steps), dev)
+    value = solves / (ms_total * 1e-3)
+    kern_avg_ms = kern_ms / max(kern_calls, 1)
+    info = db.info_host()
+
+    # End to end through the C ABI with host buffers: H2D of the inputs from
+    # pinned memory, the solve, D2H of X, every step.
+    names = [k for k in ("A", "L", "U", "C", "S") if k in db.bufs]
+    host_in = {k: torch.from_numpy(pk.ops[k]).pin_memory() for k in names}
+    host_x = torch.empty_like(db.X, device="cpu").pin_memory()
+    h2d = sum(int(host_in[k].numel()) * 8 for k in names)
+    d2h = int(host_x.numel()) * 8
+    e2e_steps = max(3, min(args.steps, 50))
+
+    def e2e_step():
+        for k in names:
+            db.bufs[k].copy_(host_in[k], non_blocking=True)
+        step()
+        host_x.copy_(db.X, non_blocking=True)
+
+    with torch.cuda.stream(stream):
+        e2e_step()
+        barrier(dist, dev)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(e2e_steps):
+            e2e_step()
+        f1.record(stream)
+    stream.synchronize()
+    e2e_ms = max_over_ranks(dist, f0.elapsed_time(f1), dev)
+    e2e_value = sum_over_ranks(dist, float(pk.batch * e2e_steps), dev) / (e2e_ms * 1e-3)
+    x_gpu = host_x.numpy()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    achieved = Falg / (kern_avg_ms * 1e-3) / 1e9
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+            "frac": achieved / FP64_PEAK_GFLOPS,
+            "traffic": read_traffic(f"{op}_{args.mode}", name),
+            "kernel": f"{op} persistent solve kernel ({args.mode})",
+            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (of derived; "
+                           "a DFMA probe measured 1248 GFLOP/s)",
+            "kernel_ms": kern_avg_ms, "algorithmic_bytes": Balg,
+            "hbm_frac": Balg / (kern_avg_ms * 1e-3) / 6801.3e9}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": name, "op": op, "batch": pk.batch,
+                   "sizes": f"n in [{int(pk.n.min())}, {int(pk.n.max())}], mean {float(pk.n.mean()):.1f}",
+                   "mode": args.mode, "cfg": cfg,
+                   "l2": f"operands {sum(int(v.numel()) * 8 for v in db.bufs.values()) / 1e6:.0f} MB > 129 MB L2; no flush"},
+        "gflops_paper_count": F / (ms_step * 1e-3) / 1e9,
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "launches_per_step": launches / args.steps,
+        "clocks": clk,
+        "info_nonzero": int((info != 0).sum()),
+    }
+
+    if not args.no_cpu:
+        threads = os.cpu_count() or 1
+        idx = sample_indices(pk, max(16, pk.batch // 8))
+        rate, done, el, out = cpu_oracle_rate(op, pk, args.cpu_seconds, threads, indices=idx)
+        # Accuracy of the GPU result on the oracle's sample.
+        errs = []
+        for b in idx:
+            nb, o = int(pk.n[b]), int(pk.off[b])
+            g = x_gpu[o:o + nb * nb].reshape(nb, nb, order="F")
+            r = out[o:o + nb * nb].reshape(nb, nb, order="F")
+            if op == "potrf":
+                g, r = np.triu(g), np.triu(r)
+            elif op == "trlyap":
+                g, r = np.tril(g), np.tril(r)
+            errs.append(np.linalg.norm(g - r) / np.linalg.norm(r))
+        line["cpu_baseline"] = {"value": rate, "unit": "solves/s", "cores": threads, "kind": "oracle",
+                                "sample": f"{len(idx)} seeded random instances of {name}, "
+                                          f"repeated for {el:.1f} s ({done} solves)"}
+        line["accuracy"] = {"max_rel_fro_err_vs_oracle": float(max(errs)), "gate": GATE,
+                            "instances_checked": len(idx), "pass": bool(max(errs) <= GATE)}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -157,8 +157,24 @@ int ss_config_describe(int op, int mode, int cfg, int *block, int *threads, int 
  */
 int ss_set_config_table(int op, int mode, int nbins, const int *cfg_by_bin);
 
-/* Library version and the number of the CUDA device the calls run on. */
+/* Library version. */
 int ss_version(void);
+
+/*
+ * Instrumentation for benchmarks (no counterpart in the paper).
+ * ss_launch_count: number of kernels this library has launched in this
+ * process so far (all entry points, all devices).
+ * ss_profile_enable(1): from now on, every solve call also records a CUDA
+ * event pair on its stream around its solve kernels (after the binning
+ * pre-pass, after the last solve launch).  ss_profile_read waits for the
+ * recorded pairs, returns their total elapsed milliseconds and count, and
+ * forgets them.  ss_profile_enable(0) stops recording.  Events are created on
+ * first use and reused; this is host-side state, not thread-safe with
+ * concurrent calls.  Returns 0 or a negative error.
+ */
+long long ss_launch_count(void);
+int ss_profile_enable(int on);
+int ss_profile_read(double *total_ms, int *calls);
 
 #ifdef __cplusplus
 }

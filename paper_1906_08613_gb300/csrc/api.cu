@@ -3,7 +3,9 @@
 // (binning pre-pass, then one persistent solve launch per launch group).
 #include <string.h>
 
+#include <atomic>
 #include <mutex>
+#include <vector>
 
 #include "ss_internal.h"
 
@@ -43,6 +45,39 @@ TableState &tables()
 }
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+std::atomic<long long> g_launches{0};
+
+struct Profile {
+    std::mutex mu;
+    bool on = false;
+    std::vector<cudaEvent_t> pool;   // pairs: 2*i start, 2*i+1 stop
+    int used = 0;                    // pairs recorded since the last read
+};
+Profile &profile()
+{
+    static Profile p;
+    return p;
+}
+
+// Returns the event pair for this call, or false when profiling is off.
+bool profile_pair(cudaEvent_t *a, cudaEvent_t *b)
+{
+    Profile &p = profile();
+    std::lock_guard<std::mutex> g(p.mu);
+    if (!p.on) return false;
+    if ((int)p.pool.size() < 2 * (p.used + 1)) {
+        cudaEvent_t e0, e1;
+        if (cudaEventCreate(&e0) != cudaSuccess) return false;
+        if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return false; }
+        p.pool.push_back(e0);
+        p.pool.push_back(e1);
+    }
+    *a = p.pool[2 * p.used];
+    *b = p.pool[2 * p.used + 1];
+    ++p.used;
+    return true;
+}
 
 }  // namespace
 
@@ -178,6 +213,10 @@ int run(int op, int batch, int max_n, const Operands &o, int mode, int cfg, void
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = launch_binning(batch, max_n, o.n, o.info, s, group_of_bin, ngroups, per, st);
     if (e != cudaSuccess) return SS_ERR_CUDA;
+    g_launches.fetch_add(1 + ngroups, std::memory_order_relaxed);
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    const bool prof = profile_pair(&ev0, &ev1);
+    if (prof) cudaEventRecord(ev0, st);
     for (int g = 0; g < ngroups; ++g) {
         Launch l{g, group_cfg[g], mode, max_n, batch};
         if (mode == SS_MODE_FP64) {
@@ -188,10 +227,9 @@ int run(int op, int batch, int max_n, const Operands &o, int mode, int cfg, void
         }
         if (e != cudaSuccess) return SS_ERR_CUDA;
     }
+    if (prof) cudaEventRecord(ev1, st);
     return 0;
 }
-
-bool bad_common(int batch, int max_n) { return batch < 0 || max_n < 0 || max_n > SS_MAX_N; }
 
 }  // namespace
 
@@ -303,5 +341,34 @@ int ss_set_config_table(int op, int mode, int nbins, const int *cfg_by_bin)
 }
 
 int ss_version(void) { return 1; }
+
+long long ss_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int ss_profile_enable(int on)
+{
+    Profile &p = profile();
+    std::lock_guard<std::mutex> g(p.mu);
+    p.on = on != 0;
+    return 0;
+}
+
+int ss_profile_read(double *total_ms, int *calls)
+{
+    if (!total_ms) return -1;
+    if (!calls) return -2;
+    Profile &p = profile();
+    std::lock_guard<std::mutex> g(p.mu);
+    double t = 0.0;
+    for (int i = 0; i < p.used; ++i) {
+        if (cudaEventSynchronize(p.pool[2 * i + 1]) != cudaSuccess) return SS_ERR_CUDA;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.pool[2 * i], p.pool[2 * i + 1]) != cudaSuccess) return SS_ERR_CUDA;
+        t += ms;
+    }
+    *total_ms = t;
+    *calls = p.used;
+    p.used = 0;
+    return 0;
+}
 
 }  // extern "C"

@@ -1,0 +1,66 @@
+// Configuration tables and dispatch of the mixed-precision modes.
+#include "ss_internal.h"
+
+namespace ss {
+
+cudaError_t launch_mixed_trsyl(int prec, int cfg, const Operands &o, const Sched &s, const Launch &l,
+                               cudaStream_t st, int raw);
+cudaError_t launch_mixed_trlyap(int prec, int cfg, const Operands &o, const Sched &s, const Launch &l,
+                                cudaStream_t st, int raw);
+
+namespace {
+
+// variant: bit 0 = residual (0 double-float on the FP32 pipe, 1 FP64 FMA);
+// bit 1 = solve (0 blocked lazy, block size `block`; 1 shared-memory-resident
+// eager wavefront for n <= block, blocked with B = 32 above).
+const Config kFp32Cfg[] = {{16, 64, 0},  {16, 128, 0},  {32, 128, 0},  {16, 128, 1},
+                           {32, 128, 1}, {128, 1024, 2}, {64, 512, 2}, {128, 1024, 3}};
+const Config kTcCfg[] = {{16, 64, 0}, {32, 128, 0}, {16, 64, 1}, {32, 128, 1}};
+
+// Low-precision arithmetic of a mode: 0 FP32, 1 TF32, 2 BF16; -1 not mixed.
+int mode_prec(int mode)
+{
+    switch (mode) {
+    case SS_MODE_FP32_REFINED: case SS_MODE_FP32_RAW: return 0;
+    case SS_MODE_TF32_REFINED: case SS_MODE_TF32_RAW: return 1;
+    case SS_MODE_BF16_REFINED: case SS_MODE_BF16_RAW: return 2;
+    }
+    return -1;
+}
+bool mode_raw(int mode)
+{
+    return mode == SS_MODE_FP32_RAW || mode == SS_MODE_TF32_RAW || mode == SS_MODE_BF16_RAW;
+}
+
+}  // namespace
+
+int mixed_config_count(int op, int mode)
+{
+    const int p = mode_prec(mode);
+    if (p < 0 || op == SS_OP_POTRF) return 0;
+    return p == 0 ? (int)(sizeof(kFp32Cfg) / sizeof(Config)) : (int)(sizeof(kTcCfg) / sizeof(Config));
+}
+
+const Config *mixed_config_get(int op, int mode, int cfg)
+{
+    if (cfg < 0 || cfg >= mixed_config_count(op, mode)) return nullptr;
+    return mode_prec(mode) == 0 ? &kFp32Cfg[cfg] : &kTcCfg[cfg];
+}
+
+// Scratch per instance in floats per n^2: the right-hand side / correction
+// and the reciprocal divisors.
+long long mixed_scratch_per_n2(int op, int mode)
+{
+    return mixed_config_count(op, mode) > 0 ? 2 : 0;
+}
+
+cudaError_t launch_mixed(int op, const Operands &o, const Sched &s, const Launch &l, cudaStream_t st)
+{
+    const int p = mode_prec(l.mode);
+    const int raw = mode_raw(l.mode) ? 1 : 0;
+    if (op == SS_OP_TRSYL) return launch_mixed_trsyl(p, l.cfg, o, s, l, st, raw);
+    if (op == SS_OP_TRLYAP) return launch_mixed_trlyap(p, l.cfg, o, s, l, st, raw);
+    return cudaErrorNotSupported;
+}
+
+}  // namespace ss

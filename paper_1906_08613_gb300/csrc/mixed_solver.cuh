@@ -1,0 +1,498 @@
+// Mixed-precision Sylvester / Lyapunov instance driver and persistent kernel
+// (see mixed.cuh for the method).  Included by mixed_syl.cu (Sylvester) and
+// mixed_lyap.cu (Lyapunov), one translation unit each.
+#pragma once
+
+#include "mixed.cuh"
+
+namespace ss {
+namespace mx {
+
+// Tensor-core fragments per warp (1 for the FP32 path, which uses none).
+template <int B, int T, int P>
+struct FragN { static constexpr int value = MmaShape<B, T>::TPW; };
+template <int B, int T>
+struct FragN<B, T, P_FP32> { static constexpr int value = 1; };
+
+template <int B>
+constexpr size_t mixed_smem_bytes()
+{
+    // Five float tiles for the solve; the residual reuses the same memory as
+    // two 8-byte tiles (float2 or double); plus a reduction buffer.
+    return (size_t)5 * FTile<B>::SZ * sizeof(float) + 64 * sizeof(float);
+}
+
+// Low-precision solve of L D + D U = RHS into W (FP32, ld n), in place when
+// the right-hand side is W itself (SRC_D = false) or from the FP64 C.
+template <int B, int T, bool LYAP, int P, bool SRC_D>
+__device__ void low_solve(int n, const double *L, long ldl, const double *U, long ldu,
+                          const double *Cd, long ldc, float *W, const float *Rinv, float *sm)
+{
+    constexpr int LD = FTile<B>::LD, SZ = FTile<B>::SZ, E = B * B / T;
+    float *sA = sm, *sB = sm + SZ, *sT = sm + 2 * SZ, *sL = sm + 3 * SZ, *sU = sm + 4 * SZ;
+    const int nb = (n + B - 1) / B;
+    const long ldw = n;
+    Slots<B, T> sl;
+    for (int I = 0; I < nb; ++I) {
+        const int mI = min(B, n - I * B), i0 = I * B;
+        __syncthreads();
+        stage_f<B, T, F_LOWER>(sL, L + i0 + (long)i0 * ldl, ldl, mI, mI);
+        const int jend = LYAP ? I + 1 : nb;
+        for (int J = 0; J < jend; ++J) {
+            const int nJ = min(B, n - J * B), j0 = J * B;
+            __syncthreads();
+            if (SRC_D) {
+                if (LYAP && I == J) stage_f<B, T, F_SYM_LOWER>(sT, Cd + i0 + (long)j0 * ldc, ldc, mI, nJ);
+                else stage_f<B, T, F_FULL>(sT, Cd + i0 + (long)j0 * ldc, ldc, mI, nJ);
+            } else {
+                stage_f<B, T, F_FULL>(sT, W + i0 + (long)j0 * ldw, ldw, mI, nJ);
+            }
+            __syncthreads();
+            float acc[E];
+            float frag[FragN<B, T, P>::value][4];
+            if constexpr (P == P_FP32) {
+                sl.set(Shape::Full, mI, nJ);
+#pragma unroll
+                for (int r = 0; r < E; ++r) acc[r] = sl.ok(r) ? sT[sl.row[r] + sl.col[r] * LD] : 0.0f;
+            } else {
+                frag_load<B, T>(frag, sT);
+            }
+            auto update = [&](bool tb) {
+                if constexpr (P == P_FP32) {
+                    if (tb) slot_update_f<B, T, false, true>(acc, sl, sA, sB, B);
+                    else slot_update_f<B, T, false, false>(acc, sl, sA, sB, B);
+                } else {
+                    if (tb) mma_update<B, T, P, false, true>(frag, sA, sB, B);
+                    else mma_update<B, T, P, false, false>(frag, sA, sB, B);
+                }
+            };
+            // sum_{K<I} L_IK D_KJ
+            for (int K = 0; K < I; ++K) {
+                const int k0 = K * B;
+                __syncthreads();
+                stage_f<B, T, F_FULL>(sA, L + i0 + (long)k0 * ldl, ldl, mI, B);
+                const bool tr = LYAP && K < J;
+                if (!tr) stage_f<B, T, F_FULL>(sB, W + k0 + (long)j0 * ldw, ldw, B, nJ);
+                else stage_f<B, T, F_FULL>(sB, W + j0 + (long)k0 * ldw, ldw, nJ, B);
+                __syncthreads();
+                update(tr);
+            }
+            // sum_{K<J} D_IK U_KJ   (Lyapunov: U_KJ = L_JK^T)
+            for (int K = 0; K < J; ++K) {
+                const int k0 = K * B;
+                __syncthreads();
+                stage_f<B, T, F_FULL>(sA, W + i0 + (long)k0 * ldw, ldw, mI, B);
+                if (!LYAP) stage_f<B, T, F_FULL>(sB, U + k0 + (long)j0 * ldu, ldu, B, nJ);
+                else stage_f<B, T, F_FULL>(sB, L + j0 + (long)k0 * ldl, ldl, nJ, B);
+                __syncthreads();
+                update(LYAP);
+            }
+            __syncthreads();
+            if constexpr (P == P_FP32) {
+#pragma unroll
+                for (int r = 0; r < E; ++r)
+                    if (sl.ok(r)) sT[sl.row[r] + sl.col[r] * LD] = acc[r];
+            } else {
+                frag_store<B, T>(frag, sT);
+            }
+            if (!LYAP) stage_f<B, T, F_UPPER>(sU, U + j0 + (long)j0 * ldu, ldu, nJ, nJ);
+            else stage_f<B, T, F_LOWER>(sU, L + j0 + (long)j0 * ldl, ldl, nJ, nJ);
+            __syncthreads();
+            syl_diag_f<B, T, LYAP>(sL, sU, sT, mI, nJ, Rinv + i0 + (long)j0 * ldw, ldw);
+            for (int e = threadIdx.x; e < mI * nJ; e += T) {
+                const int r = e % mI, c = e / mI;
+                W[(i0 + r) + (long)(j0 + c) * ldw] = sT[r + c * LD];
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// R = C - L X - X U (Lyapunov: U = L^T, lower blocks, X read through its
+// lower triangle) into W with FP64-class accuracy: double-float on the FP32
+// pipe (RS = R_DF) or FP64 FMA (RS = R_FP64).
+template <int B, int T, bool LYAP, int RS>
+__device__ void residual(int n, const double *L, long ldl, const double *U, long ldu,
+                         const double *C, long ldc, const double *X, long ldx, float *W, long ldw,
+                         float *sm)
+{
+    constexpr int E = B * B / T;
+    using Elem = typename std::conditional<RS == R_DF, float2, double>::type;
+    Elem *sA = reinterpret_cast<Elem *>(sm);
+    Elem *sB = sA + FTile<B>::SZ;
+    const int nb = (n + B - 1) / B;
+    Slots<B, T> sl;
+
+    auto stage = [&](Elem *S, const double *G, long ld, int rows, int cols, Fill f) {
+        if constexpr (RS == R_DF) {
+            float2 *S2 = reinterpret_cast<float2 *>(S);
+            switch (f) {
+            case F_FULL: stage_df<B, T, F_FULL>(S2, G, ld, rows, cols); break;
+            case F_LOWER: stage_df<B, T, F_LOWER>(S2, G, ld, rows, cols); break;
+            case F_UPPER: stage_df<B, T, F_UPPER>(S2, G, ld, rows, cols); break;
+            default: stage_df<B, T, F_SYM_LOWER>(S2, G, ld, rows, cols); break;
+            }
+        } else {
+            double *Sd = reinterpret_cast<double *>(S);
+            switch (f) {
+            case F_FULL: stage_d<B, T, F_FULL>(Sd, G, ld, rows, cols); break;
+            case F_LOWER: stage_d<B, T, F_LOWER>(Sd, G, ld, rows, cols); break;
+            case F_UPPER: stage_d<B, T, F_UPPER>(Sd, G, ld, rows, cols); break;
+            default: stage_d<B, T, F_SYM_LOWER>(Sd, G, ld, rows, cols); break;
+            }
+        }
+    };
+
+    for (int I = 0; I < nb; ++I) {
+        const int mI = min(B, n - I * B), i0 = I * B;
+        const int jend = LYAP ? I + 1 : nb;
+        for (int J = 0; J < jend; ++J) {
+            const int nJ = min(B, n - J * B), j0 = J * B;
+            sl.set(Shape::Full, mI, nJ);
+            float ah[E], al[E];
+            double ad[E];
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                ah[r] = 0.f; al[r] = 0.f; ad[r] = 0.0;
+                if (sl.ok(r)) {
+                    int rr = sl.row[r], cc = sl.col[r];
+                    if (LYAP && I == J && rr < cc) { const int t = rr; rr = cc; cc = t; }
+                    const double c = C[(i0 + rr) + (long)(j0 + cc) * ldc];
+                    if (RS == R_DF) split_df(c, ah[r], al[r]);
+                    else ad[r] = c;
+                }
+            }
+            auto upd = [&](bool tb, int kw) {
+                if constexpr (RS == R_DF) {
+                    const float2 *a = reinterpret_cast<const float2 *>(sA);
+                    const float2 *b = reinterpret_cast<const float2 *>(sB);
+                    if (tb) slot_update_df<B, T, false, true>(ah, al, sl, a, b, kw);
+                    else slot_update_df<B, T, false, false>(ah, al, sl, a, b, kw);
+                } else {
+                    const double *a = reinterpret_cast<const double *>(sA);
+                    const double *b = reinterpret_cast<const double *>(sB);
+                    if (tb) slot_update<B, T, false, true>(ad, sl, a, b, kw);
+                    else slot_update<B, T, false, false>(ad, sl, a, b, kw);
+                }
+            };
+            // sum_{K<=I} L_IK X_KJ
+            for (int K = 0; K <= I; ++K) {
+                const int k0 = K * B, kw = min(B, n - k0);
+                __syncthreads();
+                stage(sA, L + i0 + (long)k0 * ldl, ldl, mI, kw, K == I ? F_LOWER : F_FULL);
+                bool tb = false;
+                if (!LYAP || K > J) stage(sB, X + k0 + (long)j0 * ldx, ldx, kw, nJ, F_FULL);
+                else if (K == J) stage(sB, X + j0 + (long)j0 * ldx, ldx, kw, nJ, F_SYM_LOWER);
+                else { stage(sB, X + j0 + (long)k0 * ldx, ldx, nJ, kw, F_FULL); tb = true; }
+                __syncthreads();
+                upd(tb, kw);
+            }
+            // sum_{K<=J} X_IK U_KJ   (Lyapunov: L_JK^T)
+            for (int K = 0; K <= J; ++K) {
+                const int k0 = K * B, kw = min(B, n - k0);
+                __syncthreads();
+                if (LYAP && K == I) stage(sA, X + i0 + (long)i0 * ldx, ldx, mI, kw, F_SYM_LOWER);
+                else stage(sA, X + i0 + (long)k0 * ldx, ldx, mI, kw, F_FULL);
+                if (!LYAP) stage(sB, U + k0 + (long)j0 * ldu, ldu, kw, nJ, K == J ? F_UPPER : F_FULL);
+                else stage(sB, L + j0 + (long)k0 * ldl, ldl, nJ, kw, K == J ? F_LOWER : F_FULL);
+                __syncthreads();
+                upd(LYAP, kw);
+            }
+#pragma unroll
+            for (int r = 0; r < E; ++r) {
+                if (sl.ok(r)) {
+                    const float v = RS == R_DF ? __fadd_rn(ah[r], al[r]) : (float)ad[r];
+                    W[(i0 + sl.row[r]) + (long)(j0 + sl.col[r]) * ldw] = v;
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// X (FP64, the meaningful triangle) = X + D (first: X = D); returns |D|_F^2.
+template <int T, bool LYAP>
+__device__ float update_x(int n, double *X, long ldx, const float *W, long ldw, bool first,
+                          float *s_red)
+{
+    float ss = 0.0f;
+    for (int e = threadIdx.x; e < n * n; e += T) {
+        const int r = e % n, c = e / n;
+        if (LYAP && r < c) continue;
+        const float d = W[r + (long)c * ldw];
+        ss = fmaf(d, d, ss);
+        double *p = X + r + (long)c * ldx;
+        *p = first ? f2d_exact(d) : *p + f2d_exact(d);
+    }
+    return block_sum_f(ss, s_red);
+}
+
+// r_ij = 1 / (l_ii + u_jj) computed in FP64, stored (rounded) as FP32 into
+// Rinv (ld n); returns 1 if a divisor is tiny or NaN.
+template <int T, bool LYAP>
+__device__ int reciprocal_divisors(int n, const double *L, long ldl, const double *U, long ldu,
+                                   float *Rinv, float *s_red)
+{
+    double md = 0.0;
+    for (int i = threadIdx.x; i < n; i += T) {
+        md = fmax(md, fabs(L[i + (long)i * ldl]));
+        if (!LYAP) md = fmax(md, fabs(U[i + (long)i * ldu]));
+    }
+    for (int o = 16; o > 0; o >>= 1) md = fmax(md, __shfl_xor_sync(0xffffffffu, md, o));
+    double *s_md = reinterpret_cast<double *>(s_red);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) s_md[threadIdx.x >> 5] = md;
+    __syncthreads();
+    md = 0.0;
+    for (int w = 0; w < T / 32; ++w) md = fmax(md, s_md[w]);
+    const double delta = divisor_delta(n, md);
+    int bad = 0;
+    for (int e = threadIdx.x; e < n * n; e += T) {
+        const int i = e % n, j = e / n;
+        const double d = L[i + (long)i * ldl] + (LYAP ? L[j + (long)j * ldl] : U[j + (long)j * ldu]);
+        if (!(fabs(d) > delta)) bad = 1;
+        Rinv[e] = d2f_trunc(1.0 / d);
+    }
+    return __syncthreads_or(bad);
+}
+
+template <int B, int T, bool LYAP, int P, int RS>
+__device__ void mixed_instance(int n, const double *L, long ldl, const double *U, long ldu,
+                               const double *C, long ldc, double *X, long ldx, int *info,
+                               float *W, float *Rinv, bool raw, float *sm)
+{
+    float *s_red = sm + 5 * FTile<B>::SZ;
+    const int bad = reciprocal_divisors<T, LYAP>(n, L, ldl, U, ldu, Rinv, s_red);
+    low_solve<B, T, LYAP, P, true>(n, L, ldl, U, ldu, C, ldc, W, Rinv, sm);
+    const float nx2 = update_x<T, LYAP>(n, X, ldx, W, n, true, s_red);
+    int conv = nx2 == 0.0f;
+    if (!raw) {
+        const float tol = (float)SS_REFINE_TOL;
+        const float nx = sqrtf(nx2);
+        float prev = nx;
+        for (int it = 0; it < MAXIT && !conv; ++it) {
+            residual<B, T, LYAP, RS>(n, L, ldl, U, ldu, C, ldc, X, ldx, W, n, sm);
+            low_solve<B, T, LYAP, P, false>(n, L, ldl, U, ldu, C, ldc, W, Rinv, sm);
+            const float nd = sqrtf(update_x<T, LYAP>(n, X, ldx, W, n, false, s_red));
+            const float pred = prev > 0.0f ? nd * (nd / prev) : nd;
+            conv = (nd <= tol * nx) || (pred <= tol * nx);
+            prev = nd;
+        }
+    } else {
+        conv = 1;
+    }
+    if (threadIdx.x == 0) *info = bad ? 1 : (conv ? 0 : n + 1);
+}
+
+// ------------------------------------------------ shared-memory-resident variant
+//
+// For n <= NMAX the whole low-precision problem lives in shared memory as
+// FP32: L, U (for the Lyapunov form U = L^T, stored explicitly so both are
+// read with unit stride) and the right-hand side / solution D, each n x ld
+// with ld = n rounded up to even (so a row walk, stride ld - 1, is odd and
+// hits distinct banks).  The solve is an eager wavefront over the
+// anti-diagonals d = i + j, one barrier per anti-diagonal: entries with
+// i + j = d are final; every entry with a + b > d subtracts the two terms that
+// involve them,
+//     t_ab -= l_{a, d-b} x_{d-b, b}   (b <= d)   and   t_ab -= x_{a, d-a} u_{d-a, b}   (a <= d),
+// and entries reaching a + b = d + 1 are finished by the FP64-computed
+// reciprocal.  Each thread keeps its entries' partial sums in registers.
+// Larger instances fall back to the blocked path with B = 32.
+
+template <int NMAX, int T>
+__device__ void smem_wavefront(float *Xs, const float *Ls, const float *Us, int n, int ld,
+                               const float *Rinv)
+{
+    constexpr int R = (NMAX * NMAX + T - 1) / T;
+    const int nn = n * n;
+    float tv[R];
+    int ab[R];      // row | column << 16; entries beyond n*n get a row past n
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int e = threadIdx.x + T * r;
+        const int a = e < nn ? e % n : 0x7fff, b = e < nn ? e / n : 0;
+        ab[r] = a | (b << 16);
+        tv[r] = e < nn ? Xs[a + b * ld] : 0.0f;
+        if (e == 0) {
+            tv[r] *= Rinv[0];
+            Xs[0] = tv[r];
+        }
+    }
+    __syncthreads();
+    for (int d = 0; d <= 2 * n - 3; ++d) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int a = ab[r] & 0xffff, b = ab[r] >> 16;
+            if (a + b > d && a < n) {
+                float t = tv[r];
+                if (b <= d) t = fmaf(-Ls[a + (d - b) * ld], Xs[(d - b) + b * ld], t);
+                if (a <= d) t = fmaf(-Xs[a + (d - a) * ld], Us[(d - a) + b * ld], t);
+                if (a + b == d + 1) {
+                    t *= Rinv[a + (long)b * n];
+                    Xs[a + b * ld] = t;
+                }
+                tv[r] = t;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int NMAX>
+constexpr size_t smem_variant_bytes()
+{
+    // L, U and D (n x ld floats each, ld <= NMAX + 1), the residual's two
+    // B = 32 tiles of 8-byte elements, the blocked fallback (five float B = 32
+    // tiles, which fit inside the same region) and a reduction buffer.
+    return (size_t)3 * NMAX * (NMAX + 1) * sizeof(float) + 2 * FTile<32>::SZ * 8 + 64 * sizeof(float);
+}
+
+template <int NMAX, int T, bool LYAP, int RS>
+__device__ void smem_instance(int n, const double *L, long ldl, const double *U, long ldu,
+                              const double *C, long ldc, double *X, long ldx, int *info,
+                              float *W, bool raw, float *sm)
+{
+    constexpr size_t tiles_off = (size_t)3 * NMAX * (NMAX + 1);     // floats
+    float *s_red = sm + tiles_off + 2 * FTile<32>::SZ * 2;
+    if (n > NMAX) {
+        // Blocked fallback: its five tiles live at the start of shared memory.
+        float *Rinv = W + (long)n * n;
+        const int bad = reciprocal_divisors<T, LYAP>(n, L, ldl, U, ldu, Rinv, s_red);
+        low_solve<32, T, LYAP, P_FP32, true>(n, L, ldl, U, ldu, C, ldc, W, Rinv, sm);
+        const float nx = sqrtf(update_x<T, LYAP>(n, X, ldx, W, n, true, s_red));
+        int conv = nx == 0.0f || raw;
+        float prev = nx;
+        for (int it = 0; it < MAXIT && !conv; ++it) {
+            residual<32, T, LYAP, RS>(n, L, ldl, U, ldu, C, ldc, X, ldx, W, n, sm);
+            low_solve<32, T, LYAP, P_FP32, false>(n, L, ldl, U, ldu, C, ldc, W, Rinv, sm);
+            const float nd = sqrtf(update_x<T, LYAP>(n, X, ldx, W, n, false, s_red));
+            const float pred = prev > 0.0f ? nd * (nd / prev) : nd;
+            conv = (nd <= (float)SS_REFINE_TOL * nx) || (pred <= (float)SS_REFINE_TOL * nx);
+            prev = nd;
+        }
+        if (threadIdx.x == 0) *info = bad ? 1 : (conv ? 0 : n + 1);
+        return;
+    }
+    const int ld = (n + 1) & ~1;
+    float *Ls = sm, *Us = sm + (long)n * ld, *Xs = sm + 2l * n * ld;
+    float *tiles = sm + tiles_off;
+    float *Rinv = W + (long)n * n;
+    const int bad = reciprocal_divisors<T, LYAP>(n, L, ldl, U, ldu, Rinv, s_red);
+    for (int e = threadIdx.x; e < n * n; e += T) {
+        const int a = e % n, b = e / n;
+        Ls[a + b * ld] = a > b ? d2f_trunc(L[a + (long)b * ldl]) : 0.0f;
+        const double u = LYAP ? L[b + (long)a * ldl] : U[a + (long)b * ldu];
+        Us[a + b * ld] = a < b ? d2f_trunc(u) : 0.0f;
+        const double c = (LYAP && a < b) ? C[b + (long)a * ldc] : C[a + (long)b * ldc];
+        Xs[a + b * ld] = d2f_trunc(c);
+    }
+    __syncthreads();
+    smem_wavefront<NMAX, T>(Xs, Ls, Us, n, ld, Rinv);
+    const float nx = sqrtf(update_x<T, LYAP>(n, X, ldx, Xs, ld, true, s_red));
+    int conv = nx == 0.0f || raw;
+    float prev = nx;
+    for (int it = 0; it < MAXIT && !conv; ++it) {
+        residual<32, T, LYAP, RS>(n, L, ldl, U, ldu, C, ldc, X, ldx, Xs, ld, tiles);
+        if (LYAP) {
+            // The residual is symmetric; it was written for the lower blocks.
+            for (int e = threadIdx.x; e < n * n; e += T) {
+                const int a = e % n, b = e / n;
+                if (a < b) Xs[a + b * ld] = Xs[b + a * ld];
+            }
+            __syncthreads();
+        }
+        smem_wavefront<NMAX, T>(Xs, Ls, Us, n, ld, Rinv);
+        const float nd = sqrtf(update_x<T, LYAP>(n, X, ldx, Xs, ld, false, s_red));
+        const float pred = prev > 0.0f ? nd * (nd / prev) : nd;
+        conv = (nd <= (float)SS_REFINE_TOL * nx) || (pred <= (float)SS_REFINE_TOL * nx);
+        prev = nd;
+    }
+    if (threadIdx.x == 0) *info = bad ? 1 : (conv ? 0 : n + 1);
+}
+
+template <int NMAX, int T, bool LYAP, int RS>
+__global__ void __launch_bounds__(T) smem_syl_kernel(Operands o, Sched s, int group, int raw)
+{
+    extern __shared__ __align__(16) float smf[];
+    __shared__ int s_slot;
+    const int lo = s.meta[META_RANGE + 2 * group], hi = s.meta[META_RANGE + 2 * group + 1];
+    for (;;) {
+        const int w = lo + claim_slot(s.meta + META_HEAD + group, &s_slot);
+        if (w >= hi) break;
+        const int b = s.perm[w];
+        const int n = o.n[b];
+        if (n == 0) { if (threadIdx.x == 0) o.info[b] = 0; continue; }
+        const long long off = s.scr[w];
+        if (off + 2ll * n * n > s.scratch_elems) {
+            if (threadIdx.x == 0) o.info[b] = SS_INFO_NO_WORK;
+            continue;
+        }
+        float *W = static_cast<float *>(s.scratch) + off;
+        smem_instance<NMAX, T, LYAP, RS>(n, o.A[b], o.lda[b], LYAP ? nullptr : o.U[b],
+                                         LYAP ? 0 : o.ldu[b], o.C[b], o.ldc[b], o.X[b], o.ldx[b],
+                                         o.info + b, W, raw != 0, smf);
+    }
+}
+
+template <int NMAX, int T, bool LYAP, int RS>
+cudaError_t launch_smem_syl(const Operands &o, const Sched &s, const Launch &l, cudaStream_t st, int raw)
+{
+    auto kern = smem_syl_kernel<NMAX, T, LYAP, RS>;
+    const size_t smem = smem_variant_bytes<NMAX>();
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    long grid = (long)per_sm * sm_count();
+    if (grid > l.batch) grid = l.batch;
+    if (grid < 1) grid = 1;
+    kern<<<(int)grid, T, smem, st>>>(o, s, l.group, raw);
+    return cudaGetLastError();
+}
+
+template <int B, int T, bool LYAP, int P, int RS>
+__global__ void __launch_bounds__(T) mixed_syl_kernel(Operands o, Sched s, int group, int raw)
+{
+    extern __shared__ __align__(16) float smf[];
+    __shared__ int s_slot;
+    const int lo = s.meta[META_RANGE + 2 * group], hi = s.meta[META_RANGE + 2 * group + 1];
+    for (;;) {
+        const int w = lo + claim_slot(s.meta + META_HEAD + group, &s_slot);
+        if (w >= hi) break;
+        const int b = s.perm[w];
+        const int n = o.n[b];
+        if (n == 0) { if (threadIdx.x == 0) o.info[b] = 0; continue; }
+        const long long off = s.scr[w];
+        if (off + 2ll * n * n > s.scratch_elems) {
+            if (threadIdx.x == 0) o.info[b] = SS_INFO_NO_WORK;
+            continue;
+        }
+        float *W = static_cast<float *>(s.scratch) + off;
+        mixed_instance<B, T, LYAP, P, RS>(n, o.A[b], o.lda[b], LYAP ? nullptr : o.U[b],
+                                          LYAP ? 0 : o.ldu[b], o.C[b], o.ldc[b], o.X[b], o.ldx[b],
+                                          o.info + b, W, W + (long)n * n, raw != 0, smf);
+    }
+}
+
+template <int B, int T, bool LYAP, int P, int RS>
+cudaError_t launch_mixed_syl(const Operands &o, const Sched &s, const Launch &l, cudaStream_t st, int raw)
+{
+    auto kern = mixed_syl_kernel<B, T, LYAP, P, RS>;
+    const size_t smem = mixed_smem_bytes<B>();
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    long grid = (long)per_sm * sm_count();
+    if (grid > l.batch) grid = l.batch;
+    if (grid < 1) grid = 1;
+    kern<<<(int)grid, T, smem, st>>>(o, s, l.group, raw);
+    return cudaGetLastError();
+}
+
+}  // namespace mx
+}  // namespace ss

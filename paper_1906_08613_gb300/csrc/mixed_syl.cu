@@ -1,0 +1,40 @@
+// Instantiations of the mixed-precision Sylvester kernels (see mixed_solver.cuh).
+#include "mixed_solver.cuh"
+
+namespace ss {
+
+// cfg -> (B, T, residual) per precision; the table is mirrored in mixed_api.cu.
+cudaError_t launch_mixed_trsyl(int prec, int cfg, const Operands &o, const Sched &s, const Launch &l,
+                             cudaStream_t st, int raw)
+{
+    using namespace mx;
+    if (prec == P_FP32) {
+        switch (cfg) {
+        case 0: return launch_mixed_syl<16, 64, false, P_FP32, R_DF>(o, s, l, st, raw);
+        case 1: return launch_mixed_syl<16, 128, false, P_FP32, R_DF>(o, s, l, st, raw);
+        case 2: return launch_mixed_syl<32, 128, false, P_FP32, R_DF>(o, s, l, st, raw);
+        case 3: return launch_mixed_syl<16, 128, false, P_FP32, R_FP64>(o, s, l, st, raw);
+        case 4: return launch_mixed_syl<32, 128, false, P_FP32, R_FP64>(o, s, l, st, raw);
+        case 5: return launch_smem_syl<128, 1024, false, R_DF>(o, s, l, st, raw);
+        case 6: return launch_smem_syl<64, 512, false, R_DF>(o, s, l, st, raw);
+        case 7: return launch_smem_syl<128, 1024, false, R_FP64>(o, s, l, st, raw);
+        }
+    } else if (prec == P_TF32) {
+        switch (cfg) {
+        case 0: return launch_mixed_syl<16, 64, false, P_TF32, R_DF>(o, s, l, st, raw);
+        case 1: return launch_mixed_syl<32, 128, false, P_TF32, R_DF>(o, s, l, st, raw);
+        case 2: return launch_mixed_syl<16, 64, false, P_TF32, R_FP64>(o, s, l, st, raw);
+        case 3: return launch_mixed_syl<32, 128, false, P_TF32, R_FP64>(o, s, l, st, raw);
+        }
+    } else if (prec == P_BF16) {
+        switch (cfg) {
+        case 0: return launch_mixed_syl<16, 64, false, P_BF16, R_DF>(o, s, l, st, raw);
+        case 1: return launch_mixed_syl<32, 128, false, P_BF16, R_DF>(o, s, l, st, raw);
+        case 2: return launch_mixed_syl<16, 64, false, P_BF16, R_FP64>(o, s, l, st, raw);
+        case 3: return launch_mixed_syl<32, 128, false, P_BF16, R_FP64>(o, s, l, st, raw);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace ss

@@ -44,36 +44,48 @@ __device__ __forceinline__ double block_max_abs_diag(const double *P, long ld, i
 //
 // Solve Lt Y + Y Ut = T in place for an m x nn block in sT, Lt = sL (lower
 // triangular m x m), Ut = sU (upper, nn x nn) or, with UT, the transpose of
-// the lower triangular sU.  Wavefront over anti-diagonals d = i + j; the
-// entries of one anti-diagonal are independent and each is a dot product of
-// length d split over `split` lanes.  Returns 1 if a divisor was tiny.
+// the lower triangular sU.  First the block's reciprocal divisors
+// 1 / (l_ii + u_jj) go to sR with every lane busy; then a wavefront over the
+// anti-diagonals d = i + j: the entries of one anti-diagonal are independent,
+// and each is one dot product of exactly d terms (i from the L row, j from the
+// U column), split over `split` lanes so that one anti-diagonal fills one
+// warp.  FP64 lanes are the scarce resource on this GPU, so idle warps are
+// preferred to partially filled ones.  Returns 1 if a divisor was tiny.
 template <int B, int T, bool UT>
-__device__ int syl_diag(const double *sL, const double *sU, double *sT, int m, int nn, double delta)
+__device__ int syl_diag(const double *sL, const double *sU, double *sT, double *sR, int m, int nn,
+                        double delta)
 {
     constexpr int LD = Tile<B>::LD;
     int bad = 0;
+    for (int e = threadIdx.x; e < m * nn; e += T) {
+        const int i = e % m, j = e / m;
+        const double dd = sL[i + i * LD] + sU[j + j * LD];
+        if (!(fabs(dd) > delta)) bad = 1;
+        sR[i + j * LD] = 1.0 / dd;
+    }
+    __syncthreads();
     for (int d = 0; d <= m + nn - 2; ++d) {
         const int ilo = max(0, d - nn + 1), ihi = min(d, m - 1);
         const int cnt = ihi - ilo + 1;
-        const int split = pick_split<T>(cnt, d);
+        int split = cnt >= 32 ? 1 : pow2_floor(32 / cnt);
+        const int byLen = pow2_floor(d > 1 ? d : 1);
+        split = split < byLen ? split : byLen;
         if (warp_has_work(cnt, split)) {
             const int idx = threadIdx.x / split, part = threadIdx.x % split;
             const bool act = idx < cnt;
             const int i = ilo + (act ? idx : 0), j = d - i;
             double s = 0.0;
             if (act) {
-                for (int k = part; k < i; k += split) s = fma(sL[i + k * LD], sT[k + j * LD], s);
-                for (int k = part; k < j; k += split) {
-                    const double u = UT ? sU[j + k * LD] : sU[k + j * LD];
-                    s = fma(sT[i + k * LD], u, s);
+                for (int t = part; t < d; t += split) {
+                    const bool lt = t < i;
+                    const int k = t - i;
+                    const double a = lt ? sL[i + t * LD] : sT[i + k * LD];
+                    const double b = lt ? sT[t + j * LD] : (UT ? sU[j + k * LD] : sU[k + j * LD]);
+                    s = fma(a, b, s);
                 }
             }
             s = group_sum(s, split);
-            if (act && part == 0) {
-                const double dd = sL[i + i * LD] + (UT ? sU[j + j * LD] : sU[j + j * LD]);
-                if (!(fabs(dd) > delta)) bad = 1;
-                sT[i + j * LD] = (sT[i + j * LD] - s) / dd;
-            }
+            if (act && part == 0) sT[i + j * LD] = (sT[i + j * LD] - s) * sR[i + j * LD];
         }
         __syncthreads();
     }
@@ -149,7 +161,7 @@ __device__ void syl_instance(int n, const double *L, long ldl, const double *U, 
             if (!LYAP) stage_tri<B, T>(sU, U + j0 + (long)j0 * ldu, ldu, nJ, false);
             else       stage_tri<B, T>(sU, L + j0 + (long)j0 * ldl, ldl, nJ, true);
             __syncthreads();
-            bad |= syl_diag<B, T, LYAP>(sL, sU, sT, mI, nJ, delta);
+            bad |= syl_diag<B, T, LYAP>(sL, sU, sT, sA, mI, nJ, delta);
             // syl_diag ends with a barrier.
 #pragma unroll
             for (int r = 0; r < E; ++r) {

@@ -78,6 +78,12 @@ def lib():
             L.ss_set_config_table.restype = i
             L.ss_version.argtypes = []
             L.ss_version.restype = i
+            L.ss_launch_count.argtypes = []
+            L.ss_launch_count.restype = ctypes.c_longlong
+            L.ss_profile_enable.argtypes = [i]
+            L.ss_profile_enable.restype = i
+            L.ss_profile_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i)]
+            L.ss_profile_read.restype = i
             _lib = L
     return _lib
 
@@ -133,6 +139,23 @@ def ss_set_config_table(op, mode, cfg_by_bin) -> None:
 
 def ss_version() -> int:
     return int(lib().ss_version())
+
+
+def ss_launch_count() -> int:
+    return int(lib().ss_launch_count())
+
+
+def ss_profile_enable(on: bool) -> None:
+    _check(lib().ss_profile_enable(1 if on else 0), "ss_profile_enable")
+
+
+def ss_profile_read():
+    """(total milliseconds, number of calls) of the solve kernels recorded
+    since the last read."""
+    t = ctypes.c_double(0.0)
+    c = ctypes.c_int(0)
+    _check(lib().ss_profile_read(ctypes.byref(t), ctypes.byref(c)), "ss_profile_read")
+    return float(t.value), int(c.value)
 
 
 def size_bin(n: int) -> int:
