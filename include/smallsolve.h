@@ -96,6 +96,7 @@ extern "C" {
 
 /* return and info codes */
 #define SS_ERR_CUDA       (-100)
+#define SS_ERR_SCRATCH_LIMIT (-101)
 #define SS_INFO_BAD_SIZE  (-1)
 #define SS_INFO_NO_WORK   (-2)
 
@@ -156,6 +157,25 @@ int ss_config_describe(int op, int mode, int cfg, int *block, int *threads, int 
  * nbins = 0 clears it.  Calls are not thread-safe with concurrent solves.
  */
 int ss_set_config_table(int op, int mode, int nbins, const int *cfg_by_bin);
+
+/*
+ * trsyl_lu without a workspace argument, for callers that cannot allocate
+ * device memory (the paper has no counterpart; this is a library interface
+ * choice).  Same arguments, layout and info codes as trsyl_lu in
+ * SS_MODE_FP64 with SS_CFG_DEFAULT, minus d_work/work_bytes: the scratch is a
+ * fixed 1 MiB area in the library's own device memory, held on every device
+ * that loads the library until the process exits.  That is enough for any
+ * batch up to 262016 instances (any max_n); a larger batch returns
+ * SS_ERR_SCRATCH_LIMIT before anything is launched.  The first call on each
+ * device looks the area's address up (cudaGetSymbolAddress) with that device
+ * current, so make it before any stream capture.  All calls share the area:
+ * calls that overlap on the GPU race and must be ordered.  Allocates nothing.
+ */
+int trsyl_lu_noalloc(int batch, int max_n, const int *d_n,
+                     const double *const *d_L, const int *d_ldl,
+                     const double *const *d_U, const int *d_ldu,
+                     const double *const *d_C, const int *d_ldc,
+                     double *const *d_X, const int *d_ldx, int *d_info, void *stream);
 
 /* Library version. */
 int ss_version(void);

@@ -36,6 +36,7 @@ CFG_DEFAULT = -1
 CFG_TABLE = -2
 
 ERR_CUDA = -100
+ERR_SCRATCH_LIMIT = -101
 INFO_BAD_SIZE = -1
 INFO_NO_WORK = -2
 MAX_N = 4096
@@ -67,6 +68,8 @@ def lib():
             L.trlyap_l.argtypes = [i, i, vp, vp, vp, vp, vp, vp, vp, vp, i, i, vp, sz, vp]
             for f in (L.potrf_upper, L.trsyl_lu, L.trlyap_l):
                 f.restype = i
+            L.trsyl_lu_noalloc.argtypes = [i, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+            L.trsyl_lu_noalloc.restype = i
             L.ss_workspace_size.argtypes = [i, i, i, i, ctypes.POINTER(sz)]
             L.ss_workspace_size.restype = i
             L.ss_config_count.argtypes = [i, i]
@@ -106,6 +109,15 @@ def trsyl_lu(batch, max_n, d_n, d_L, d_ldl, d_U, d_ldu, d_C, d_ldc, d_X, d_ldx, 
     rc = lib().trsyl_lu(batch, max_n, d_n, d_L, d_ldl, d_U, d_ldu, d_C, d_ldc, d_X, d_ldx,
                         d_info, mode, cfg, d_work or None, work_bytes, stream or None)
     return _check(rc, "trsyl_lu") if check else rc
+
+
+def trsyl_lu_noalloc(batch, max_n, d_n, d_L, d_ldl, d_U, d_ldu, d_C, d_ldc, d_X, d_ldx, d_info,
+                     stream=0, check=True):
+    """trsyl_lu (FP64, default configuration) using the library's fixed scratch
+    area instead of a caller-provided workspace; allocates nothing."""
+    rc = lib().trsyl_lu_noalloc(batch, max_n, d_n, d_L, d_ldl, d_U, d_ldu, d_C, d_ldc, d_X,
+                                d_ldx, d_info, stream or None)
+    return _check(rc, "trsyl_lu_noalloc") if check else rc
 
 
 def trlyap_l(batch, max_n, d_n, d_L, d_ldl, d_S, d_lds, d_X, d_ldx, d_info, mode=MODE_FP64,
