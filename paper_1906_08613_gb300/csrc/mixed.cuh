@@ -207,7 +207,7 @@ __device__ __forceinline__ void slot_update_df(float (&ah)[B * B / T], float (&a
 {
     constexpr int LD = FTile<B>::LD;
     constexpr int E = B * B / T;
-#pragma unroll 2
+#pragma unroll 1
     for (int k = 0; k < kk; ++k) {
 #pragma unroll
         for (int r = 0; r < E; ++r) {
@@ -233,6 +233,12 @@ struct MmaShape {
     static constexpr int TPW = TILES / NW;
     static_assert(TILES % NW == 0 && TPW >= 1, "mma tiling needs whole tiles per warp");
 };
+
+// Tensor-core fragments per warp (1 for the FP32 path, which uses none).
+template <int B, int T, int P>
+struct FragN { static constexpr int value = MmaShape<B, T>::TPW; };
+template <int B, int T>
+struct FragN<B, T, P_FP32> { static constexpr int value = 1; };
 
 __device__ __forceinline__ unsigned to_tf32(float x)
 {

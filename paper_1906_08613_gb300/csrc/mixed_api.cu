@@ -7,6 +7,8 @@ cudaError_t launch_mixed_trsyl(int prec, int cfg, const Operands &o, const Sched
                                cudaStream_t st, int raw);
 cudaError_t launch_mixed_trlyap(int prec, int cfg, const Operands &o, const Sched &s, const Launch &l,
                                 cudaStream_t st, int raw);
+cudaError_t launch_mixed_potrf(int prec, int cfg, const Operands &o, const Sched &s, const Launch &l,
+                               cudaStream_t st, int raw);
 
 namespace {
 
@@ -16,6 +18,9 @@ namespace {
 const Config kFp32Cfg[] = {{16, 64, 0},  {16, 128, 0},  {32, 128, 0},  {16, 128, 1},
                            {32, 128, 1}, {128, 1024, 2}, {64, 512, 2}, {128, 1024, 3}};
 const Config kTcCfg[] = {{16, 64, 0}, {32, 128, 0}, {16, 64, 1}, {32, 128, 1}};
+// Cholesky (blocked lazy factorization, then factor refinement).
+const Config kCholFp32Cfg[] = {{16, 64, 0}, {16, 128, 0}, {32, 128, 0}, {32, 128, 1}};
+const Config kCholTcCfg[] = {{16, 64, 0}, {32, 128, 0}, {32, 128, 1}};
 
 // Low-precision arithmetic of a mode: 0 FP32, 1 TF32, 2 BF16; -1 not mixed.
 int mode_prec(int mode)
@@ -37,13 +42,16 @@ bool mode_raw(int mode)
 int mixed_config_count(int op, int mode)
 {
     const int p = mode_prec(mode);
-    if (p < 0 || op == SS_OP_POTRF) return 0;
+    if (p < 0) return 0;
+    if (op == SS_OP_POTRF)
+        return p == 0 ? (int)(sizeof(kCholFp32Cfg) / sizeof(Config)) : (int)(sizeof(kCholTcCfg) / sizeof(Config));
     return p == 0 ? (int)(sizeof(kFp32Cfg) / sizeof(Config)) : (int)(sizeof(kTcCfg) / sizeof(Config));
 }
 
 const Config *mixed_config_get(int op, int mode, int cfg)
 {
     if (cfg < 0 || cfg >= mixed_config_count(op, mode)) return nullptr;
+    if (op == SS_OP_POTRF) return mode_prec(mode) == 0 ? &kCholFp32Cfg[cfg] : &kCholTcCfg[cfg];
     return mode_prec(mode) == 0 ? &kFp32Cfg[cfg] : &kTcCfg[cfg];
 }
 
@@ -60,6 +68,7 @@ cudaError_t launch_mixed(int op, const Operands &o, const Sched &s, const Launch
     const int raw = mode_raw(l.mode) ? 1 : 0;
     if (op == SS_OP_TRSYL) return launch_mixed_trsyl(p, l.cfg, o, s, l, st, raw);
     if (op == SS_OP_TRLYAP) return launch_mixed_trlyap(p, l.cfg, o, s, l, st, raw);
+    if (op == SS_OP_POTRF) return launch_mixed_potrf(p, l.cfg, o, s, l, st, raw);
     return cudaErrorNotSupported;
 }
 

@@ -8,12 +8,6 @@
 namespace ss {
 namespace mx {
 
-// Tensor-core fragments per warp (1 for the FP32 path, which uses none).
-template <int B, int T, int P>
-struct FragN { static constexpr int value = MmaShape<B, T>::TPW; };
-template <int B, int T>
-struct FragN<B, T, P_FP32> { static constexpr int value = 1; };
-
 template <int B>
 constexpr size_t mixed_smem_bytes()
 {
@@ -453,7 +447,7 @@ cudaError_t launch_smem_syl(const Operands &o, const Sched &s, const Launch &l, 
 }
 
 template <int B, int T, bool LYAP, int P, int RS>
-__global__ void __launch_bounds__(T) mixed_syl_kernel(Operands o, Sched s, int group, int raw)
+__global__ void __launch_bounds__(T, 1024 / T) mixed_syl_kernel(Operands o, Sched s, int group, int raw)
 {
     extern __shared__ __align__(16) float smf[];
     __shared__ int s_slot;

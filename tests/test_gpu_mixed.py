@@ -30,7 +30,7 @@ def run(op, pk, mode, cfg=ss.CFG_DEFAULT, **kw):
     return db.x_host(), db.info_host()
 
 
-@pytest.mark.parametrize("op", ["trsyl", "trlyap"])
+@pytest.mark.parametrize("op", ["potrf", "trsyl", "trlyap"])
 @pytest.mark.parametrize("mode", REFINED)
 def test_refined_every_config(op, mode):
     n = np.array(SIZES, dtype=np.int32)
@@ -42,7 +42,7 @@ def test_refined_every_config(op, mode):
         assert_parity(op, pk, x, ref, sentinel=SENT)
 
 
-@pytest.mark.parametrize("op", ["trsyl", "trlyap"])
+@pytest.mark.parametrize("op", ["potrf", "trsyl", "trlyap"])
 @pytest.mark.parametrize("mode", sorted(RAW_BOUND))
 def test_raw_modes_error_is_that_of_the_low_precision(op, mode):
     n = np.array([7, 40, 96], dtype=np.int32)
@@ -55,7 +55,7 @@ def test_raw_modes_error_is_that_of_the_low_precision(op, mode):
     assert np.all(errs > 0)   # it is genuinely the low-precision result
 
 
-@pytest.mark.parametrize("op", ["trsyl", "trlyap"])
+@pytest.mark.parametrize("op", ["potrf", "trsyl", "trlyap"])
 @pytest.mark.parametrize("mode", REFINED)
 def test_refinement_reports_non_convergence(op, mode):
     # A NaN in the right-hand side (the divisors are fine) keeps every
@@ -65,7 +65,15 @@ def test_refinement_reports_non_convergence(op, mode):
     # the iteration still contracts and stops at the residual's precision.)
     n = np.array([24, 24], dtype=np.int32)
     pk = inputs.make_batch(op, n, seed=33)
-    rhs = "C" if op == "trsyl" else "S"
+    rhs = {"trsyl": "C", "trlyap": "S", "potrf": "A"}[op]
+    if op == "potrf":
+        # For the Cholesky factor the NaN reaches a pivot first, which is
+        # reported as that leading minor's failure, exactly as the oracle does.
+        pk.view(rhs, 1)[3, 20] = np.nan
+        _, rinfo = oracle_batch(op, pk)
+        _, info = run(op, pk, mode)
+        assert list(info) == list(rinfo) and info[1] == 21
+        return
     pk.view(rhs, 1)[20, 3] = np.nan
     _, info = run(op, pk, mode)
     assert info[0] == 0
@@ -85,7 +93,27 @@ def test_singular_divisor_flagged(op):
     assert info[0] == 1
 
 
-@pytest.mark.parametrize("name,mode", [("trsyl_4096xU4-128", "fp32_refined"),
+def test_mixed_cholesky_failure_and_untouched_lower():
+    n = np.array([5, 30, 40], dtype=np.int32)
+    pk = inputs.cholesky_batch(n, seed=36)
+    pk.view("A", 1)[12, 12] = -100.0            # leading minor 13 fails
+    pk.view("A", 2)[np.tril_indices(40, -1)] = np.nan   # never read
+    ref, rinfo = oracle_batch("potrf", pk)
+    for mode in REFINED:
+        x, info = run("potrf", pk, mode)
+        assert list(info) == [0, 13, 0] == list(rinfo)
+        for b in (0, 2):
+            nb, o = int(n[b]), int(pk.off[b])
+            g = x[o:o + nb * nb].reshape(nb, nb, order="F")
+            r = ref[o:o + nb * nb].reshape(nb, nb, order="F")
+            assert np.linalg.norm(np.triu(g - r)) <= 1e-11 * np.linalg.norm(np.triu(r))
+            assert np.all(g[np.tril_indices(nb, -1)] == SENT)
+
+
+@pytest.mark.parametrize("name,mode", [("potrf_1024x64", "fp32_refined"),
+                                       ("potrf_8192xLU8-256", "bf16_refined"),
+                                       ("potrf_8192xLU8-256", "fp32_refined"),
+                                       ("trsyl_4096xU4-128", "fp32_refined"),
                                        ("trsyl_4096xU4-128", "tf32_refined"),
                                        ("trlyap_2048x128", "tf32_refined"),
                                        ("trlyap_2048x128", "fp32_refined")])
