@@ -41,6 +41,12 @@
  * SS_REFINE_MAXIT steps ran.  The *_RAW modes stop after the low-precision
  * solve.  Refined and raw modes need workspace (see ss_workspace_size).
  *
+ * SS_MODE_AUTO solves each size bin in the (mode, cfg) pair given by
+ * ss_set_auto_table (the autotuner's or the learned selector's choice among
+ * FP64 and the refined modes, all of which meet the same accuracy); bins the
+ * table leaves unset run in SS_MODE_FP64 with the default configuration, and
+ * `cfg` is ignored.
+ *
  * Configurations (`cfg`).  cfg >= 0 selects a kernel configuration by id
  * (0 <= cfg < ss_config_count(op, mode)); cfg = SS_CFG_TABLE uses the per-size
  * table set with ss_set_config_table (the autotuner's or the learned
@@ -89,6 +95,7 @@ extern "C" {
 #define SS_MODE_TF32_RAW      5
 #define SS_MODE_BF16_RAW      6
 #define SS_NUM_MODES          7
+#define SS_MODE_AUTO          7   /* per-size (mode, cfg) table, see ss_set_auto_table */
 
 /* configuration selectors */
 #define SS_CFG_DEFAULT (-1)
@@ -135,7 +142,8 @@ int trlyap_l(int batch, int max_n, const int *d_n,
 
 /*
  * Workspace, in bytes, that a call of `op` with this batch, max_n and mode
- * needs (the bound assumes every instance has order max_n).  Returns 0 and
+ * needs (the bound assumes every instance has order max_n; for SS_MODE_AUTO
+ * it covers whichever modes the table may choose).  Returns 0 and
  * writes *bytes, or a negative argument error.
  */
 int ss_workspace_size(int op, int batch, int max_n, int mode, size_t *bytes);
@@ -176,6 +184,46 @@ int trsyl_lu_noalloc(int batch, int max_n, const int *d_n,
                      const double *const *d_U, const int *d_ldu,
                      const double *const *d_C, const int *d_ldc,
                      double *const *d_X, const int *d_ldx, int *d_info, void *stream);
+
+/*
+ * Per-size (mode, cfg) table used by mode = SS_MODE_AUTO: bin k (bin(n) as for
+ * ss_set_config_table) runs in mode_by_bin[k] (SS_MODE_FP64 or one of the
+ * *_REFINED modes; -1 = unset) with configuration cfg_by_bin[k] (-1 = that
+ * mode's default).  nbins = 0 clears the table.  Host-side state, copied.
+ */
+int ss_set_auto_table(int op, int nbins, const int *mode_by_bin, const int *cfg_by_bin);
+
+/*
+ * The learned selector's cost model (the paper's "Limitations and future
+ * work" paragraph: replace the autotuning loops with a model-based approach).
+ * A fixed MLP  h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), y = W3 h2 + b3
+ * maps SS_MLP_IN features (op one-hot [3], log2 n, log2 batch, mode one-hot
+ * [FP64, FP32, TF32, BF16 refined]) to SS_MLP_OUT predicted log2 run times,
+ * one per kernel configuration id.  Parameters: one device float array of
+ * SS_MLP_PARAMS values laid out W1 (H x IN, row-major), b1, W2 (H x H), b2,
+ * W3 (OUT x H), b3.  All arrays are device pointers, row-major per row.
+ *
+ * ss_mlp_forward: y[nrows x OUT] = MLP(x[nrows x IN]).
+ * ss_mlp_grad: loss = sum mask (y - t)^2 / mask_total and its gradient with
+ *   respect to every parameter (written to d_grad[SS_MLP_PARAMS], loss to
+ *   *d_loss); mask_total must be the sum of the mask (> 0).  Needs
+ *   ss_mlp_workspace_size(nrows) bytes of workspace.  Deterministic.
+ * ss_mlp_adam: one Adam step (bias-corrected, step >= 1) updating d_params
+ *   and the moment arrays d_m, d_v (each SS_MLP_PARAMS floats, zero at start).
+ * Return 0, -k for an invalid argument k, or SS_ERR_CUDA.
+ */
+#define SS_MLP_IN 9
+#define SS_MLP_HIDDEN 64
+#define SS_MLP_OUT 8
+#define SS_MLP_PARAMS (SS_MLP_HIDDEN * SS_MLP_IN + SS_MLP_HIDDEN + SS_MLP_HIDDEN * SS_MLP_HIDDEN + \
+                       SS_MLP_HIDDEN + SS_MLP_OUT * SS_MLP_HIDDEN + SS_MLP_OUT)
+int ss_mlp_workspace_size(int nrows, size_t *bytes);
+int ss_mlp_forward(const float *d_params, int nrows, const float *d_x, float *d_y, void *stream);
+int ss_mlp_grad(const float *d_params, int nrows, const float *d_x, const float *d_t,
+                const float *d_mask, float mask_total, float *d_grad, float *d_loss,
+                void *d_work, size_t work_bytes, void *stream);
+int ss_mlp_adam(float *d_params, const float *d_grad, float *d_m, float *d_v, int step, float lr,
+                float beta1, float beta2, float eps, void *stream);
 
 /* Library version. */
 int ss_version(void);

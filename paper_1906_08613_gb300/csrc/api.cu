@@ -29,13 +29,23 @@ int host_bin(int n) { int k = 0; while ((1 << k) < n) ++k; return k; }
 
 bool valid_op(int op) { return op == SS_OP_POTRF || op == SS_OP_TRSYL || op == SS_OP_TRLYAP; }
 bool valid_mode(int m) { return m >= 0 && m < SS_NUM_MODES; }
+bool valid_call_mode(int m) { return valid_mode(m) || m == SS_MODE_AUTO; }
+bool refined_or_fp64(int m)
+{
+    return m == SS_MODE_FP64 || m == SS_MODE_FP32_REFINED || m == SS_MODE_TF32_REFINED ||
+           m == SS_MODE_BF16_REFINED;
+}
 
 struct TableState {
     std::mutex mu;
     int table[3][SS_NUM_MODES][NUM_BINS];
+    int auto_mode[3][NUM_BINS];
+    int auto_cfg[3][NUM_BINS];
     TableState()
     {
         for (auto &a : table) for (auto &b : a) for (int &c : b) c = -1;
+        for (auto &a : auto_mode) for (int &c : a) c = -1;
+        for (auto &a : auto_cfg) for (int &c : a) c = -1;
     }
 };
 TableState &tables()
@@ -122,6 +132,14 @@ int sm_count()
 
 static long long scratch_per_n2(int op, int mode)
 {
+    if (mode == SS_MODE_AUTO) {
+        long long m = 0;
+        for (int md = 1; md < SS_NUM_MODES; ++md) {
+            const long long v = mixed_scratch_per_n2(op, md);
+            if (v > m) m = v;
+        }
+        return m;
+    }
     return mode == SS_MODE_FP64 ? 0 : mixed_scratch_per_n2(op, mode);
 }
 
@@ -164,38 +182,48 @@ namespace {
 int run(int op, int batch, int max_n, const Operands &o, int mode, int cfg, void *d_work,
         size_t work_bytes, void *stream, int arg_mode, int arg_work)
 {
-    if (!valid_mode(mode)) return -arg_mode;
-    const int ncfg = config_count(op, mode);
+    if (!valid_call_mode(mode)) return -arg_mode;
+    const bool autom = mode == SS_MODE_AUTO;
+    const int ncfg = autom ? 1 : config_count(op, mode);
     if (ncfg <= 0) return -arg_mode;
-    if (!(cfg == SS_CFG_DEFAULT || cfg == SS_CFG_TABLE || (cfg >= 0 && cfg < ncfg))) return -(arg_mode + 1);
+    if (!autom && !(cfg == SS_CFG_DEFAULT || cfg == SS_CFG_TABLE || (cfg >= 0 && cfg < ncfg)))
+        return -(arg_mode + 1);
     if (batch == 0) return 0;
     const size_t need = workspace_bytes(op, batch, max_n, mode);
     if (d_work == nullptr) return -arg_work;
     if (work_bytes < need) return -(arg_work + 1);
 
-    // Configuration per size bin, then launch groups = runs of equal configs.
-    int by_bin[NUM_BINS];
+    // (mode, configuration) per size bin, then launch groups = runs of equal pairs.
+    int mode_of_bin[NUM_BINS], by_bin[NUM_BINS];
     const int top = host_bin(max_n > 0 ? max_n : 1);
     for (int k = 0; k < NUM_BINS; ++k) {
-        int c = -1;
-        if (cfg >= 0) c = cfg;
-        else if (cfg == SS_CFG_TABLE) {
+        int md = mode, c = -1;
+        if (autom) {
+            std::lock_guard<std::mutex> g(tables().mu);
+            md = tables().auto_mode[op][k];
+            c = tables().auto_cfg[op][k];
+            if (md < 0 || !refined_or_fp64(md) || config_count(op, md) <= 0) { md = SS_MODE_FP64; c = -1; }
+        } else if (cfg >= 0) {
+            c = cfg;
+        } else if (cfg == SS_CFG_TABLE) {
             std::lock_guard<std::mutex> g(tables().mu);
             c = tables().table[op][mode][k];
         }
-        if (c < 0 || c >= ncfg) c = config_default(op, mode, max_n);
+        if (c < 0 || c >= config_count(op, md)) c = config_default(op, md, max_n);
+        mode_of_bin[k] = md;
         by_bin[k] = c;
     }
     int group_of_bin[NUM_BINS];
-    int group_cfg[MAX_GROUPS];
+    int group_cfg[MAX_GROUPS], group_mode[MAX_GROUPS];
     int ngroups = 0;
     for (int k = NUM_BINS - 1; k >= 0; --k) {
         if (k > top) { group_of_bin[k] = -1; continue; }
-        if (ngroups > 0 && group_cfg[ngroups - 1] == by_bin[k]) {
+        if (ngroups > 0 && group_cfg[ngroups - 1] == by_bin[k] && group_mode[ngroups - 1] == mode_of_bin[k]) {
             group_of_bin[k] = ngroups - 1;
         } else {
             if (ngroups == MAX_GROUPS) return SS_ERR_CUDA;
             group_cfg[ngroups] = by_bin[k];
+            group_mode[ngroups] = mode_of_bin[k];
             group_of_bin[k] = ngroups++;
         }
     }
@@ -218,8 +246,8 @@ int run(int op, int batch, int max_n, const Operands &o, int mode, int cfg, void
     const bool prof = profile_pair(&ev0, &ev1);
     if (prof) cudaEventRecord(ev0, st);
     for (int g = 0; g < ngroups; ++g) {
-        Launch l{g, group_cfg[g], mode, max_n, batch};
-        if (mode == SS_MODE_FP64) {
+        Launch l{g, group_cfg[g], group_mode[g], max_n, batch};
+        if (l.mode == SS_MODE_FP64) {
             if (op == SS_OP_POTRF) e = launch_potrf_fp64(o, s, l, st);
             else e = launch_syl_fp64(o, s, l, st, op == SS_OP_TRLYAP);
         } else {
@@ -301,7 +329,7 @@ int ss_workspace_size(int op, int batch, int max_n, int mode, size_t *bytes)
     if (!valid_op(op)) return -1;
     if (batch < 0) return -2;
     if (max_n < 0 || max_n > SS_MAX_N) return -3;
-    if (!valid_mode(mode)) return -4;
+    if (!valid_call_mode(mode)) return -4;
     if (!bytes) return -5;
     *bytes = workspace_bytes(op, batch, max_n, mode);
     return 0;
@@ -337,6 +365,26 @@ int ss_set_config_table(int op, int mode, int nbins, const int *cfg_by_bin)
         if (cfg_by_bin[k] < -1 || cfg_by_bin[k] >= ncfg) return -4;
     std::lock_guard<std::mutex> g(tables().mu);
     for (int k = 0; k < NUM_BINS; ++k) tables().table[op][mode][k] = k < nbins ? cfg_by_bin[k] : -1;
+    return 0;
+}
+
+int ss_set_auto_table(int op, int nbins, const int *mode_by_bin, const int *cfg_by_bin)
+{
+    if (!valid_op(op)) return -1;
+    if (nbins < 0 || nbins > NUM_BINS) return -2;
+    if (nbins > 0 && !mode_by_bin) return -3;
+    if (nbins > 0 && !cfg_by_bin) return -4;
+    for (int k = 0; k < nbins; ++k) {
+        const int md = mode_by_bin[k];
+        if (md == -1) continue;
+        if (!refined_or_fp64(md) || config_count(op, md) <= 0) return -3;
+        if (cfg_by_bin[k] < -1 || cfg_by_bin[k] >= config_count(op, md)) return -4;
+    }
+    std::lock_guard<std::mutex> g(tables().mu);
+    for (int k = 0; k < NUM_BINS; ++k) {
+        tables().auto_mode[op][k] = k < nbins ? mode_by_bin[k] : -1;
+        tables().auto_cfg[op][k] = k < nbins ? cfg_by_bin[k] : -1;
+    }
     return 0;
 }
 

@@ -1,0 +1,224 @@
+"""Learned selector: an MLP cost model that predicts, for an (operation, n,
+batch, precision mode) bucket, the run time of every kernel configuration, so
+that the fastest (mode, configuration) can be chosen without timing them.
+
+The paper names this as future work: replacing the autotuning loops with a
+model-based approach ("Limitations and future work" paragraph).  The network
+and its training run in the library's CUDA kernels (``ss_mlp_forward``,
+``ss_mlp_grad``, ``ss_mlp_adam``); this module only encodes features, moves
+arrays and picks the argmin.  The exhaustive autotuner (``tune.py``) produces
+the training table, stays the fallback, and judges the selector's regret.
+
+Features (SS_MLP_IN = 9): op one-hot (potrf, trsyl, trlyap), log2(n)/9,
+log2(batch)/14, mode one-hot (fp64, fp32_refined, tf32_refined, bf16_refined).
+Targets: log2(milliseconds) per configuration id (SS_MLP_OUT = 8 slots, masked
+to the configurations the mode has).
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+import numpy as np
+
+from . import smallsolve as ss
+from . import tune
+
+OP_ORDER = ("potrf", "trsyl", "trlyap")
+MODE_ORDER = ("fp64", "fp32_refined", "tf32_refined", "bf16_refined")
+TRAIN_MAX_BIN = 7          # n <= 128: the size range of the tuned workloads
+
+
+def features(op: str, n: float, batch: float, mode: str) -> np.ndarray:
+    f = np.zeros(ss.MLP_IN, dtype=np.float32)
+    f[OP_ORDER.index(op)] = 1.0
+    f[3] = math.log2(max(n, 1.0)) / 9.0
+    f[4] = math.log2(max(batch, 1.0)) / 14.0
+    f[5 + MODE_ORDER.index(mode)] = 1.0
+    return f
+
+
+def bin_center(k: int) -> float:
+    lo, hi = tune.bin_range(k)
+    return math.sqrt(lo * hi)
+
+
+def dataset(entries, bins=None):
+    """Rows (features, log2-ms targets, mask, keys) from tuning entries."""
+    rows = {}
+    for e in entries:
+        if e.get("info_nonzero", 0) or e["mode"] not in MODE_ORDER:
+            continue
+        if bins is not None and e["bin"] not in bins:
+            continue
+        key = (e["op"], e["bin"], e["batch"], e["mode"])
+        rows.setdefault(key, {})[e["cfg"]] = e["ms"]
+    keys = sorted(rows)
+    X = np.zeros((len(keys), ss.MLP_IN), dtype=np.float32)
+    T = np.zeros((len(keys), ss.MLP_OUT), dtype=np.float32)
+    M = np.zeros((len(keys), ss.MLP_OUT), dtype=np.float32)
+    for i, key in enumerate(keys):
+        op, k, batch, mode = key
+        X[i] = features(op, bin_center(k), batch, mode)
+        for c, ms in rows[key].items():
+            if c < ss.MLP_OUT:
+                T[i, c] = math.log2(max(ms, 1e-6))
+                M[i, c] = 1.0
+    return X, T, M, keys
+
+
+def init_params(seed: int = 0) -> np.ndarray:
+    """He-style initialisation in the library's parameter layout."""
+    rng = np.random.default_rng(seed)
+    H, IN, OUT = ss.MLP_HIDDEN, ss.MLP_IN, ss.MLP_OUT
+    parts = [rng.standard_normal(H * IN) * math.sqrt(2.0 / IN), np.zeros(H),
+             rng.standard_normal(H * H) * math.sqrt(2.0 / H), np.zeros(H),
+             rng.standard_normal(OUT * H) * math.sqrt(1.0 / H), np.zeros(OUT)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+class Selector:
+    def __init__(self, params=None, device="cuda"):
+        self.params = init_params() if params is None else np.asarray(params, dtype=np.float32)
+        assert self.params.shape == (ss.MLP_PARAMS,)
+        self.device = device
+        self.meta = {}
+
+    # ----------------------------------------------------------- training
+    def train(self, X, T, M, steps=3000, lr=3e-3, log_every=0, log=print):
+        """Adam on the masked MSE, on the GPU; returns the loss history."""
+        import torch
+        dev = torch.device(self.device)
+        t = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device=dev)
+        P, dX, dT, dM = t(self.params), t(X), t(T), t(M)
+        G = torch.zeros_like(P)
+        m1 = torch.zeros_like(P)
+        m2 = torch.zeros_like(P)
+        L = torch.zeros(1, dtype=torch.float32, device=dev)
+        rows = int(X.shape[0])
+        wb = ss.ss_mlp_workspace_size(rows)
+        W = torch.empty(max(wb, 4), dtype=torch.uint8, device=dev)
+        total = float(M.sum())
+        hist = []
+        for step in range(1, steps + 1):
+            ss.ss_mlp_grad(P.data_ptr(), rows, dX.data_ptr(), dT.data_ptr(), dM.data_ptr(), total,
+                           G.data_ptr(), L.data_ptr(), W.data_ptr(), wb)
+            ss.ss_mlp_adam(P.data_ptr(), G.data_ptr(), m1.data_ptr(), m2.data_ptr(), step, lr)
+            if step == 1 or step % 50 == 0 or step == steps:
+                hist.append((step, float(L.item())))
+                if log_every and step % log_every == 0:
+                    log(f"step {step} loss {hist[-1][1]:.5f}")
+        torch.cuda.synchronize(dev)
+        self.params = P.cpu().numpy()
+        return hist
+
+    # ---------------------------------------------------------- inference
+    def predict(self, X):
+        """log2-ms predictions [rows x SS_MLP_OUT] by the CUDA forward kernel."""
+        import torch
+        dev = torch.device(self.device)
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        P = torch.as_tensor(self.params, device=dev)
+        dX = torch.as_tensor(X, device=dev)
+        Y = torch.zeros((X.shape[0], ss.MLP_OUT), dtype=torch.float32, device=dev)
+        if X.shape[0]:
+            ss.ss_mlp_forward(P.data_ptr(), X.shape[0], dX.data_ptr(), Y.data_ptr())
+        torch.cuda.synchronize(dev)
+        return Y.cpu().numpy()
+
+    def choose_many(self, queries):
+        """queries: list of (op, n, batch) -> list of (mode, cfg, predicted ms)."""
+        rows, idx = [], []
+        for qi, (op, n, batch) in enumerate(queries):
+            for mode in MODE_ORDER:
+                cnt = ss.ss_config_count(ss.OPS[op], ss.MODES[mode])
+                if cnt <= 0:
+                    continue
+                rows.append(features(op, n, batch, mode))
+                idx.append((qi, mode, cnt))
+        Y = self.predict(np.array(rows)) if rows else np.zeros((0, ss.MLP_OUT))
+        best = [None] * len(queries)
+        for (qi, mode, cnt), y in zip(idx, Y):
+            c = int(np.argmin(y[:cnt]))
+            if best[qi] is None or y[c] < best[qi][2]:
+                best[qi] = (mode, c, float(y[c]))
+        return [(m, c, 2.0 ** v) for (m, c, v) in best]
+
+    def auto_table(self, op: str, batch, nbins: int = ss.NUM_BINS):
+        """Per-bin (mode ids, cfg ids) for ss_set_auto_table.  `batch` is the
+        number of instances per size bin (a list, or one number for all);
+        bins with no instances keep the library default (-1)."""
+        counts = list(batch) if hasattr(batch, "__len__") else [batch] * nbins
+        want = [k for k in range(nbins) if counts[k] > 0]
+        ch = self.choose_many([(op, bin_center(k), counts[k]) for k in want])
+        modes, cfgs = [-1] * nbins, [-1] * nbins
+        for k, (m, c, _) in zip(want, ch):
+            modes[k], cfgs[k] = ss.MODES[m], c
+        return modes, cfgs
+
+    def install(self, op: str, batch):
+        modes, cfgs = self.auto_table(op, batch)
+        ss.ss_set_auto_table(ss.OPS[op], modes, cfgs)
+        return modes, cfgs
+
+    # ------------------------------------------------------------ storage
+    def save(self, path: str, **meta):
+        np.save(path + ".npy", self.params)
+        with open(path + ".json", "w") as f:
+            json.dump({"params": os.path.basename(path) + ".npy", "n_params": int(self.params.size),
+                       "features": "op one-hot, log2(n)/9, log2(batch)/14, mode one-hot",
+                       "op_order": OP_ORDER, "mode_order": MODE_ORDER, **meta}, f, indent=1)
+
+    @classmethod
+    def load(cls, path: str, device="cuda"):
+        s = cls(np.load(path + ".npy"), device=device)
+        with open(path + ".json") as f:
+            s.meta = json.load(f)
+        return s
+
+
+def counts_by_bin(n, nbins: int = ss.NUM_BINS):
+    """Number of instances of each order in each size bin."""
+    c = [0] * nbins
+    for v in np.asarray(n).ravel():
+        c[ss.size_bin(int(v))] += 1
+    return c
+
+
+def regret_report(choices, entries, buckets):
+    """For each bucket (op, bin, batch): the measured ms of the chosen
+    (mode, cfg), of the exhaustive best and of the FP64 default; summary of
+    regret (chosen / best - 1) and gain over the default (default / chosen)."""
+    best = tune.best_per_bucket(entries)
+    out = []
+    for (op, k, batch), (mode, cfg) in zip(buckets, choices):
+        key = (op, k, batch)
+        if key not in best:
+            continue
+        t_c = tune.lookup(entries, op, k, batch, mode, cfg)
+        t_b = best[key][2]
+        dflt = default_fp64_cfg(1 << k)
+        t_d = tune.lookup(entries, op, k, batch, "fp64", dflt)
+        if t_c is None or t_d is None:
+            continue
+        out.append(dict(op=op, bin=k, batch=batch, mode=mode, cfg=cfg, ms=t_c, best_ms=t_b,
+                        best=best[key][:2], default_ms=t_d, regret=t_c / t_b - 1.0, gain=t_d / t_c))
+    if not out:
+        return {"buckets": 0}
+    return {"buckets": len(out),
+            "mean_regret": float(np.mean([o["regret"] for o in out])),
+            "max_regret": float(np.max([o["regret"] for o in out])),
+            "geomean_gain_over_default": float(np.exp(np.mean([math.log(o["gain"]) for o in out]))),
+            "rows": out}
+
+
+def default_fp64_cfg(max_n: int) -> int:
+    """The library's built-in FP64 default (SS_CFG_DEFAULT) for a given max n."""
+    if max_n <= 8:
+        return 0
+    if max_n <= 16:
+        return 1
+    if max_n <= 32:
+        return 2
+    return 3

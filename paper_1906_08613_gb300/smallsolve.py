@@ -32,6 +32,9 @@ MODE_BF16_RAW = 6
 MODES = {"fp64": 0, "fp32_refined": 1, "tf32_refined": 2, "bf16_refined": 3,
          "fp32_raw": 4, "tf32_raw": 5, "bf16_raw": 6}
 
+MODE_AUTO = 7
+REFINED_MODES = (MODE_FP32_REFINED, MODE_TF32_REFINED, MODE_BF16_REFINED)
+
 CFG_DEFAULT = -1
 CFG_TABLE = -2
 
@@ -40,6 +43,9 @@ ERR_SCRATCH_LIMIT = -101
 INFO_BAD_SIZE = -1
 INFO_NO_WORK = -2
 MAX_N = 4096
+MLP_IN, MLP_HIDDEN, MLP_OUT = 9, 64, 8
+MLP_PARAMS = MLP_HIDDEN * MLP_IN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + \
+    MLP_OUT * MLP_HIDDEN + MLP_OUT
 NUM_BINS = 13
 REFINE_TOL = 1e-13
 REFINE_MAXIT = 10
@@ -79,6 +85,17 @@ def lib():
             L.ss_config_describe.restype = i
             L.ss_set_config_table.argtypes = [i, i, i, ip]
             L.ss_set_config_table.restype = i
+            L.ss_set_auto_table.argtypes = [i, i, ip, ip]
+            L.ss_set_auto_table.restype = i
+            fl = ctypes.c_float
+            L.ss_mlp_workspace_size.argtypes = [i, ctypes.POINTER(sz)]
+            L.ss_mlp_workspace_size.restype = i
+            L.ss_mlp_forward.argtypes = [vp, i, vp, vp, vp]
+            L.ss_mlp_forward.restype = i
+            L.ss_mlp_grad.argtypes = [vp, i, vp, vp, vp, fl, vp, vp, vp, sz, vp]
+            L.ss_mlp_grad.restype = i
+            L.ss_mlp_adam.argtypes = [vp, vp, vp, vp, i, fl, fl, fl, fl, vp]
+            L.ss_mlp_adam.restype = i
             L.ss_version.argtypes = []
             L.ss_version.restype = i
             L.ss_launch_count.argtypes = []
@@ -147,6 +164,36 @@ def ss_config_describe(op, mode, cfg):
 def ss_set_config_table(op, mode, cfg_by_bin) -> None:
     arr = (ctypes.c_int * max(1, len(cfg_by_bin)))(*[int(c) for c in cfg_by_bin])
     _check(lib().ss_set_config_table(op, mode, len(cfg_by_bin), arr), "ss_set_config_table")
+
+
+def ss_set_auto_table(op, mode_by_bin, cfg_by_bin) -> None:
+    """Per-size-bin (mode, cfg) choices for MODE_AUTO (empty lists clear)."""
+    nb = len(mode_by_bin)
+    assert len(cfg_by_bin) == nb
+    ma = (ctypes.c_int * max(1, nb))(*[int(m) for m in mode_by_bin])
+    ca = (ctypes.c_int * max(1, nb))(*[int(c) for c in cfg_by_bin])
+    _check(lib().ss_set_auto_table(op, nb, ma, ca), "ss_set_auto_table")
+
+
+def ss_mlp_workspace_size(nrows) -> int:
+    out = ctypes.c_size_t(0)
+    _check(lib().ss_mlp_workspace_size(nrows, ctypes.byref(out)), "ss_mlp_workspace_size")
+    return int(out.value)
+
+
+def ss_mlp_forward(d_params, nrows, d_x, d_y, stream=0):
+    return _check(lib().ss_mlp_forward(d_params, nrows, d_x, d_y, stream or None), "ss_mlp_forward")
+
+
+def ss_mlp_grad(d_params, nrows, d_x, d_t, d_mask, mask_total, d_grad, d_loss, d_work, work_bytes,
+                stream=0):
+    return _check(lib().ss_mlp_grad(d_params, nrows, d_x, d_t, d_mask, float(mask_total), d_grad,
+                                    d_loss, d_work, work_bytes, stream or None), "ss_mlp_grad")
+
+
+def ss_mlp_adam(d_params, d_grad, d_m, d_v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=0):
+    return _check(lib().ss_mlp_adam(d_params, d_grad, d_m, d_v, step, lr, beta1, beta2, eps,
+                                    stream or None), "ss_mlp_adam")
 
 
 def ss_version() -> int:

@@ -141,3 +141,30 @@ def test_workspace_too_small_is_reported():
                      db.info.data_ptr(), mode=ss.MODE_FP32_REFINED, d_work=db.work.data_ptr(),
                      work_bytes=short, check=False)
     assert rc == -16          # shorter than the bound: rejected on the host
+
+
+@pytest.mark.parametrize("op", ["potrf", "trsyl", "trlyap"])
+def test_auto_mode_mixes_modes_per_size_bin(op):
+    """SS_MODE_AUTO with a different (mode, cfg) in every size bin (as the
+    selector sets it) still meets the FP64 gate on every instance."""
+    n = inputs.sizes_uniform(200, 1, 200, seed=37)
+    pk = inputs.make_batch(op, n, seed=37)
+    ref, rinfo = oracle_batch(op, pk)
+    o = ss.OPS[op]
+    cycle = [ss.MODE_FP64, ss.MODE_FP32_REFINED, ss.MODE_TF32_REFINED, ss.MODE_BF16_REFINED]
+    modes, cfgs = [], []
+    for k in range(ss.NUM_BINS):
+        m = cycle[k % 4]
+        modes.append(m)
+        cfgs.append(k % ss.ss_config_count(o, m))
+    ss.ss_set_auto_table(o, modes, cfgs)
+    try:
+        from paper_1906_08613_gb300.device import DeviceBatch
+        db = DeviceBatch(pk.n, pk.off, pk.ops, op, x_fill=SENT)
+        db.solve(mode=ss.MODE_AUTO)
+        torch.cuda.synchronize()
+        x, info = db.x_host(), db.info_host()
+    finally:
+        ss.ss_set_auto_table(o, [], [])
+    assert np.array_equal(info, rinfo)
+    assert_parity(op, pk, x, ref, sentinel=SENT)

@@ -1,0 +1,85 @@
+"""Host logic of the autotuner and the learned selector, and what the trained
+selector gains, evaluated on the tuning database measured on a GB300 (no GPU
+needed: the committed network is evaluated with the oracle's FP64 forward)."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import mlp
+from paper_1906_08613_gb300 import selector as sel
+from paper_1906_08613_gb300 import smallsolve as ss
+from paper_1906_08613_gb300 import tune
+
+DATA = os.path.join(os.path.dirname(sel.__file__), "data")
+DB = os.path.join(DATA, "tune_gb300.json")
+WEIGHTS = os.path.join(DATA, "selector_gb300")
+
+
+def test_features_and_bins():
+    f = sel.features("trlyap", 128, 2048, "bf16_refined")
+    assert list(f[:3]) == [0, 0, 1] and list(f[5:]) == [0, 0, 0, 1]
+    assert math.isclose(f[3], 7 / 9, rel_tol=1e-6) and math.isclose(f[4], 11 / 14, rel_tol=1e-6)
+    assert tune.bin_range(7) == (65, 128) and tune.bin_range(0) == (1, 1)
+    for n in (1, 2, 3, 64, 65, 128, 129, 4096):
+        k = ss.size_bin(n)
+        lo, hi = tune.bin_range(k)
+        assert lo <= n <= hi
+    assert sel.counts_by_bin([1, 3, 4, 100, 128]) [:8] == [1, 0, 2, 0, 0, 0, 0, 2]
+
+
+def synthetic_entries():
+    # fp64 cfg 1 fastest in small bins, cfg 3 in large; one refined mode wins bin 6.
+    out = []
+    for k in range(2, 8):
+        for mode, ncfg in (("fp64", 5), ("fp32_refined", 3)):
+            for c in range(ncfg):
+                ms = 1.0 + abs(c - (1 if k < 5 else 3)) + (0.5 if mode != "fp64" else 0.0)
+                if k == 6 and mode == "fp32_refined" and c == 2:
+                    ms = 0.5
+                out.append(dict(op="trsyl", bin=k, batch=256, mode=mode, cfg=c, ms=ms, info_nonzero=0))
+    return out
+
+
+def test_dataset_exhaustive_table_and_regret():
+    ent = synthetic_entries()
+    X, T, M, keys = sel.dataset(ent)
+    assert X.shape == (12, ss.MLP_IN) and M.sum() == 6 * 8
+    modes, cfgs = tune.exhaustive_table(ent, "trsyl", 256)
+    assert modes[6] == ss.MODE_FP32_REFINED and cfgs[6] == 2
+    assert modes[3] == ss.MODE_FP64 and cfgs[3] == 1 and cfgs[7] == 3 and modes[9] == -1
+    buckets = [("trsyl", k, 256) for k in range(2, 8)]
+    rep = sel.regret_report([("fp64", 1)] * 6, ent, buckets)
+    assert rep["buckets"] == 6 and rep["max_regret"] > 0 and rep["mean_regret"] > 0
+
+
+def choices_with_oracle_forward(params, buckets):
+    out = []
+    for op, k, batch in buckets:
+        best = None
+        for mode in sel.MODE_ORDER:
+            cnt = ss.ss_config_count(ss.OPS[op], ss.MODES[mode])
+            y, _ = mlp.forward(params, sel.features(op, sel.bin_center(k), batch, mode)[None, :])
+            c = int(np.argmin(y[0, :cnt]))
+            if best is None or y[0, c] < best[2]:
+                best = (mode, c, y[0, c])
+        out.append(best[:2])
+    return out
+
+
+@pytest.mark.skipif(not os.path.exists(DB), reason="no tuning database")
+def test_trained_selector_gain_and_regret_on_measured_gb300_timings():
+    entries = tune.load(DB)["entries"]
+    params = np.load(WEIGHTS + ".npy").astype(np.float64)
+    held = sorted({(e["op"], e["bin"], e["batch"]) for e in entries if e["bin"] > sel.TRAIN_MAX_BIN})
+    train = sorted({(e["op"], e["bin"], e["batch"]) for e in entries if e["bin"] <= sel.TRAIN_MAX_BIN})
+    r_held = sel.regret_report(choices_with_oracle_forward(params, held), entries, held)
+    r_train = sel.regret_report(choices_with_oracle_forward(params, train), entries, train)
+    # The network never saw the held-out sizes (n > 128); it must still beat
+    # the fixed FP64 default and stay near the exhaustive search.
+    assert r_held["buckets"] == len(held) > 0
+    assert r_held["geomean_gain_over_default"] >= 1.0
+    assert r_held["mean_regret"] <= 0.15
+    assert r_train["geomean_gain_over_default"] >= 1.0
+    assert r_train["mean_regret"] <= 0.10
