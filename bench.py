@@ -7,8 +7,16 @@ is one batched solve of the whole workload.  Inputs are seeded synthetic data
 (see paper_1906_08613_gb300/inputs.py); the operand buffers are larger than
 the 129 MB L2, so no flush is needed between steps.
 
+The headline path (``--path learned``, the default) is SS_MODE_AUTO driven by
+the trained selector: each size bin runs in the (precision mode, kernel
+configuration) the MLP cost model predicts fastest among FP64 and the refined
+modes, all of which meet the 1e-11 accuracy gate.  Plain FP64 (built-in
+default configuration, and the autotuner's best FP64 configuration per size
+bin) is timed in the same run for comparison.
+
 Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-        [--workload NAME] [--mode fp64|fp32_refined|...] [--cfg C]
+        [--workload NAME] [--path learned|mode] [--mode fp64|fp32_refined|...]
+        [--cfg C] [--graph]
 For N > 1 launch with torch.distributed.run; each rank solves its own copy of
 the workload (independent replicas, weak scaling, no collective on the data
 path).  ``--impl reference`` times the CPU oracle on the host cores instead.
@@ -191,6 +199,21 @@ def cpu_oracle_rate(op, pk, seconds: float, threads: int, indices=None):
     return done / el, done, el, out
 
 
+def launch_groups(table, max_n):
+    """Solve launches per call: runs of equal (mode, cfg) over the size bins
+    up to bin(max_n), from the largest bin down (one group without a table)."""
+    if not table:
+        return 1
+    from paper_1906_08613_gb300 import smallsolve as ss
+    pairs = list(zip(*table))[: ss.size_bin(max_n) + 1]
+    runs, prev = 0, None
+    for p in reversed(pairs):
+        if p != prev:
+            runs += 1
+            prev = p
+    return runs
+
+
 def sample_indices(pk, k, seed=7):
     rng = np.random.default_rng(seed)
     k = min(k, pk.batch)
@@ -246,8 +269,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="graft", choices=["graft", "reference"])
     ap.add_argument("--workload", default="trsyl_4096xU4-128")
+    ap.add_argument("--path", default="learned", choices=["learned", "mode"],
+                    help="learned: SS_MODE_AUTO with the trained selector's tables (default); "
+                         "mode: one explicit --mode/--cfg")
     ap.add_argument("--mode", default="fp64")
     ap.add_argument("--cfg", type=int, default=None)
+    ap.add_argument("--graph", action="store_true", help="replay each step from a captured CUDA graph")
+    ap.add_argument("--no-compare", action="store_true", help="skip the plain-FP64 comparison runs")
     ap.add_argument("--seed", type=int, default=1234)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-sample", type=int, default=256)
@@ -271,8 +299,18 @@ def main():
     name = args.workload
     op = inputs.WORKLOADS[name]["op"]
     pk = inputs.make_workload(name, seed=args.seed)
-    mode = ss.MODES[args.mode]
-    cfg = ss.CFG_DEFAULT if args.cfg is None else args.cfg
+    o = ss.OPS[op]
+    learned = args.path == "learned"
+    table = None
+    if learned:
+        from paper_1906_08613_gb300 import selector as sel
+        s_model = sel.Selector.load(os.path.join(ROOT, "paper_1906_08613_gb300", "data", "selector_gb300"),
+                                    device=str(dev))
+        table = s_model.install(op, sel.counts_by_bin(pk.n))
+        mode, cfg = ss.MODE_AUTO, ss.CFG_DEFAULT
+    else:
+        mode = ss.MODES[args.mode]
+        cfg = ss.CFG_DEFAULT if args.cfg is None else args.cfg
 
     db = DeviceBatch(pk.n, pk.off, pk.ops, op, device=dev)
     db.ensure_work(mode)
@@ -283,10 +321,19 @@ def main():
     def step():
         db.solve(mode=mode, cfg=cfg, stream=sh)
 
+    graph = None
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             step()
+        if args.graph:
+            stream.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=stream):
+                step()
+            for _ in range(2):
+                graph.replay()
     barrier(dist, dev)
+    run_step = graph.replay if graph is not None else step
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -297,10 +344,12 @@ def main():
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     barrier(dist, dev)
+    if graph is not None:
+        ss.ss_profile_enable(False)     # events inside a graph are not re-recorded per replay
     with torch.cuda.stream(stream):
         e0.record(stream)
         for _ in range(args.steps):
-            step()
+            run_step()
         e1.record(stream)
     stream.synchronize()
     barrier(dist, dev)
@@ -310,6 +359,11 @@ def main():
     clk = clocks.stop()
     ms_total = e0.elapsed_time(e1)
     ms_total = max_over_ranks(dist, ms_total, dev)
+    if graph is not None:
+        # Launches and kernel time inside graph replays are not seen by the
+        # library's counters: one call launches 1 + (launch groups) kernels.
+        launches = args.steps * (1 + launch_groups(table, int(pk.n.max())))
+        kern_ms, kern_calls = ms_total, args.steps
     ms_step = ms_total / args.steps
     solves = sum_over_ranks(dist, float(pk.batch * args.steps), dev)
     value = solves / (ms_total * 1e-3)
@@ -345,6 +399,41 @@ def main():
     e2e_value = sum_over_ranks(dist, float(pk.batch * e2e_steps), dev) / (e2e_ms * 1e-3)
     x_gpu = host_x.numpy()
 
+    # Plain FP64 in the same run (the comparator): default configuration, and
+    # the autotuner's best FP64 configuration per size bin (FP64-only table).
+    compare = {}
+    if not args.no_compare:
+        from paper_1906_08613_gb300 import tune as tn
+        from paper_1906_08613_gb300 import selector as sel2
+        entries = tn.load(os.path.join(ROOT, "paper_1906_08613_gb300", "data", "tune_gb300.json"))["entries"]
+        fp_entries = [e for e in entries if e["mode"] == "fp64"]
+        fm, fc = tn.exhaustive_table(fp_entries, op, sel2.counts_by_bin(pk.n))
+        variants = [("fp64_default", ss.MODE_FP64, ss.CFG_DEFAULT, None),
+                    ("fp64_tuned", ss.MODE_AUTO, ss.CFG_DEFAULT, (fm, fc))]
+        saved = table
+        for label, md, cf, tab in variants:
+            if tab is not None:
+                ss.ss_set_auto_table(o, *tab)
+            db.ensure_work(md)
+            with torch.cuda.stream(stream):
+                for _ in range(3):
+                    db.solve(mode=md, cfg=cf, stream=sh)
+                c0 = torch.cuda.Event(enable_timing=True)
+                c1 = torch.cuda.Event(enable_timing=True)
+                reps = max(3, min(args.steps, 50))
+                c0.record(stream)
+                for _ in range(reps):
+                    db.solve(mode=md, cfg=cf, stream=sh)
+                c1.record(stream)
+            stream.synchronize()
+            cms = max_over_ranks(dist, c0.elapsed_time(c1) / reps, dev)
+            compare[label] = {"ms_per_step": cms,
+                              "value": sum_over_ranks(dist, float(pk.batch), dev) / (cms * 1e-3)}
+        if saved is not None:
+            ss.ss_set_auto_table(o, *saved)
+        else:
+            ss.ss_set_auto_table(o, [], [])
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -354,7 +443,7 @@ def main():
     roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
             "frac": achieved / FP64_PEAK_GFLOPS,
             "traffic": read_traffic(f"{op}_{args.mode}", name),
-            "kernel": f"{op} persistent solve kernel ({args.mode})",
+            "kernel": f"{op} persistent solve kernels ({'selector tables' if learned else args.mode})",
             "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (of derived; "
                            "a DFMA probe measured 1248 GFLOP/s)",
             "kernel_ms": kern_avg_ms, "algorithmic_bytes": Balg,
@@ -364,10 +453,13 @@ def main():
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
+        "dtype": "f64" if (not learned and args.mode == "fp64") else "f64 out (f64 / f32+df64-refined per size bin)",
+        "data": "synthetic",
         "config": {"workload": name, "op": op, "batch": pk.batch,
                    "sizes": f"n in [{int(pk.n.min())}, {int(pk.n.max())}], mean {float(pk.n.mean()):.1f}",
-                   "mode": args.mode, "cfg": cfg,
+                   "path": "mixed+learned (SS_MODE_AUTO, trained selector)" if learned else args.mode,
+                   "cfg": cfg, "graph": bool(args.graph),
+                   "selector_table": [[int(m), int(c)] for m, c in zip(*table)] if table else None,
                    "l2": f"operands {sum(int(v.numel()) * 8 for v in db.bufs.values()) / 1e6:.0f} MB > 129 MB L2; no flush"},
         "gflops_paper_count": F / (ms_step * 1e-3) / 1e9,
         "roofline": roof,
@@ -377,6 +469,9 @@ def main():
         "launches_per_step": launches / args.steps,
         "clocks": clk,
         "info_nonzero": int((info != 0).sum()),
+        "plain_fp64": compare or None,
+        "speedup_vs_plain_fp64_default": (value / compare["fp64_default"]["value"]) if compare else None,
+        "speedup_vs_plain_fp64_tuned": (value / compare["fp64_tuned"]["value"]) if compare else None,
     }
 
     if not args.no_cpu:

@@ -98,6 +98,22 @@ __device__ __forceinline__ float to_f(Src v) { return (float)v; }
 template <>
 __device__ __forceinline__ float to_f<double>(double v) { return d2f_trunc(v); }
 
+// Element conversion for staging: float (truncating FP64), float2 (double-float
+// split of an FP64 value).
+template <typename Elem, typename Src>
+__device__ __forceinline__ Elem cvt_elem(Src v);
+template <>
+__device__ __forceinline__ float cvt_elem<float, float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float cvt_elem<float, double>(double v) { return d2f_trunc(v); }
+template <>
+__device__ __forceinline__ float2 cvt_elem<float2, double>(double v)
+{
+    float2 r;
+    split_df(v, r.x, r.y);
+    return r;
+}
+
 // acc -= x * y in double-float (acc, x, y each hi + lo); the steps are never
 // contracted into FMAs, so the error-free transformations stay exact.
 __device__ __forceinline__ void df_msub(float &ah, float &al, float xh, float xl, float yh, float yl)
@@ -114,10 +130,12 @@ __device__ __forceinline__ void df_msub(float &ah, float &al, float xh, float xl
 
 // ------------------------------------------------------------------ tiles
 
+// Shared tiles: natural layout uses LD = B + 1; every tile slot holds
+// B * (B + 4) elements so the k-major micro-tile layouts fit as well.
 template <int B>
 struct FTile {
     static constexpr int LD = B + 1;
-    static constexpr int SZ = B * (B + 1);
+    static constexpr int SZ = B * (B + 4);
 };
 
 // Modes of staging a B x B tile from a column-major global matrix.
@@ -217,6 +235,105 @@ __device__ __forceinline__ void slot_update_df(float (&ah)[B * B / T], float (&a
                 df_msub(ah[r], al[r], a.x, a.y, b.x, b.y);
             }
         }
+    }
+}
+
+// ---------------------------------------- register micro-tiles (full blocks)
+//
+// For a full B x B output block each thread owns an MR x MC micro-tile at rows
+// r0 = (tid % TX) * MR and columns c0 = (tid / TX) * MC.  Operands are staged
+// "k-major": sOA[r + k*LDA] = op(A)(r, k) (LDA = B + 4, so a column of MR = 4
+// rows is one aligned 16-byte load) and sOB[c + k*LDB] = op(B)(k, c)
+// (LDB = B + 1), transposing at staging time when the operand is read
+// transposed.  One k step is MR/4 + MC loads for MR * MC FMAs.
+template <int B, int T>
+struct Micro {
+    static constexpr int P = (B * B) / T >= 1 ? (B * B) / T : 1;   // outputs per thread
+    static constexpr int MR = P >= 4 ? 4 : P;
+    static constexpr int MC = P / MR;
+    static constexpr int TX = B / MR;
+    static constexpr int TY = B / MC;
+    static constexpr int LDA = B + 4;
+    static constexpr int LDB = B + 1;
+    static constexpr bool OK = B * B >= T && TX * TY == T && TX * MR == B && TY * MC == B;
+    __device__ __forceinline__ static int r0() { return (threadIdx.x % TX) * MR; }
+    __device__ __forceinline__ static int c0() { return (threadIdx.x / TX) * MC; }
+};
+
+// Stage op(A) (rows x kk valid, zero elsewhere) k-major: sOA[r + k*LDA].
+// TRANS: op(A)(r, k) = G(k, r).
+template <int B, int T, bool TRANS, typename Src, typename Elem>
+__device__ __forceinline__ void stage_opA(Elem *S, const Src *G, long ldg, int rows, int kk)
+{
+    constexpr int LDA = Micro<B, T>::LDA;
+#pragma unroll 4
+    for (int e = threadIdx.x; e < B * B; e += T) {
+        const int x = e % B, y = e / B;      // fast index x walks memory
+        const int r = TRANS ? y : x, k = TRANS ? x : y;
+        Elem v{};
+        if (r < rows && k < kk) v = cvt_elem<Elem>(G[x + (long)y * ldg]);
+        S[r + k * LDA] = v;
+    }
+}
+
+// Stage op(B) (kk x cols valid) k-major: sOB[c + k*LDB].  TRANS: op(B)(k, c) = G(c, k).
+template <int B, int T, bool TRANS, typename Src, typename Elem>
+__device__ __forceinline__ void stage_opB(Elem *S, const Src *G, long ldg, int kk, int cols)
+{
+    constexpr int LDB = Micro<B, T>::LDB;
+#pragma unroll 4
+    for (int e = threadIdx.x; e < B * B; e += T) {
+        const int x = e % B, y = e / B;
+        const int k = TRANS ? y : x, c = TRANS ? x : y;
+        Elem v{};
+        if (k < kk && c < cols) v = cvt_elem<Elem>(G[x + (long)y * ldg]);
+        S[c + k * LDB] = v;
+    }
+}
+
+template <int B, int T>
+__device__ __forceinline__ void micro_update_f(float (&acc)[Micro<B, T>::MR][Micro<B, T>::MC],
+                                               const float *sOA, const float *sOB, int kk)
+{
+    using M = Micro<B, T>;
+    const int r0 = M::r0(), c0 = M::c0();
+#pragma unroll 4
+    for (int k = 0; k < kk; ++k) {
+        float a[M::MR], b[M::MC];
+        if constexpr (M::MR == 4) {
+            const float4 v = *reinterpret_cast<const float4 *>(sOA + r0 + k * M::LDA);
+            a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w;
+        } else {
+#pragma unroll
+            for (int i = 0; i < M::MR; ++i) a[i] = sOA[r0 + i + k * M::LDA];
+        }
+#pragma unroll
+        for (int j = 0; j < M::MC; ++j) b[j] = sOB[c0 + j + k * M::LDB];
+#pragma unroll
+        for (int i = 0; i < M::MR; ++i)
+#pragma unroll
+            for (int j = 0; j < M::MC; ++j) acc[i][j] = fmaf(-a[i], b[j], acc[i][j]);
+    }
+}
+
+template <int B, int T>
+__device__ __forceinline__ void micro_update_df(float (&ah)[Micro<B, T>::MR][Micro<B, T>::MC],
+                                                float (&al)[Micro<B, T>::MR][Micro<B, T>::MC],
+                                                const float2 *sOA, const float2 *sOB, int kk)
+{
+    using M = Micro<B, T>;
+    const int r0 = M::r0(), c0 = M::c0();
+#pragma unroll 1
+    for (int k = 0; k < kk; ++k) {
+        float2 a[M::MR], b[M::MC];
+#pragma unroll
+        for (int i = 0; i < M::MR; ++i) a[i] = sOA[r0 + i + k * M::LDA];
+#pragma unroll
+        for (int j = 0; j < M::MC; ++j) b[j] = sOB[c0 + j + k * M::LDB];
+#pragma unroll
+        for (int i = 0; i < M::MR; ++i)
+#pragma unroll
+            for (int j = 0; j < M::MC; ++j) df_msub(ah[i][j], al[i][j], a[i].x, a[i].y, b[j].x, b[j].y);
     }
 }
 
@@ -340,13 +457,19 @@ __device__ __forceinline__ float group_sum_f(float v, int split)
 }
 
 // Solve Lt Y + Y Ut = T in place (m x nn block in sT), multiplying by the
-// FP64-computed reciprocals Rg[i + j*ldr] (global, float).  UT: Ut is the
-// transpose of the lower-triangular sU.
+// FP64-computed reciprocals Rg[i + j*ldr] (global, float), which are first
+// staged into the shared tile sR so no step of the wavefront waits on a
+// global load.  UT: Ut is the transpose of the lower-triangular sU.
 template <int B, int T, bool UT>
 __device__ void syl_diag_f(const float *sL, const float *sU, float *sT, int m, int nn,
-                           const float *Rg, long ldr)
+                           const float *Rg, long ldr, float *sR)
 {
     constexpr int LD = FTile<B>::LD;
+    for (int e = threadIdx.x; e < m * nn; e += T) {
+        const int i = e % m, j = e / m;
+        sR[i + j * LD] = Rg[i + (long)j * ldr];
+    }
+    __syncthreads();
     for (int d = 0; d <= m + nn - 2; ++d) {
         const int ilo = max(0, d - nn + 1), ihi = min(d, m - 1);
         const int cnt = ihi - ilo + 1;
@@ -366,7 +489,7 @@ __device__ void syl_diag_f(const float *sL, const float *sU, float *sT, int m, i
                 }
             }
             s = group_sum_f(s, split);
-            if (act && part == 0) sT[i + j * LD] = (sT[i + j * LD] - s) * Rg[i + (long)j * ldr];
+            if (act && part == 0) sT[i + j * LD] = (sT[i + j * LD] - s) * sR[i + j * LD];
         }
         __syncthreads();
     }

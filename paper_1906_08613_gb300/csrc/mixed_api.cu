@@ -13,10 +13,10 @@ cudaError_t launch_mixed_potrf(int prec, int cfg, const Operands &o, const Sched
 namespace {
 
 // variant: bit 0 = residual (0 double-float on the FP32 pipe, 1 FP64 FMA);
-// bit 1 = solve (0 blocked lazy, block size `block`; 1 shared-memory-resident
-// eager wavefront for n <= block, blocked with B = 32 above).
-const Config kFp32Cfg[] = {{16, 64, 0},  {16, 128, 0},  {32, 128, 0},  {16, 128, 1},
-                           {32, 128, 1}, {128, 1024, 2}, {64, 512, 2}, {128, 1024, 3}};
+// bit 1 = solve (0 blocked lazy with block size `block`; 1 warp-block
+// wavefront, 32 x 32 blocks, one warp per block of a block anti-diagonal).
+const Config kFp32Cfg[] = {{16, 64, 0},  {16, 128, 0}, {32, 128, 0}, {16, 128, 1},
+                           {32, 128, 1}, {32, 128, 2}, {32, 64, 2},  {32, 256, 2}};
 const Config kTcCfg[] = {{16, 64, 0}, {32, 128, 0}, {16, 64, 1}, {32, 128, 1}};
 // Cholesky (blocked lazy factorization, then factor refinement).
 const Config kCholFp32Cfg[] = {{16, 64, 0}, {16, 128, 0}, {32, 128, 0}, {32, 128, 1}};
@@ -56,10 +56,12 @@ const Config *mixed_config_get(int op, int mode, int cfg)
 }
 
 // Scratch per instance in floats per n^2: the right-hand side / correction
-// and the reciprocal divisors.
+// and the reciprocal divisors; the warp-block variant also keeps FP32 copies
+// of L and U.
 long long mixed_scratch_per_n2(int op, int mode)
 {
-    return mixed_config_count(op, mode) > 0 ? 2 : 0;
+    if (mixed_config_count(op, mode) <= 0) return 0;
+    return (op != SS_OP_POTRF && mode_prec(mode) == 0) ? 4 : 2;
 }
 
 cudaError_t launch_mixed(int op, const Operands &o, const Sched &s, const Launch &l, cudaStream_t st)

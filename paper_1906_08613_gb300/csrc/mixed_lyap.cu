@@ -1,5 +1,5 @@
 // Instantiations of the mixed-precision Lyapunov kernels (see mixed_solver.cuh).
-#include "mixed_solver.cuh"
+#include "mixed_warp.cuh"
 
 namespace ss {
 
@@ -15,9 +15,9 @@ cudaError_t launch_mixed_trlyap(int prec, int cfg, const Operands &o, const Sche
         case 2: return launch_mixed_syl<32, 128, true, P_FP32, R_DF>(o, s, l, st, raw);
         case 3: return launch_mixed_syl<16, 128, true, P_FP32, R_FP64>(o, s, l, st, raw);
         case 4: return launch_mixed_syl<32, 128, true, P_FP32, R_FP64>(o, s, l, st, raw);
-        case 5: return launch_smem_syl<128, 1024, true, R_DF>(o, s, l, st, raw);
-        case 6: return launch_smem_syl<64, 512, true, R_DF>(o, s, l, st, raw);
-        case 7: return launch_smem_syl<128, 1024, true, R_FP64>(o, s, l, st, raw);
+        case 5: return wb::launch_warp_syl<4, true>(o, s, l, st, raw);
+        case 6: return wb::launch_warp_syl<2, true>(o, s, l, st, raw);
+        case 7: return wb::launch_warp_syl<8, true>(o, s, l, st, raw);
         }
     } else if (prec == P_TF32) {
         switch (cfg) {

@@ -42,32 +42,53 @@ __device__ void low_solve(int n, const double *L, long ldl, const double *U, lon
                 stage_f<B, T, F_FULL>(sT, W + i0 + (long)j0 * ldw, ldw, mI, nJ);
             }
             __syncthreads();
+            using MT = Micro<B, T>;
+            const bool micro = MT::OK && (P == P_FP32) && mI == B && nJ == B;
             float acc[E];
+            float macc[MT::MR][MT::MC];
             float frag[FragN<B, T, P>::value][4];
             if constexpr (P == P_FP32) {
-                sl.set(Shape::Full, mI, nJ);
+                if (micro) {
 #pragma unroll
-                for (int r = 0; r < E; ++r) acc[r] = sl.ok(r) ? sT[sl.row[r] + sl.col[r] * LD] : 0.0f;
+                    for (int i = 0; i < MT::MR; ++i)
+#pragma unroll
+                        for (int j = 0; j < MT::MC; ++j) macc[i][j] = sT[(MT::r0() + i) + (MT::c0() + j) * LD];
+                } else {
+                    sl.set(Shape::Full, mI, nJ);
+#pragma unroll
+                    for (int r = 0; r < E; ++r) acc[r] = sl.ok(r) ? sT[sl.row[r] + sl.col[r] * LD] : 0.0f;
+                }
             } else {
                 frag_load<B, T>(frag, sT);
             }
             auto update = [&](bool tb) {
                 if constexpr (P == P_FP32) {
-                    if (tb) slot_update_f<B, T, false, true>(acc, sl, sA, sB, B);
+                    if (micro) micro_update_f<B, T>(macc, sA, sB, B);
+                    else if (tb) slot_update_f<B, T, false, true>(acc, sl, sA, sB, B);
                     else slot_update_f<B, T, false, false>(acc, sl, sA, sB, B);
                 } else {
                     if (tb) mma_update<B, T, P, false, true>(frag, sA, sB, B);
                     else mma_update<B, T, P, false, false>(frag, sA, sB, B);
                 }
             };
+            // Stage A (not transposed) and B (transposed when tb) for either layout.
+            auto stageAB = [&](const auto *GA, long lda_, int ra, const auto *GB, long ldb_, int rb, int cb, bool tb) {
+                if (micro) {
+                    stage_opA<B, T, false>(sA, GA, lda_, ra, B);
+                    if (tb) stage_opB<B, T, true>(sB, GB, ldb_, B, rb);
+                    else stage_opB<B, T, false>(sB, GB, ldb_, B, cb);
+                } else {
+                    stage_f<B, T, F_FULL>(sA, GA, lda_, ra, B);
+                    stage_f<B, T, F_FULL>(sB, GB, ldb_, rb, cb);
+                }
+            };
             // sum_{K<I} L_IK D_KJ
             for (int K = 0; K < I; ++K) {
                 const int k0 = K * B;
                 __syncthreads();
-                stage_f<B, T, F_FULL>(sA, L + i0 + (long)k0 * ldl, ldl, mI, B);
                 const bool tr = LYAP && K < J;
-                if (!tr) stage_f<B, T, F_FULL>(sB, W + k0 + (long)j0 * ldw, ldw, B, nJ);
-                else stage_f<B, T, F_FULL>(sB, W + j0 + (long)k0 * ldw, ldw, nJ, B);
+                if (!tr) stageAB(L + i0 + (long)k0 * ldl, ldl, mI, W + k0 + (long)j0 * ldw, ldw, B, nJ, false);
+                else stageAB(L + i0 + (long)k0 * ldl, ldl, mI, W + j0 + (long)k0 * ldw, ldw, nJ, B, true);
                 __syncthreads();
                 update(tr);
             }
@@ -75,24 +96,30 @@ __device__ void low_solve(int n, const double *L, long ldl, const double *U, lon
             for (int K = 0; K < J; ++K) {
                 const int k0 = K * B;
                 __syncthreads();
-                stage_f<B, T, F_FULL>(sA, W + i0 + (long)k0 * ldw, ldw, mI, B);
-                if (!LYAP) stage_f<B, T, F_FULL>(sB, U + k0 + (long)j0 * ldu, ldu, B, nJ);
-                else stage_f<B, T, F_FULL>(sB, L + j0 + (long)k0 * ldl, ldl, nJ, B);
+                if (!LYAP) stageAB(W + i0 + (long)k0 * ldw, ldw, mI, U + k0 + (long)j0 * ldu, ldu, B, nJ, false);
+                else stageAB(W + i0 + (long)k0 * ldw, ldw, mI, L + j0 + (long)k0 * ldl, ldl, nJ, B, true);
                 __syncthreads();
                 update(LYAP);
             }
             __syncthreads();
             if constexpr (P == P_FP32) {
+                if (micro) {
 #pragma unroll
-                for (int r = 0; r < E; ++r)
-                    if (sl.ok(r)) sT[sl.row[r] + sl.col[r] * LD] = acc[r];
+                    for (int i = 0; i < MT::MR; ++i)
+#pragma unroll
+                        for (int j = 0; j < MT::MC; ++j) sT[(MT::r0() + i) + (MT::c0() + j) * LD] = macc[i][j];
+                } else {
+#pragma unroll
+                    for (int r = 0; r < E; ++r)
+                        if (sl.ok(r)) sT[sl.row[r] + sl.col[r] * LD] = acc[r];
+                }
             } else {
                 frag_store<B, T>(frag, sT);
             }
             if (!LYAP) stage_f<B, T, F_UPPER>(sU, U + j0 + (long)j0 * ldu, ldu, nJ, nJ);
             else stage_f<B, T, F_LOWER>(sU, L + j0 + (long)j0 * ldl, ldl, nJ, nJ);
             __syncthreads();
-            syl_diag_f<B, T, LYAP>(sL, sU, sT, mI, nJ, Rinv + i0 + (long)j0 * ldw, ldw);
+            syl_diag_f<B, T, LYAP>(sL, sU, sT, mI, nJ, Rinv + i0 + (long)j0 * ldw, ldw, sA);
             for (int e = threadIdx.x; e < mI * nJ; e += T) {
                 const int r = e % mI, c = e / mI;
                 W[(i0 + r) + (long)(j0 + c) * ldw] = sT[r + c * LD];
@@ -142,25 +169,40 @@ __device__ void residual(int n, const double *L, long ldl, const double *U, long
         const int jend = LYAP ? I + 1 : nb;
         for (int J = 0; J < jend; ++J) {
             const int nJ = min(B, n - J * B), j0 = J * B;
-            sl.set(Shape::Full, mI, nJ);
+            using MT = Micro<B, T>;
+            const bool micro = MT::OK && RS == R_DF && mI == B && nJ == B;
+            float mh[MT::MR][MT::MC], ml[MT::MR][MT::MC];
             float ah[E], al[E];
             double ad[E];
+            if (micro) {
 #pragma unroll
-            for (int r = 0; r < E; ++r) {
-                ah[r] = 0.f; al[r] = 0.f; ad[r] = 0.0;
-                if (sl.ok(r)) {
-                    int rr = sl.row[r], cc = sl.col[r];
-                    if (LYAP && I == J && rr < cc) { const int t = rr; rr = cc; cc = t; }
-                    const double c = C[(i0 + rr) + (long)(j0 + cc) * ldc];
-                    if (RS == R_DF) split_df(c, ah[r], al[r]);
-                    else ad[r] = c;
+                for (int i = 0; i < MT::MR; ++i)
+#pragma unroll
+                    for (int j = 0; j < MT::MC; ++j) {
+                        int rr = MT::r0() + i, cc = MT::c0() + j;
+                        if (LYAP && I == J && rr < cc) { const int t = rr; rr = cc; cc = t; }
+                        split_df(C[(i0 + rr) + (long)(j0 + cc) * ldc], mh[i][j], ml[i][j]);
+                    }
+            } else {
+                sl.set(Shape::Full, mI, nJ);
+#pragma unroll
+                for (int r = 0; r < E; ++r) {
+                    ah[r] = 0.f; al[r] = 0.f; ad[r] = 0.0;
+                    if (sl.ok(r)) {
+                        int rr = sl.row[r], cc = sl.col[r];
+                        if (LYAP && I == J && rr < cc) { const int t = rr; rr = cc; cc = t; }
+                        const double c = C[(i0 + rr) + (long)(j0 + cc) * ldc];
+                        if (RS == R_DF) split_df(c, ah[r], al[r]);
+                        else ad[r] = c;
+                    }
                 }
             }
             auto upd = [&](bool tb, int kw) {
                 if constexpr (RS == R_DF) {
                     const float2 *a = reinterpret_cast<const float2 *>(sA);
                     const float2 *b = reinterpret_cast<const float2 *>(sB);
-                    if (tb) slot_update_df<B, T, false, true>(ah, al, sl, a, b, kw);
+                    if (micro) micro_update_df<B, T>(mh, ml, a, b, kw);
+                    else if (tb) slot_update_df<B, T, false, true>(ah, al, sl, a, b, kw);
                     else slot_update_df<B, T, false, false>(ah, al, sl, a, b, kw);
                 } else {
                     const double *a = reinterpret_cast<const double *>(sA);
@@ -169,15 +211,48 @@ __device__ void residual(int n, const double *L, long ldl, const double *U, long
                     else slot_update<B, T, false, false>(ad, sl, a, b, kw);
                 }
             };
+            // Micro-tile staging (double-float, k-major) of one A / B operand;
+            // triangles (F_LOWER/F_UPPER) and the symmetric mirror are applied
+            // by staging through the natural layout first when needed.
+            auto stageM = [&](bool isA, const double *G, long ld, int rows, int cols, Fill f, bool tb) {
+                float2 *S = reinterpret_cast<float2 *>(isA ? sA : sB);
+                constexpr int LDA = MT::LDA, LDB = MT::LDB;
+                for (int e = threadIdx.x; e < B * B; e += T) {
+                    const int x = e % B, y = e / B;            // (x, y) of the source block
+                    float2 v = make_float2(0.f, 0.f);
+                    bool keep = x < rows && y < cols;
+                    if (keep) {
+                        if (f == F_LOWER) keep = x >= y;
+                        else if (f == F_UPPER) keep = x <= y;
+                    }
+                    if (keep) {
+                        const long idx = (f == F_SYM_LOWER && x < y) ? (y + (long)x * ld) : (x + (long)y * ld);
+                        split_df(G[idx], v.x, v.y);
+                    }
+                    if (isA) S[x + y * LDA] = v;                 // op(A)(r=x, k=y)
+                    else if (!tb) S[y + x * LDB] = v;            // op(B)(k=x, c=y)
+                    else S[x + y * LDB] = v;                     // op(B)(k=y, c=x) = G(x, y)
+                }
+            };
+            auto stage2 = [&](const double *GA, long lda_, int ra, int ca, Fill fa,
+                              const double *GB, long ldb_, int rb, int cb, Fill fb, bool tb) {
+                if (micro) {
+                    stageM(true, GA, lda_, ra, ca, fa, false);
+                    stageM(false, GB, ldb_, rb, cb, fb, tb);
+                } else {
+                    stage(sA, GA, lda_, ra, ca, fa);
+                    stage(sB, GB, ldb_, rb, cb, fb);
+                }
+            };
             // sum_{K<=I} L_IK X_KJ
             for (int K = 0; K <= I; ++K) {
                 const int k0 = K * B, kw = min(B, n - k0);
                 __syncthreads();
-                stage(sA, L + i0 + (long)k0 * ldl, ldl, mI, kw, K == I ? F_LOWER : F_FULL);
+                const Fill fa = K == I ? F_LOWER : F_FULL;
                 bool tb = false;
-                if (!LYAP || K > J) stage(sB, X + k0 + (long)j0 * ldx, ldx, kw, nJ, F_FULL);
-                else if (K == J) stage(sB, X + j0 + (long)j0 * ldx, ldx, kw, nJ, F_SYM_LOWER);
-                else { stage(sB, X + j0 + (long)k0 * ldx, ldx, nJ, kw, F_FULL); tb = true; }
+                if (!LYAP || K > J) stage2(L + i0 + (long)k0 * ldl, ldl, mI, kw, fa, X + k0 + (long)j0 * ldx, ldx, kw, nJ, F_FULL, false);
+                else if (K == J) stage2(L + i0 + (long)k0 * ldl, ldl, mI, kw, fa, X + j0 + (long)j0 * ldx, ldx, kw, nJ, F_SYM_LOWER, false);
+                else { stage2(L + i0 + (long)k0 * ldl, ldl, mI, kw, fa, X + j0 + (long)k0 * ldx, ldx, nJ, kw, F_FULL, true); tb = true; }
                 __syncthreads();
                 upd(tb, kw);
             }
@@ -185,18 +260,26 @@ __device__ void residual(int n, const double *L, long ldl, const double *U, long
             for (int K = 0; K <= J; ++K) {
                 const int k0 = K * B, kw = min(B, n - k0);
                 __syncthreads();
-                if (LYAP && K == I) stage(sA, X + i0 + (long)i0 * ldx, ldx, mI, kw, F_SYM_LOWER);
-                else stage(sA, X + i0 + (long)k0 * ldx, ldx, mI, kw, F_FULL);
-                if (!LYAP) stage(sB, U + k0 + (long)j0 * ldu, ldu, kw, nJ, K == J ? F_UPPER : F_FULL);
-                else stage(sB, L + j0 + (long)k0 * ldl, ldl, nJ, kw, K == J ? F_LOWER : F_FULL);
+                const Fill fa = (LYAP && K == I) ? F_SYM_LOWER : F_FULL;
+                const long aoff = (LYAP && K == I) ? (i0 + (long)i0 * ldx) : (i0 + (long)k0 * ldx);
+                if (!LYAP) stage2(X + aoff, ldx, mI, kw, fa, U + k0 + (long)j0 * ldu, ldu, kw, nJ, K == J ? F_UPPER : F_FULL, false);
+                else stage2(X + aoff, ldx, mI, kw, fa, L + j0 + (long)k0 * ldl, ldl, nJ, kw, K == J ? F_LOWER : F_FULL, true);
                 __syncthreads();
                 upd(LYAP, kw);
             }
+            if (micro) {
 #pragma unroll
-            for (int r = 0; r < E; ++r) {
-                if (sl.ok(r)) {
-                    const float v = RS == R_DF ? __fadd_rn(ah[r], al[r]) : (float)ad[r];
-                    W[(i0 + sl.row[r]) + (long)(j0 + sl.col[r]) * ldw] = v;
+                for (int i = 0; i < MT::MR; ++i)
+#pragma unroll
+                    for (int j = 0; j < MT::MC; ++j)
+                        W[(i0 + MT::r0() + i) + (long)(j0 + MT::c0() + j) * ldw] = __fadd_rn(mh[i][j], ml[i][j]);
+            } else {
+#pragma unroll
+                for (int r = 0; r < E; ++r) {
+                    if (sl.ok(r)) {
+                        const float v = RS == R_DF ? __fadd_rn(ah[r], al[r]) : (float)ad[r];
+                        W[(i0 + sl.row[r]) + (long)(j0 + sl.col[r]) * ldw] = v;
+                    }
                 }
             }
         }
@@ -210,6 +293,7 @@ __device__ float update_x(int n, double *X, long ldx, const float *W, long ldw, 
                           float *s_red)
 {
     float ss = 0.0f;
+#pragma unroll 4
     for (int e = threadIdx.x; e < n * n; e += T) {
         const int r = e % n, c = e / n;
         if (LYAP && r < c) continue;
@@ -241,6 +325,7 @@ __device__ int reciprocal_divisors(int n, const double *L, long ldl, const doubl
     for (int w = 0; w < T / 32; ++w) md = fmax(md, s_md[w]);
     const double delta = divisor_delta(n, md);
     int bad = 0;
+#pragma unroll 4
     for (int e = threadIdx.x; e < n * n; e += T) {
         const int i = e % n, j = e / n;
         const double d = L[i + (long)i * ldl] + (LYAP ? L[j + (long)j * ldl] : U[j + (long)j * ldu]);
@@ -280,65 +365,88 @@ __device__ void mixed_instance(int n, const double *L, long ldl, const double *U
 
 // ------------------------------------------------ shared-memory-resident variant
 //
-// For n <= NMAX the whole low-precision problem lives in shared memory as
-// FP32: L, U (for the Lyapunov form U = L^T, stored explicitly so both are
-// read with unit stride) and the right-hand side / solution D, each n x ld
-// with ld = n rounded up to even (so a row walk, stride ld - 1, is odd and
-// hits distinct banks).  The solve is an eager wavefront over the
-// anti-diagonals d = i + j, one barrier per anti-diagonal: entries with
-// i + j = d are final; every entry with a + b > d subtracts the two terms that
-// involve them,
-//     t_ab -= l_{a, d-b} x_{d-b, b}   (b <= d)   and   t_ab -= x_{a, d-a} u_{d-a, b}   (a <= d),
-// and entries reaching a + b = d + 1 are finished by the FP64-computed
-// reciprocal.  Each thread keeps its entries' partial sums in registers.
-// Larger instances fall back to the blocked path with B = 32.
+// For n <= NMAX the low-precision solves keep the whole problem in shared
+// memory as FP32: L, U (for the Lyapunov form U = L^T, stored explicitly) and
+// the right-hand side / solution D, each n x ld with ld = n | 1 (odd, so the
+// strided reads of a split dot product fall in distinct banks).  The solve is
+// the entry-wise recurrence run as a lazy wavefront over the anti-diagonals
+// d = i + j: the entries of one anti-diagonal are independent, and each is one
+// dot product of exactly d terms (i from row i of L, j from column j of U),
+// split over a power-of-two group of lanes; one barrier per anti-diagonal.
+// The residual reuses the same shared memory for its RB x RB double-float
+// tiles and writes to the scratch W; L and U are then reloaded.  Larger
+// instances fall back to the blocked path with B = 32.
 
-template <int NMAX, int T>
+template <int T>
 __device__ void smem_wavefront(float *Xs, const float *Ls, const float *Us, int n, int ld,
                                const float *Rinv)
 {
-    constexpr int R = (NMAX * NMAX + T - 1) / T;
-    const int nn = n * n;
-    float tv[R];
-    int ab[R];      // row | column << 16; entries beyond n*n get a row past n
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int e = threadIdx.x + T * r;
-        const int a = e < nn ? e % n : 0x7fff, b = e < nn ? e / n : 0;
-        ab[r] = a | (b << 16);
-        tv[r] = e < nn ? Xs[a + b * ld] : 0.0f;
-        if (e == 0) {
-            tv[r] *= Rinv[0];
-            Xs[0] = tv[r];
-        }
-    }
-    __syncthreads();
-    for (int d = 0; d <= 2 * n - 3; ++d) {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int a = ab[r] & 0xffff, b = ab[r] >> 16;
-            if (a + b > d && a < n) {
-                float t = tv[r];
-                if (b <= d) t = fmaf(-Ls[a + (d - b) * ld], Xs[(d - b) + b * ld], t);
-                if (a <= d) t = fmaf(-Xs[a + (d - a) * ld], Us[(d - a) + b * ld], t);
-                if (a + b == d + 1) {
-                    t *= Rinv[a + (long)b * n];
-                    Xs[a + b * ld] = t;
+    for (int d = 0; d <= 2 * n - 2; ++d) {
+        const int ilo = max(0, d - n + 1), ihi = min(d, n - 1);
+        const int cnt = ihi - ilo + 1;
+        const int split = pick_split<T>(cnt, d);
+        if (warp_has_work(cnt, split)) {
+            const int idx = threadIdx.x / split, part = threadIdx.x % split;
+            const bool act = idx < cnt;
+            const int i = ilo + (act ? idx : 0), j = d - i;
+            // Issue the divisor's global load first; the dot product hides it.
+            const float r = (act && part == 0) ? Rinv[i + (long)j * n] : 0.0f;
+            float s = 0.0f;
+            if (act) {
+#pragma unroll 4
+                for (int t = part; t < d; t += split) {
+                    const bool lt = t < i;
+                    const int k = t - i;
+                    const float a = lt ? Ls[i + t * ld] : Xs[i + k * ld];
+                    const float b = lt ? Xs[t + j * ld] : Us[k + j * ld];
+                    s = fmaf(a, b, s);
                 }
-                tv[r] = t;
             }
+            s = group_sum_f(s, split);
+            if (act && part == 0) Xs[i + j * ld] = (Xs[i + j * ld] - s) * r;
         }
         __syncthreads();
     }
 }
 
+// Residual tile size of the shared-memory variant.
+template <int NMAX>
+struct SmemRB { static constexpr int value = NMAX >= 128 ? 64 : 32; };
+
 template <int NMAX>
 constexpr size_t smem_variant_bytes()
 {
-    // L, U and D (n x ld floats each, ld <= NMAX + 1), the residual's two
-    // B = 32 tiles of 8-byte elements, the blocked fallback (five float B = 32
-    // tiles, which fit inside the same region) and a reduction buffer.
-    return (size_t)3 * NMAX * (NMAX + 1) * sizeof(float) + 2 * FTile<32>::SZ * 8 + 64 * sizeof(float);
+    // L, U and D (n x ld floats each, ld <= NMAX + 1), which the residual's
+    // two RB x RB tiles of 8-byte elements and the blocked fallback's five
+    // float tiles reuse, plus a reduction buffer.
+    constexpr size_t solve = (size_t)3 * NMAX * (NMAX + 1) * sizeof(float);
+    constexpr size_t res = (size_t)2 * FTile<SmemRB<NMAX>::value>::SZ * 8;
+    constexpr size_t blk = (size_t)5 * FTile<32>::SZ * sizeof(float);
+    constexpr size_t m1 = solve > res ? solve : res;
+    return (m1 > blk ? m1 : blk) + 64 * sizeof(float);
+}
+
+// Load L, U (the strict triangles the wavefront reads) as FP32 into shared
+// memory; with rhs, also load D from C (FP64) or from the float scratch W.
+template <int T, bool LYAP>
+__device__ void smem_load(float *Ls, float *Us, float *Xs, int n, int ld, const double *L, long ldl,
+                          const double *U, long ldu, const double *C, long ldc, const float *W)
+{
+    for (int e = threadIdx.x; e < n * n; e += T) {
+        const int a = e % n, b = e / n;
+        Ls[a + b * ld] = a > b ? d2f_trunc(L[a + (long)b * ldl]) : 0.0f;
+        const double u = LYAP ? L[b + (long)a * ldl] : U[a + (long)b * ldu];
+        Us[a + b * ld] = a < b ? d2f_trunc(u) : 0.0f;
+        if (W) {
+            float w = W[e];
+            if (LYAP && a < b) w = W[b + (long)a * n];    // residual holds the lower blocks
+            Xs[a + b * ld] = w;
+        } else if (C) {
+            const double c = (LYAP && a < b) ? C[b + (long)a * ldc] : C[a + (long)b * ldc];
+            Xs[a + b * ld] = d2f_trunc(c);
+        }
+    }
+    __syncthreads();
 }
 
 template <int NMAX, int T, bool LYAP, int RS>
@@ -346,11 +454,11 @@ __device__ void smem_instance(int n, const double *L, long ldl, const double *U,
                               const double *C, long ldc, double *X, long ldx, int *info,
                               float *W, bool raw, float *sm)
 {
-    constexpr size_t tiles_off = (size_t)3 * NMAX * (NMAX + 1);     // floats
-    float *s_red = sm + tiles_off + 2 * FTile<32>::SZ * 2;
+    constexpr int RB = SmemRB<NMAX>::value;
+    float *s_red = sm + (smem_variant_bytes<NMAX>() / sizeof(float) - 64);
+    float *Rinv = W + (long)n * n;
     if (n > NMAX) {
         // Blocked fallback: its five tiles live at the start of shared memory.
-        float *Rinv = W + (long)n * n;
         const int bad = reciprocal_divisors<T, LYAP>(n, L, ldl, U, ldu, Rinv, s_red);
         low_solve<32, T, LYAP, P_FP32, true>(n, L, ldl, U, ldu, C, ldc, W, Rinv, sm);
         const float nx = sqrtf(update_x<T, LYAP>(n, X, ldx, W, n, true, s_red));
@@ -367,35 +475,18 @@ __device__ void smem_instance(int n, const double *L, long ldl, const double *U,
         if (threadIdx.x == 0) *info = bad ? 1 : (conv ? 0 : n + 1);
         return;
     }
-    const int ld = (n + 1) & ~1;
+    const int ld = n | 1;
     float *Ls = sm, *Us = sm + (long)n * ld, *Xs = sm + 2l * n * ld;
-    float *tiles = sm + tiles_off;
-    float *Rinv = W + (long)n * n;
     const int bad = reciprocal_divisors<T, LYAP>(n, L, ldl, U, ldu, Rinv, s_red);
-    for (int e = threadIdx.x; e < n * n; e += T) {
-        const int a = e % n, b = e / n;
-        Ls[a + b * ld] = a > b ? d2f_trunc(L[a + (long)b * ldl]) : 0.0f;
-        const double u = LYAP ? L[b + (long)a * ldl] : U[a + (long)b * ldu];
-        Us[a + b * ld] = a < b ? d2f_trunc(u) : 0.0f;
-        const double c = (LYAP && a < b) ? C[b + (long)a * ldc] : C[a + (long)b * ldc];
-        Xs[a + b * ld] = d2f_trunc(c);
-    }
-    __syncthreads();
-    smem_wavefront<NMAX, T>(Xs, Ls, Us, n, ld, Rinv);
+    smem_load<T, LYAP>(Ls, Us, Xs, n, ld, L, ldl, U, ldu, C, ldc, nullptr);
+    smem_wavefront<T>(Xs, Ls, Us, n, ld, Rinv);
     const float nx = sqrtf(update_x<T, LYAP>(n, X, ldx, Xs, ld, true, s_red));
     int conv = nx == 0.0f || raw;
     float prev = nx;
     for (int it = 0; it < MAXIT && !conv; ++it) {
-        residual<32, T, LYAP, RS>(n, L, ldl, U, ldu, C, ldc, X, ldx, Xs, ld, tiles);
-        if (LYAP) {
-            // The residual is symmetric; it was written for the lower blocks.
-            for (int e = threadIdx.x; e < n * n; e += T) {
-                const int a = e % n, b = e / n;
-                if (a < b) Xs[a + b * ld] = Xs[b + a * ld];
-            }
-            __syncthreads();
-        }
-        smem_wavefront<NMAX, T>(Xs, Ls, Us, n, ld, Rinv);
+        residual<RB, T, LYAP, RS>(n, L, ldl, U, ldu, C, ldc, X, ldx, W, n, sm);
+        smem_load<T, LYAP>(Ls, Us, Xs, n, ld, L, ldl, U, ldu, nullptr, 0, W);
+        smem_wavefront<T>(Xs, Ls, Us, n, ld, Rinv);
         const float nd = sqrtf(update_x<T, LYAP>(n, X, ldx, Xs, ld, false, s_red));
         const float pred = prev > 0.0f ? nd * (nd / prev) : nd;
         conv = (nd <= (float)SS_REFINE_TOL * nx) || (pred <= (float)SS_REFINE_TOL * nx);

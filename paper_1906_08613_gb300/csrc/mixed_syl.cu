@@ -1,5 +1,5 @@
 // Instantiations of the mixed-precision Sylvester kernels (see mixed_solver.cuh).
-#include "mixed_solver.cuh"
+#include "mixed_warp.cuh"
 
 namespace ss {
 
@@ -15,9 +15,9 @@ cudaError_t launch_mixed_trsyl(int prec, int cfg, const Operands &o, const Sched
         case 2: return launch_mixed_syl<32, 128, false, P_FP32, R_DF>(o, s, l, st, raw);
         case 3: return launch_mixed_syl<16, 128, false, P_FP32, R_FP64>(o, s, l, st, raw);
         case 4: return launch_mixed_syl<32, 128, false, P_FP32, R_FP64>(o, s, l, st, raw);
-        case 5: return launch_smem_syl<128, 1024, false, R_DF>(o, s, l, st, raw);
-        case 6: return launch_smem_syl<64, 512, false, R_DF>(o, s, l, st, raw);
-        case 7: return launch_smem_syl<128, 1024, false, R_FP64>(o, s, l, st, raw);
+        case 5: return wb::launch_warp_syl<4, false>(o, s, l, st, raw);
+        case 6: return wb::launch_warp_syl<2, false>(o, s, l, st, raw);
+        case 7: return wb::launch_warp_syl<8, false>(o, s, l, st, raw);
         }
     } else if (prec == P_TF32) {
         switch (cfg) {
