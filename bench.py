@@ -275,6 +275,8 @@ def main():
     ap.add_argument("--mode", default="fp64")
     ap.add_argument("--cfg", type=int, default=None)
     ap.add_argument("--graph", action="store_true", help="replay each step from a captured CUDA graph")
+    ap.add_argument("--policy", default="per-bin", choices=["per-bin", "call"],
+                    help="selector policy: a (mode, cfg) per size bin, or one for the whole call")
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-FP64 comparison runs")
     ap.add_argument("--seed", type=int, default=1234)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -306,7 +308,7 @@ def main():
         from paper_1906_08613_gb300 import selector as sel
         s_model = sel.Selector.load(os.path.join(ROOT, "paper_1906_08613_gb300", "data", "selector_gb300"),
                                     device=str(dev))
-        table = s_model.install(op, sel.counts_by_bin(pk.n))
+        table = s_model.install(op, sel.counts_by_bin(pk.n), per_bin=args.policy == "per-bin")
         mode, cfg = ss.MODE_AUTO, ss.CFG_DEFAULT
     else:
         mode = ss.MODES[args.mode]
@@ -457,7 +459,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": name, "op": op, "batch": pk.batch,
                    "sizes": f"n in [{int(pk.n.min())}, {int(pk.n.max())}], mean {float(pk.n.mean()):.1f}",
-                   "path": "mixed+learned (SS_MODE_AUTO, trained selector)" if learned else args.mode,
+                   "path": (f"mixed+learned (SS_MODE_AUTO, trained selector, {args.policy} policy)"
+                            if learned else args.mode),
                    "cfg": cfg, "graph": bool(args.graph),
                    "selector_table": [[int(m), int(c)] for m, c in zip(*table)] if table else None,
                    "l2": f"operands {sum(int(v.numel()) * 8 for v in db.bufs.values()) / 1e6:.0f} MB > 129 MB L2; no flush"},

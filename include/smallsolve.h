@@ -68,7 +68,12 @@
  *   SS_INFO_NO_WORK    the workspace was too small for this instance.
  *
  * Streams.  `stream` is a cudaStream_t (NULL: the legacy default stream).
- * Every call is asynchronous with respect to the host.
+ * Every call is asynchronous with respect to the host.  When a call uses
+ * several (mode, cfg) launch groups (SS_CFG_TABLE, SS_MODE_AUTO), groups after
+ * the first run on the library's auxiliary streams (three per device, created
+ * on first use), forked from `stream` after the pre-pass and joined back
+ * before the call returns, so their persistent kernels overlap; the whole call
+ * stays ordered on `stream` and can be captured into a CUDA graph.
  */
 #ifndef SMALLSOLVE_H
 #define SMALLSOLVE_H

@@ -58,6 +58,37 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 std::atomic<long long> g_launches{0};
 
+// Auxiliary streams of one device: launch groups 2..k of a call run on them,
+// forked from and joined back to the caller's stream with events, so that the
+// persistent kernels of different groups overlap (one group's CTAs fill the
+// SM slots another group's drained CTAs free).  Created once per device on
+// first use; they hold no device memory.
+constexpr int kAux = 3;
+struct AuxPool {
+    bool ready = false;
+    cudaStream_t aux[kAux];
+    cudaEvent_t fork;
+    cudaEvent_t join[kAux];
+};
+std::mutex g_aux_mu;
+AuxPool g_aux[64];
+
+AuxPool *aux_pool()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    AuxPool &p = g_aux[dev];
+    if (!p.ready) {
+        for (int i = 0; i < kAux; ++i) {
+            if (cudaStreamCreateWithFlags(&p.aux[i], cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+            if (cudaEventCreateWithFlags(&p.join[i], cudaEventDisableTiming) != cudaSuccess) return nullptr;
+        }
+        if (cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+        p.ready = true;
+    }
+    return &p;
+}
+
 struct Profile {
     std::mutex mu;
     bool on = false;
@@ -245,15 +276,33 @@ int run(int op, int batch, int max_n, const Operands &o, int mode, int cfg, void
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     const bool prof = profile_pair(&ev0, &ev1);
     if (prof) cudaEventRecord(ev0, st);
+    // Groups beyond the first go to auxiliary streams forked after the pre-pass.
+    std::unique_lock<std::mutex> aux_lock(g_aux_mu, std::defer_lock);
+    AuxPool *ap = nullptr;
+    if (ngroups > 1) {
+        aux_lock.lock();
+        ap = aux_pool();
+        if (ap && cudaEventRecord(ap->fork, st) != cudaSuccess) ap = nullptr;
+        if (ap)
+            for (int i = 0; i < kAux && i < ngroups - 1; ++i)
+                if (cudaStreamWaitEvent(ap->aux[i], ap->fork, 0) != cudaSuccess) { ap = nullptr; break; }
+    }
     for (int g = 0; g < ngroups; ++g) {
         Launch l{g, group_cfg[g], group_mode[g], max_n, batch};
+        cudaStream_t gs = (g == 0 || ap == nullptr) ? st : ap->aux[(g - 1) % kAux];
         if (l.mode == SS_MODE_FP64) {
-            if (op == SS_OP_POTRF) e = launch_potrf_fp64(o, s, l, st);
-            else e = launch_syl_fp64(o, s, l, st, op == SS_OP_TRLYAP);
+            if (op == SS_OP_POTRF) e = launch_potrf_fp64(o, s, l, gs);
+            else e = launch_syl_fp64(o, s, l, gs, op == SS_OP_TRLYAP);
         } else {
-            e = launch_mixed(op, o, s, l, st);
+            e = launch_mixed(op, o, s, l, gs);
         }
         if (e != cudaSuccess) return SS_ERR_CUDA;
+    }
+    if (ap) {
+        for (int i = 0; i < kAux && i < ngroups - 1; ++i) {
+            if (cudaEventRecord(ap->join[i], ap->aux[i]) != cudaSuccess) return SS_ERR_CUDA;
+            if (cudaStreamWaitEvent(st, ap->join[i], 0) != cudaSuccess) return SS_ERR_CUDA;
+        }
     }
     if (prof) cudaEventRecord(ev1, st);
     return 0;

@@ -157,8 +157,42 @@ class Selector:
             modes[k], cfgs[k] = ss.MODES[m], c
         return modes, cfgs
 
-    def install(self, op: str, batch):
-        modes, cfgs = self.auto_table(op, batch)
+    def call_choice(self, op: str, batch, nbins: int = ss.NUM_BINS):
+        """One (mode, cfg) for a whole call: the candidate whose predicted
+        total over the call's size bins (bin k with batch[k] instances) is
+        smallest.  One launch keeps every size in one persistent queue, whose
+        longest-first order balances the SMs; a different choice per bin would
+        split the call into serialized launches, each with its own tail."""
+        counts = list(batch) if hasattr(batch, "__len__") else [batch] * nbins
+        want = [k for k in range(nbins) if counts[k] > 0]
+        rows, cand = [], []
+        for mode in MODE_ORDER:
+            cnt = ss.ss_config_count(ss.OPS[op], ss.MODES[mode])
+            if cnt <= 0:
+                continue
+            cand.append((mode, cnt))
+            for k in want:
+                rows.append(features(op, bin_center(k), counts[k], mode))
+        Y = self.predict(np.array(rows)) if rows else np.zeros((0, ss.MLP_OUT))
+        best, i = None, 0
+        for mode, cnt in cand:
+            tot = np.zeros(cnt)
+            for _ in want:
+                tot += 2.0 ** Y[i, :cnt]
+                i += 1
+            c = int(np.argmin(tot))
+            if best is None or tot[c] < best[2]:
+                best = (mode, c, float(tot[c]))
+        return best
+
+    def call_table(self, op: str, batch, nbins: int = ss.NUM_BINS):
+        """AUTO table with the single call_choice in every bin that has instances."""
+        counts = list(batch) if hasattr(batch, "__len__") else [batch] * nbins
+        mode, cfg, _ = self.call_choice(op, counts, nbins)
+        return [ss.MODES[mode]] * nbins, [cfg] * nbins
+
+    def install(self, op: str, batch, per_bin: bool = False):
+        modes, cfgs = (self.auto_table if per_bin else self.call_table)(op, batch)
         ss.ss_set_auto_table(ss.OPS[op], modes, cfgs)
         return modes, cfgs
 

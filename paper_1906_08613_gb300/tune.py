@@ -140,6 +140,27 @@ def exhaustive_table(entries, op, batch, nbins=ss.NUM_BINS):
     return modes, cfgs
 
 
+def exhaustive_call_choice(entries, op, batch, nbins=ss.NUM_BINS):
+    """The single (mode, cfg) with the smallest measured total over the call's
+    size bins (bucket closest in log batch per bin); None if unmeasured."""
+    counts = list(batch) if hasattr(batch, "__len__") else [batch] * nbins
+    pairs = sorted({(e["mode"], e["cfg"]) for e in entries if e["op"] == op and not e.get("info_nonzero", 0)})
+    best = None
+    for mode, cfg in pairs:
+        tot = 0.0
+        for k in range(nbins):
+            if counts[k] <= 0:
+                continue
+            t = lookup(entries, op, k, counts[k], mode, cfg)
+            if t is None:
+                tot = None
+                break
+            tot += t
+        if tot is not None and (best is None or tot < best[2]):
+            best = (mode, cfg, tot)
+    return best
+
+
 def save(entries, path, extra=None):
     d = {"gpu": None, "created": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()), "entries": entries}
     try:
