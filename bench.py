@@ -164,9 +164,10 @@ def sum_over_ranks(dist, value, dev):
     return float(t.item())
 
 
-def read_traffic(kernel_prefix, workload):
+def read_traffic(key):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, if it was taken on the current kernel sources."""
+    summary (profiles/traffic.json, keyed workload:op:mode:cfg), if it was
+    taken on the current kernel sources."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -175,7 +176,7 @@ def read_traffic(kernel_prefix, workload):
     except (OSError, ValueError):
         return None
     from paper_1906_08613_gb300 import build as b
-    ent = d.get(f"{workload}:{kernel_prefix}")
+    ent = d.get(key)
     if not ent or ent.get("sources_sha") != b.sources_sha():
         return None
     return ent.get("dram_bytes_per_launch")
@@ -275,7 +276,7 @@ def main():
     ap.add_argument("--mode", default="fp64")
     ap.add_argument("--cfg", type=int, default=None)
     ap.add_argument("--graph", action="store_true", help="replay each step from a captured CUDA graph")
-    ap.add_argument("--policy", default="per-bin", choices=["per-bin", "call"],
+    ap.add_argument("--policy", default="call", choices=["per-bin", "call"],
                     help="selector policy: a (mode, cfg) per size bin, or one for the whole call")
     ap.add_argument("--no-compare", action="store_true", help="skip the plain-FP64 comparison runs")
     ap.add_argument("--seed", type=int, default=1234)
@@ -441,11 +442,20 @@ def main():
             dist.destroy_process_group()
         return 0
 
+    # The dominant kernel: the (mode, cfg) of the largest size bin's group.
+    if table:
+        kbin = ss.size_bin(int(pk.n.max()))
+        dm, dc = table[0][kbin], table[1][kbin]
+        inv = {v: k for k, v in ss.MODES.items()}
+        dominant_key = f"{name}:{op}:{inv.get(dm, 'fp64')}:{dc}"
+    else:
+        dominant_key = f"{name}:{op}:{args.mode}:{cfg}"
     achieved = Falg / (kern_avg_ms * 1e-3) / 1e9
     roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
             "frac": achieved / FP64_PEAK_GFLOPS,
-            "traffic": read_traffic(f"{op}_{args.mode}", name),
+            "traffic": read_traffic(dominant_key),
             "kernel": f"{op} persistent solve kernels ({'selector tables' if learned else args.mode})",
+            "dominant": dominant_key,
             "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (of derived; "
                            "a DFMA probe measured 1248 GFLOP/s)",
             "kernel_ms": kern_avg_ms, "algorithmic_bytes": Balg,
