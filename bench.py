@@ -142,11 +142,16 @@ def dist_init():
 def barrier(dist, dev):
     import torch
     if dist is not None:
-        dist.barrier(device_ids=[dev.index])
-    torch.cuda.synchronize(dev)
+        if dev.type == "cuda":
+            dist.barrier(device_ids=[dev.index])
+        else:
+            dist.barrier()
+    if dev.type == "cuda":
+        torch.cuda.synchronize(dev)
 
 
 def max_over_ranks(dist, value, dev):
+    """The slowest rank's time (replicas: the job ends when the last rank does)."""
     import torch
     if dist is None:
         return value
@@ -156,12 +161,20 @@ def max_over_ranks(dist, value, dev):
 
 
 def sum_over_ranks(dist, value, dev):
+    """Units processed by all ranks together (whole-job throughput)."""
     import torch
     if dist is None:
         return value
     t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def job_throughput(dist, units_per_rank, ms_per_rank, dev):
+    """Whole-job units/s of independent replicas: all ranks' units over the
+    slowest rank's time."""
+    ms = max_over_ranks(dist, ms_per_rank, dev)
+    return sum_over_ranks(dist, float(units_per_rank), dev) / (ms * 1e-3), ms
 
 
 def read_traffic(key):
@@ -360,16 +373,13 @@ def main():
     kern_ms, kern_calls = ss.ss_profile_read()
     ss.ss_profile_enable(False)
     clk = clocks.stop()
-    ms_total = e0.elapsed_time(e1)
-    ms_total = max_over_ranks(dist, ms_total, dev)
+    value, ms_total = job_throughput(dist, pk.batch * args.steps, e0.elapsed_time(e1), dev)
     if graph is not None:
         # Launches and kernel time inside graph replays are not seen by the
         # library's counters: one call launches 1 + (launch groups) kernels.
         launches = args.steps * (1 + launch_groups(table, int(pk.n.max())))
         kern_ms, kern_calls = ms_total, args.steps
     ms_step = ms_total / args.steps
-    solves = sum_over_ranks(dist, float(pk.batch * args.steps), dev)
-    value = solves / (ms_total * 1e-3)
     kern_avg_ms = kern_ms / max(kern_calls, 1)
     info = db.info_host()
 
