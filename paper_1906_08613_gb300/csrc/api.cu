@@ -20,8 +20,10 @@ long long mixed_scratch_per_n2(int op, int mode);
 
 namespace {
 
+// variant: 0 = CTA-wide diagonal-block work, 1 = one warp (shorter chain).
 const Config kFp64Configs[] = {
     {8, 64, 0}, {16, 64, 0}, {16, 128, 0}, {32, 128, 0}, {32, 256, 0},
+    {16, 64, 1}, {16, 128, 1}, {32, 128, 1},
 };
 constexpr int kNumFp64 = sizeof(kFp64Configs) / sizeof(kFp64Configs[0]);
 

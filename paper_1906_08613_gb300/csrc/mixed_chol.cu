@@ -378,6 +378,7 @@ __global__ void __launch_bounds__(T, 1024 / T) chol_mixed_kernel(Operands o, Sch
     extern __shared__ __align__(16) float smf[];
     __shared__ int s_slot;
     const int lo = s.meta[META_RANGE + 2 * group], hi = s.meta[META_RANGE + 2 * group + 1];
+    claim_init(&s_slot);
     for (;;) {
         const int w = lo + claim_slot(s.meta + META_HEAD + group, &s_slot);
         if (w >= hi) break;

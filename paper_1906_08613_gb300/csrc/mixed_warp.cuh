@@ -350,6 +350,7 @@ __global__ void __launch_bounds__(32 * WPC) warp_syl_kernel(Operands o, Sched s,
     extern __shared__ __align__(16) float smf[];
     __shared__ int s_slot;
     const int lo = s.meta[META_RANGE + 2 * group], hi = s.meta[META_RANGE + 2 * group + 1];
+    claim_init(&s_slot);
     for (;;) {
         const int w = lo + claim_slot(s.meta + META_HEAD + group, &s_slot);
         if (w >= hi) break;

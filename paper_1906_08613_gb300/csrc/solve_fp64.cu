@@ -92,8 +92,53 @@ __device__ int syl_diag(const double *sL, const double *sU, double *sT, double *
     return bad;
 }
 
+// Warp-level version of syl_diag (B <= 32): warp 0 alone runs the
+// reciprocals and the wavefront, synchronising with __syncwarp only; each
+// entry of an anti-diagonal gets 32/B lanes.  The other warps wait at the
+// closing barrier.  Shortens the per-instance critical path when latency,
+// not the FP64 pipe, bounds the call.
+template <int B, int T, bool UT>
+__device__ int syl_diag_warp(const double *sL, const double *sU, double *sT, double *sR, int m, int nn,
+                             double delta)
+{
+    constexpr int LD = Tile<B>::LD;
+    constexpr int S = 32 / B;          // lanes per entry
+    int bad = 0;
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        for (int e = lane; e < m * nn; e += 32) {
+            const int i = e % m, j = e / m;
+            const double dd = sL[i + i * LD] + sU[j + j * LD];
+            if (!(fabs(dd) > delta)) bad = 1;
+            sR[i + j * LD] = 1.0 / dd;
+        }
+        __syncwarp();
+        const int idx = lane / S, part = lane % S;
+        for (int d = 0; d <= m + nn - 2; ++d) {
+            const int ilo = max(0, d - nn + 1), ihi = min(d, m - 1);
+            const int cnt = ihi - ilo + 1;
+            const bool act = idx < cnt;
+            const int i = ilo + (act ? idx : 0), j = d - i;
+            double s = 0.0;
+            if (act) {
+                for (int t = part; t < d; t += S) {
+                    const bool lt = t < i;
+                    const int k = t - i;
+                    const double a = lt ? sL[i + t * LD] : sT[i + k * LD];
+                    const double b = lt ? sT[t + j * LD] : (UT ? sU[j + k * LD] : sU[k + j * LD]);
+                    s = fma(a, b, s);
+                }
+            }
+            for (int o = S >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (act && part == 0) sT[i + j * LD] = (sT[i + j * LD] - s) * sR[i + j * LD];
+            __syncwarp();
+        }
+    }
+    return __syncthreads_or(bad);
+}
+
 // One Sylvester (LYAP = false) or Lyapunov (LYAP = true, U unused) instance.
-template <int B, int T, bool LYAP>
+template <int B, int T, bool LYAP, int VAR>
 __device__ void syl_instance(int n, const double *L, long ldl, const double *U, long ldu,
                              const double *C, long ldc, double *X, long ldx, int *info,
                              double *sm)
@@ -161,7 +206,8 @@ __device__ void syl_instance(int n, const double *L, long ldl, const double *U, 
             if (!LYAP) stage_tri<B, T>(sU, U + j0 + (long)j0 * ldu, ldu, nJ, false);
             else       stage_tri<B, T>(sU, L + j0 + (long)j0 * ldl, ldl, nJ, true);
             __syncthreads();
-            bad |= syl_diag<B, T, LYAP>(sL, sU, sT, sA, mI, nJ, delta);
+            if (VAR == 0) bad |= syl_diag<B, T, LYAP>(sL, sU, sT, sA, mI, nJ, delta);
+            else bad |= syl_diag_warp<B, T, LYAP>(sL, sU, sT, sA, mI, nJ, delta);
             // syl_diag ends with a barrier.
 #pragma unroll
             for (int r = 0; r < E; ++r) {
@@ -243,7 +289,61 @@ __device__ void chol_trsm(const double *sD, const double *s_rinv, double *sT, in
     }
 }
 
+// Warp-level Cholesky of the m x m upper block in sT (B <= 32): warp 0 alone,
+// rows in order, 32/B lanes per column; every lane takes the pivot from the
+// row's first entry and forms 1/sqrt once (FP64 rsqrt), so a row costs one
+// __syncwarp.  Returns 0 or the failing pivot + 1 (uniform over the CTA).
 template <int B, int T>
+__device__ int chol_diag_warp(double *sT, int m, double *s_scal)
+{
+    constexpr int LD = Tile<B>::LD;
+    constexpr int S = 32 / B;
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x, idx = lane / S, part = lane % S;
+        int fail = 0;
+        for (int i = 0; i < m; ++i) {
+            const int j = i + idx;
+            const bool act = j < m;
+            double s = 0.0;
+            if (act)
+                for (int k = part; k < i; k += S) s = fma(sT[k + i * LD], sT[k + j * LD], s);
+            for (int o = S >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            const double t = act ? sT[i + j * LD] - s : 0.0;
+            const double d = __shfl_sync(0xffffffffu, t, 0);    // pivot argument of row i
+            if (!(d > 0.0)) { fail = i + 1; break; }
+            const double r = rsqrt(d);
+            if (act && part == 0) sT[i + j * LD] = (j == i) ? d * r : t * r;
+            __syncwarp();
+        }
+        if (lane == 0) s_scal[1] = (double)fail;
+    }
+    __syncthreads();
+    return (int)s_scal[1];
+}
+
+// Warp-level solve of X_II^T Y = T for the B x nn block in sT (B <= 32):
+// warp 0, rows in order, 32/B lanes per column.
+template <int B, int T>
+__device__ void chol_trsm_warp(const double *sD, const double *s_rinv, double *sT, int m, int nn)
+{
+    constexpr int LD = Tile<B>::LD;
+    constexpr int S = 32 / B;
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x, idx = lane / S, part = lane % S;
+        const bool act = idx < nn;
+        for (int i = 0; i < m; ++i) {
+            double s = 0.0;
+            if (act)
+                for (int k = part; k < i; k += S) s = fma(sD[k + i * LD], sT[k + idx * LD], s);
+            for (int o = S >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (act && part == 0) sT[i + idx * LD] = (sT[i + idx * LD] - s) * s_rinv[i];
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+}
+
+template <int B, int T, int VAR>
 __device__ void potrf_instance(int n, const double *A, long lda, double *X, long ldx, int *info,
                                double *sm)
 {
@@ -283,10 +383,11 @@ __device__ void potrf_instance(int n, const double *A, long lda, double *X, long
                 __syncthreads();
                 for (int i = threadIdx.x; i < B; i += T) s_rinv[i] = 1.0 / sD[i + i * LD];
                 __syncthreads();
-                chol_trsm<B, T>(sD, s_rinv, sT, B, nJ);
+                if (VAR == 0) chol_trsm<B, T>(sD, s_rinv, sT, B, nJ);
+                else chol_trsm_warp<B, T>(sD, s_rinv, sT, B, nJ);
             } else {
                 __syncthreads();
-                const int f = chol_diag<B, T>(sT, nJ, s_scal);
+                const int f = VAR == 0 ? chol_diag<B, T>(sT, nJ, s_scal) : chol_diag_warp<B, T>(sT, nJ, s_scal);
                 if (f) {
                     if (threadIdx.x == 0) *info = j0 + f;
                     return;     // uniform: every thread saw the same pivot
@@ -311,29 +412,31 @@ __device__ __forceinline__ bool next_instance(const Sched &s, int group, int *s_
     return true;
 }
 
-template <int B, int T>
+template <int B, int T, int VAR>
 __global__ void __launch_bounds__(T) potrf_fp64_kernel(Operands o, Sched s, int group)
 {
     extern __shared__ double sm[];
     __shared__ int s_slot;
     int b;
+    claim_init(&s_slot);
     while (next_instance(s, group, &s_slot, b)) {
         const int n = o.n[b];
         if (n == 0) { if (threadIdx.x == 0) o.info[b] = 0; continue; }
-        potrf_instance<B, T>(n, o.A[b], o.lda[b], o.X[b], o.ldx[b], o.info + b, sm);
+        potrf_instance<B, T, VAR>(n, o.A[b], o.lda[b], o.X[b], o.ldx[b], o.info + b, sm);
     }
 }
 
-template <int B, int T, bool LYAP>
+template <int B, int T, bool LYAP, int VAR>
 __global__ void __launch_bounds__(T) syl_fp64_kernel(Operands o, Sched s, int group)
 {
     extern __shared__ double sm[];
     __shared__ int s_slot;
     int b;
+    claim_init(&s_slot);
     while (next_instance(s, group, &s_slot, b)) {
         const int n = o.n[b];
         if (n == 0) { if (threadIdx.x == 0) o.info[b] = 0; continue; }
-        syl_instance<B, T, LYAP>(n, o.A[b], o.lda[b], LYAP ? nullptr : o.U[b], LYAP ? 0 : o.ldu[b],
+        syl_instance<B, T, LYAP, VAR>(n, o.A[b], o.lda[b], LYAP ? nullptr : o.U[b], LYAP ? 0 : o.ldu[b],
                                  o.C[b], o.ldc[b], o.X[b], o.ldx[b], o.info + b, sm);
     }
 }
@@ -357,14 +460,17 @@ cudaError_t launch_persistent(K kernel, int threads, size_t smem, int batch, cud
 
 }  // namespace
 
-// Configuration id -> (B, T); the same table for all three ops in FP64.
-#define SS_FP64_CONFIGS(X)  X(0, 8, 64) X(1, 16, 64) X(2, 16, 128) X(3, 32, 128) X(4, 32, 256)
+// Configuration id -> (B, T, diagonal variant: 0 CTA-wide, 1 one warp); the
+// same table for all three ops in FP64.
+#define SS_FP64_CONFIGS(X)                                                                 \
+    X(0, 8, 64, 0) X(1, 16, 64, 0) X(2, 16, 128, 0) X(3, 32, 128, 0) X(4, 32, 256, 0) \
+    X(5, 16, 64, 1) X(6, 16, 128, 1) X(7, 32, 128, 1)
 
 cudaError_t launch_potrf_fp64(const Operands &o, const Sched &s, const Launch &l, cudaStream_t st)
 {
     switch (l.cfg) {
-#define CASE(id, B, T) \
-    case id: return launch_persistent(potrf_fp64_kernel<B, T>, T, smem_bytes<B>(), l.batch, st, o, s, l.group);
+#define CASE(id, B, T, V) \
+    case id: return launch_persistent(potrf_fp64_kernel<B, T, V>, T, smem_bytes<B>(), l.batch, st, o, s, l.group);
         SS_FP64_CONFIGS(CASE)
 #undef CASE
     }
@@ -374,10 +480,10 @@ cudaError_t launch_potrf_fp64(const Operands &o, const Sched &s, const Launch &l
 cudaError_t launch_syl_fp64(const Operands &o, const Sched &s, const Launch &l, cudaStream_t st, bool lyap)
 {
     switch (l.cfg) {
-#define CASE(id, B, T)                                                                                   \
+#define CASE(id, B, T, V)                                                                                \
     case id:                                                                                             \
-        return lyap ? launch_persistent(syl_fp64_kernel<B, T, true>, T, smem_bytes<B>(), l.batch, st, o, s, l.group) \
-                    : launch_persistent(syl_fp64_kernel<B, T, false>, T, smem_bytes<B>(), l.batch, st, o, s, l.group);
+        return lyap ? launch_persistent(syl_fp64_kernel<B, T, true, V>, T, smem_bytes<B>(), l.batch, st, o, s, l.group) \
+                    : launch_persistent(syl_fp64_kernel<B, T, false, V>, T, smem_bytes<B>(), l.batch, st, o, s, l.group);
         SS_FP64_CONFIGS(CASE)
 #undef CASE
     }

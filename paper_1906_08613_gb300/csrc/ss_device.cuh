@@ -21,10 +21,27 @@ struct Tile {
 };
 
 // Claim the next slot of the persistent queue; every thread gets the value.
+// A CTA's first slot is its block index; later slots come from the atomic
+// counter, offset by the grid size, so every slot is handed out exactly once
+// whether or not all CTAs are resident.  Why the first claim is static: the
+// queue is in longest-first order, so the first gridDim.x slots hold the
+// largest instances, and consecutive block indices are dispatched to
+// different SMs, so each SM receives one instance from every stretch of
+// (number of SMs) consecutive slots.  Claimed in arrival order at the atomic
+// instead, some SMs reach it first repeatedly and start with several of the
+// largest instances, and the FP64 pipes of the others idle at the end.
+// *s_slot holds the previous slot, negative before the first claim
+// (claim_init); the choice is made by thread 0 on that shared value, which
+// keeps it out of the solver's registers.
+__device__ __forceinline__ void claim_init(int *s_slot)
+{
+    if (threadIdx.x == 0) *s_slot = -1;
+}
+
 __device__ __forceinline__ int claim_slot(int *head, int *s_slot)
 {
     __syncthreads();
-    if (threadIdx.x == 0) *s_slot = atomicAdd(head, 1);
+    if (threadIdx.x == 0) *s_slot = *s_slot < 0 ? (int)blockIdx.x : (int)gridDim.x + atomicAdd(head, 1);
     __syncthreads();
     return *s_slot;
 }

@@ -84,6 +84,16 @@ class Selector:
         assert self.params.shape == (ss.MLP_PARAMS,)
         self.device = device
         self.meta = {}
+        # "op:mode" -> configurations with training targets; an output slot
+        # that never had a target carries no information, so choices stay
+        # within these (None: the library's count).
+        self.cfg_counts = None
+
+    def n_cfgs(self, op: str, mode: str) -> int:
+        cnt = ss.ss_config_count(ss.OPS[op], ss.MODES[mode])
+        if self.cfg_counts is not None:
+            cnt = min(cnt, int(self.cfg_counts.get(f"{op}:{mode}", 0)))
+        return cnt
 
     # ----------------------------------------------------------- training
     def train(self, X, T, M, steps=3000, lr=3e-3, log_every=0, log=print):
@@ -100,6 +110,7 @@ class Selector:
         wb = ss.ss_mlp_workspace_size(rows)
         W = torch.empty(max(wb, 4), dtype=torch.uint8, device=dev)
         total = float(M.sum())
+        self.cfg_counts = trained_cfg_counts(X, M)
         hist = []
         for step in range(1, steps + 1):
             ss.ss_mlp_grad(P.data_ptr(), rows, dX.data_ptr(), dT.data_ptr(), dM.data_ptr(), total,
@@ -132,7 +143,7 @@ class Selector:
         rows, idx = [], []
         for qi, (op, n, batch) in enumerate(queries):
             for mode in MODE_ORDER:
-                cnt = ss.ss_config_count(ss.OPS[op], ss.MODES[mode])
+                cnt = self.n_cfgs(op, mode)
                 if cnt <= 0:
                     continue
                 rows.append(features(op, n, batch, mode))
@@ -167,7 +178,7 @@ class Selector:
         want = [k for k in range(nbins) if counts[k] > 0]
         rows, cand = [], []
         for mode in MODE_ORDER:
-            cnt = ss.ss_config_count(ss.OPS[op], ss.MODES[mode])
+            cnt = self.n_cfgs(op, mode)
             if cnt <= 0:
                 continue
             cand.append((mode, cnt))
@@ -202,14 +213,30 @@ class Selector:
         with open(path + ".json", "w") as f:
             json.dump({"params": os.path.basename(path) + ".npy", "n_params": int(self.params.size),
                        "features": "op one-hot, log2(n)/9, log2(batch)/14, mode one-hot",
-                       "op_order": OP_ORDER, "mode_order": MODE_ORDER, **meta}, f, indent=1)
+                       "op_order": OP_ORDER, "mode_order": MODE_ORDER,
+                       "cfg_counts": self.cfg_counts, **meta}, f, indent=1)
 
     @classmethod
     def load(cls, path: str, device="cuda"):
         s = cls(np.load(path + ".npy"), device=device)
         with open(path + ".json") as f:
             s.meta = json.load(f)
+        s.cfg_counts = s.meta.get("cfg_counts")
         return s
+
+
+def trained_cfg_counts(X, M):
+    """{"op:mode": 1 + the highest configuration id with a target} from the
+    one-hot op and mode features of the training rows."""
+    out = {}
+    for x, m in zip(np.asarray(X), np.asarray(M)):
+        op = OP_ORDER[int(np.argmax(x[0:3]))]
+        mode = MODE_ORDER[int(np.argmax(x[5:5 + len(MODE_ORDER)]))]
+        nz = np.nonzero(m > 0)[0]
+        if nz.size:
+            key = f"{op}:{mode}"
+            out[key] = max(out.get(key, 0), int(nz[-1]) + 1)
+    return out
 
 
 def counts_by_bin(n, nbins: int = ss.NUM_BINS):

@@ -27,7 +27,7 @@ def run(op, pk, mode=ss.MODE_FP64, cfg=ss.CFG_DEFAULT, **kw):
 
 
 @pytest.mark.parametrize("op", ["potrf", "trsyl", "trlyap"])
-@pytest.mark.parametrize("cfg", list(range(5)))
+@pytest.mark.parametrize("cfg", list(range(8)))
 def test_fp64_every_config_edge_sizes(op, cfg):
     n = np.array(EDGE_SIZES, dtype=np.int32)
     pk = inputs.make_batch(op, n, seed=10 + cfg)

@@ -24,7 +24,7 @@ def test_cuda_inference_makes_the_oracle_choices():
     entries = tune.load(DB)["entries"]
     buckets = sorted({(e["op"], e["bin"], e["batch"]) for e in entries})
     got = [(m, c) for m, c, _ in s.choose_many([(op, sel.bin_center(k), b) for op, k, b in buckets])]
-    ref = choices_with_oracle_forward(s.params.astype(np.float64), buckets)
+    ref = choices_with_oracle_forward(s.params.astype(np.float64), buckets, s.cfg_counts)
     same = sum(g == r for g, r in zip(got, ref))
     assert same >= len(buckets) - 1     # an FP32 near-tie may flip one choice
 

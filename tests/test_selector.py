@@ -2,6 +2,7 @@
 selector gains, evaluated on the tuning database measured on a GB300 (no GPU
 needed: the committed network is evaluated with the oracle's FP64 forward)."""
 import math
+import json
 import os
 
 import numpy as np
@@ -54,12 +55,14 @@ def test_dataset_exhaustive_table_and_regret():
     assert rep["buckets"] == 6 and rep["max_regret"] > 0 and rep["mean_regret"] > 0
 
 
-def choices_with_oracle_forward(params, buckets):
+def choices_with_oracle_forward(params, buckets, cfg_counts):
     out = []
     for op, k, batch in buckets:
         best = None
         for mode in sel.MODE_ORDER:
-            cnt = ss.ss_config_count(ss.OPS[op], ss.MODES[mode])
+            cnt = min(ss.ss_config_count(ss.OPS[op], ss.MODES[mode]), cfg_counts.get(f"{op}:{mode}", 0))
+            if cnt <= 0:
+                continue
             y, _ = mlp.forward(params, sel.features(op, sel.bin_center(k), batch, mode)[None, :])
             c = int(np.argmin(y[0, :cnt]))
             if best is None or y[0, c] < best[2]:
@@ -72,10 +75,12 @@ def choices_with_oracle_forward(params, buckets):
 def test_trained_selector_gain_and_regret_on_measured_gb300_timings():
     entries = tune.load(DB)["entries"]
     params = np.load(WEIGHTS + ".npy").astype(np.float64)
+    with open(WEIGHTS + ".json") as f:
+        counts = json.load(f)["cfg_counts"]
     held = sorted({(e["op"], e["bin"], e["batch"]) for e in entries if e["bin"] > sel.TRAIN_MAX_BIN})
     train = sorted({(e["op"], e["bin"], e["batch"]) for e in entries if e["bin"] <= sel.TRAIN_MAX_BIN})
-    r_held = sel.regret_report(choices_with_oracle_forward(params, held), entries, held)
-    r_train = sel.regret_report(choices_with_oracle_forward(params, train), entries, train)
+    r_held = sel.regret_report(choices_with_oracle_forward(params, held, counts), entries, held)
+    r_train = sel.regret_report(choices_with_oracle_forward(params, train, counts), entries, train)
     # The network never saw the held-out sizes (n > 128); it must still beat
     # the fixed FP64 default and stay near the exhaustive search.
     assert r_held["buckets"] == len(held) > 0
@@ -83,3 +88,13 @@ def test_trained_selector_gain_and_regret_on_measured_gb300_timings():
     assert r_held["mean_regret"] <= 0.15
     assert r_train["geomean_gain_over_default"] >= 1.0
     assert r_train["mean_regret"] <= 0.10
+
+
+def test_trained_cfg_counts_follow_the_mask():
+    ent = synthetic_entries()
+    X, T, M, keys = sel.dataset(ent)
+    c = sel.trained_cfg_counts(X, M)
+    for key in {f"{op}:{mode}" for op, _, _, mode in keys}:
+        op, mode = key.split(":")
+        want = 1 + max(e["cfg"] for e in ent if e["op"] == op and e["mode"] == mode)
+        assert c[key] == want
