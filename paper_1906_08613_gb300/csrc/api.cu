@@ -20,12 +20,16 @@ long long mixed_scratch_per_n2(int op, int mode);
 
 namespace {
 
-// variant: 0 = CTA-wide diagonal-block work, 1 = one warp (shorter chain).
+// variant: 0 = CTA-wide diagonal-block work, 1 = one warp (shorter chain),
+// 2 = warp-specialised pipeline (one diagonal warp + (threads-32)/32 update
+// warps; Sylvester and Lyapunov only, so Cholesky has the first eight).
 const Config kFp64Configs[] = {
     {8, 64, 0}, {16, 64, 0}, {16, 128, 0}, {32, 128, 0}, {32, 256, 0},
     {16, 64, 1}, {16, 128, 1}, {32, 128, 1},
+    {16, 160, 2}, {16, 96, 2}, {32, 160, 2},
 };
 constexpr int kNumFp64 = sizeof(kFp64Configs) / sizeof(kFp64Configs[0]);
+constexpr int kNumFp64Potrf = 8;
 
 int host_bin(int n) { int k = 0; while ((1 << k) < n) ++k; return k; }
 
@@ -126,7 +130,7 @@ bool profile_pair(cudaEvent_t *a, cudaEvent_t *b)
 
 int config_count(int op, int mode)
 {
-    if (mode == SS_MODE_FP64) return kNumFp64;
+    if (mode == SS_MODE_FP64) return op == SS_OP_POTRF ? kNumFp64Potrf : kNumFp64;
     return mixed_config_count(op, mode);
 }
 

@@ -479,6 +479,9 @@ cudaError_t launch_potrf_fp64(const Operands &o, const Sched &s, const Launch &l
 
 cudaError_t launch_syl_fp64(const Operands &o, const Sched &s, const Launch &l, cudaStream_t st, bool lyap)
 {
+    const Config *c = config_get(lyap ? SS_OP_TRLYAP : SS_OP_TRSYL, SS_MODE_FP64, l.cfg);
+    if (c != nullptr && c->variant == 2)
+        return launch_syl_fp64_ws(c->block, (c->threads - 32) / 32, lyap, o, s, l, st);
     switch (l.cfg) {
 #define CASE(id, B, T, V)                                                                                \
     case id:                                                                                             \

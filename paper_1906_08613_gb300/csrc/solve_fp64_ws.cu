@@ -1,0 +1,475 @@
+// FP64 triangular Sylvester (L X + X U = C) and Lyapunov (L X + X L^T = S)
+// with warp-specialised CTAs.
+//
+// The blocked lazy algorithm (the Bartels-Stewart back substitution of the
+// paper's triangular Sylvester and Lyapunov solves, done block by block)
+// alternates two kinds of work per B x B block (I, J):
+//
+//   T_IJ = C_IJ - sum_{K<I} L_IK X_KJ - sum_{K<J} X_IK U_KJ   (block updates)
+//   L_II X_IJ + X_IJ U_JJ = T_IJ                             (diagonal block)
+//
+// The updates are plain FMA streams; the diagonal-block solve is a wavefront
+// whose dependent chain of FP64 operations, queued behind other warps' FMAs in
+// the SM's narrow FP64 pipe, makes it latency-bound.  Done one after the other
+// under CTA-wide barriers (solve_fp64.cu), the update warps sit idle during
+// every wavefront.  Here warp 0 (the diagonal warp) only solves diagonal
+// blocks and warps 1..NU (the update warps) only form right-hand sides, in the
+// same row-by-row block order.  While the diagonal warp solves block t, the
+// update warps already form T for block t+1 except the one term that needs
+// X of block t (K = J-1 of the second sum), which they add as soon as block t
+// is done.  The two roles meet at two named barriers per block:
+//
+//   barrier 2 "T ready": update warps arrive, the diagonal warp waits;
+//   barrier 3 "X ready": the diagonal warp arrives, the update warps wait.
+//
+// Each role makes exactly one arrival at each of them per block (the update
+// warps wait once more after their last block), so the phases of a barrier
+// never overlap.  Barrier 1 synchronises the update warps' tile staging.
+// T and X of consecutive blocks alternate between two shared tiles.
+#include "ss_internal.h"
+#include "ss_device.cuh"
+
+namespace ss {
+namespace {
+
+constexpr int kBarUpd = 1, kBarT = 2, kBarX = 3;
+
+__device__ __forceinline__ void named_sync(int id, int count)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void named_arrive(int id, int count)
+{
+    __threadfence_block();
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// Largest |p_ii| over i < n (all threads of the CTA take part).
+__device__ __forceinline__ double max_abs_diag(const double *P, long ld, int n, double *s_red)
+{
+    double m = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, fabs(P[i + (long)i * ld]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    double r = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = fmax(r, s_red[w]);
+    __syncthreads();
+    return r;
+}
+
+// ------------------------------------------------------------ diagonal warp
+
+// Stage the lower (lower = true) or upper triangle of the m x m block at G
+// into tile S with the 32 lanes of one warp; zero elsewhere.
+template <int B>
+__device__ __forceinline__ void warp_stage_tri(double *S, const double *G, long ldg, int m, bool lower, int lane)
+{
+    constexpr int LD = Tile<B>::LD;
+    for (int e = lane; e < B * B; e += 32) {
+        const int r = e % B, c = e / B;
+        const bool keep = lower ? (r >= c) : (r <= c);
+        S[r + c * LD] = (r < m && c < m && keep) ? G[r + (long)c * ldg] : 0.0;
+    }
+}
+
+// In place: Lt Y + Y Ut = T for the m x nn block in sT, Lt = sL lower, Ut =
+// sU upper or (UT) the transpose of the lower sU, reciprocal divisors in sR.
+// Anti-diagonal d = i + j at a time; each entry is a dot product of d terms,
+// split over `split` lanes (power of two, at most 32 / entries and at most
+// d) with two partial sums per lane to halve the dependent chain.
+template <int B, bool UT>
+__device__ void warp_diag_solve(const double *sL, const double *sU, double *sT, const double *sR, int m,
+                                int nn, int lane)
+{
+    constexpr int LD = Tile<B>::LD;
+    for (int d = 0; d <= m + nn - 2; ++d) {
+        const int ilo = max(0, d - nn + 1), ihi = min(d, m - 1);
+        const int cnt = ihi - ilo + 1;
+        int split = cnt >= 32 ? 1 : pow2_floor(32 / cnt);
+        const int byLen = pow2_floor(d > 1 ? d : 1);
+        split = split < byLen ? split : byLen;
+        const int idx = lane / split, part = lane % split;
+        const bool act = idx < cnt;
+        const int i = ilo + (act ? idx : 0), j = d - i;
+        double s0 = 0.0, s1 = 0.0;
+        if (act) {
+            int t = part;
+            for (; t + split < d; t += 2 * split) {
+                const int t1 = t + split;
+                const double a0 = t < i ? sL[i + t * LD] : sT[i + (t - i) * LD];
+                const double b0 = t < i ? sT[t + j * LD] : (UT ? sU[j + (t - i) * LD] : sU[(t - i) + j * LD]);
+                const double a1 = t1 < i ? sL[i + t1 * LD] : sT[i + (t1 - i) * LD];
+                const double b1 = t1 < i ? sT[t1 + j * LD] : (UT ? sU[j + (t1 - i) * LD] : sU[(t1 - i) + j * LD]);
+                s0 = fma(a0, b0, s0);
+                s1 = fma(a1, b1, s1);
+            }
+            if (t < d) {
+                const double a0 = t < i ? sL[i + t * LD] : sT[i + (t - i) * LD];
+                const double b0 = t < i ? sT[t + j * LD] : (UT ? sU[j + (t - i) * LD] : sU[(t - i) + j * LD]);
+                s0 = fma(a0, b0, s0);
+            }
+        }
+        const double s = group_sum(s0 + s1, split);
+        if (act && part == 0) sT[i + j * LD] = (sT[i + j * LD] - s) * sR[i + j * LD];
+        __syncwarp();
+    }
+}
+
+// ------------------------------------------------------------- update warps
+
+// Outputs of one update thread: flat index e = ut + TU*r over the m x nn
+// valid entries of the block (column-major), as in Slots.
+template <int B, int TU>
+struct OutMap {
+    static constexpr int E = B * B / TU;
+    int row[E], col[E];
+    unsigned valid;
+    __device__ __forceinline__ void set(int m, int nn, int ut)
+    {
+        valid = 0u;
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int e = ut + TU * r;
+            row[r] = 0;
+            col[r] = 0;
+            if (e < m * nn) {
+                row[r] = e % m;
+                col[r] = e / m;
+                valid |= 1u << r;
+            }
+        }
+    }
+    __device__ __forceinline__ bool ok(int r) const { return (valid >> r) & 1u; }
+};
+
+// Where one operand tile of a block-update step comes from: rows x cols at
+// P (leading dimension ld); sym: the symmetric diagonal block whose lower
+// triangle is stored (rows = cols = m).
+struct Src {
+    const double *P;
+    long ld;
+    int rows, cols;
+    bool sym;
+};
+
+// The tile elements one update thread loads: e = ut + TU*q, (r, c) = (e % B, e / B).
+template <int B, int TU>
+struct Prefetch {
+    static constexpr int PE = B * B / TU;
+    double a[PE], b[PE];
+
+    __device__ __forceinline__ static double get(const Src &s, int r, int c)
+    {
+        if (r >= s.rows || c >= s.cols) return 0.0;
+        if (s.sym && r < c) return s.P[c + (long)r * s.ld];
+        return s.P[r + (long)c * s.ld];
+    }
+    __device__ __forceinline__ void load(const Src &sa, const Src &sb, bool has_a, int ut)
+    {
+#pragma unroll
+        for (int q = 0; q < PE; ++q) {
+            const int e = ut + TU * q, r = e % B, c = e / B;
+            a[q] = has_a ? get(sa, r, c) : 0.0;
+            b[q] = get(sb, r, c);
+        }
+    }
+    __device__ __forceinline__ void store(double *tA, double *tB, bool has_a, int ut) const
+    {
+        constexpr int LD = Tile<B>::LD;
+#pragma unroll
+        for (int q = 0; q < PE; ++q) {
+            const int e = ut + TU * q, r = e % B, c = e / B;
+            if (has_a) tA[r + c * LD] = a[q];
+            tB[r + c * LD] = b[q];
+        }
+    }
+};
+
+// acc -= A * op(Bm) over B terms, A(row, k) = A[row + k*LD],
+// op(Bm)(k, col) = TB ? Bm[col + k*LD] : Bm[k + col*LD]; even and odd k go to
+// separate accumulators (two independent FMA chains per output).
+template <int B, int TU, bool TB>
+__device__ __forceinline__ void upd_fma(double (&ae)[B * B / TU], double (&ao)[B * B / TU],
+                                        const OutMap<B, TU> &om, const double *A, const double *Bm)
+{
+    constexpr int LD = Tile<B>::LD;
+    constexpr int E = B * B / TU;
+#pragma unroll 2
+    for (int k = 0; k < B; k += 2) {
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            if (om.ok(r)) {
+                const double a0 = A[om.row[r] + k * LD], a1 = A[om.row[r] + (k + 1) * LD];
+                const double b0 = TB ? Bm[om.col[r] + k * LD] : Bm[k + om.col[r] * LD];
+                const double b1 = TB ? Bm[om.col[r] + (k + 1) * LD] : Bm[k + 1 + om.col[r] * LD];
+                ae[r] = fma(-a0, b0, ae[r]);
+                ao[r] = fma(-a1, b1, ao[r]);
+            }
+        }
+    }
+}
+
+template <int B, int TU>
+__device__ __forceinline__ void upd_fma_rt(bool tb, double (&ae)[B * B / TU], double (&ao)[B * B / TU],
+                                           const OutMap<B, TU> &om, const double *A, const double *Bm)
+{
+    if (tb) upd_fma<B, TU, true>(ae, ao, om, A, Bm);
+    else    upd_fma<B, TU, false>(ae, ao, om, A, Bm);
+}
+
+// Operands of bulk step s of block (I, J): s < P1 is K = s of the first sum,
+// then K = s - P1 (< J - 1) of the second.  P1 = I, except for a Lyapunov
+// diagonal block, whose first-sum term K = I-1 reads X_{I-1,I} = X_{I,I-1}^T,
+// the block solved just before it: that term joins the last phase.  *tb: use
+// op(Bm) transposed.
+template <int B, bool LYAP>
+__device__ __forceinline__ void step_src(int s, int P1, int I, int J, int mI, int nJ, const double *L, long ldl,
+                                         const double *U, long ldu, const double *X, long ldx, Src &a, Src &b,
+                                         bool &tb)
+{
+    const int i0 = I * B, j0 = J * B;
+    if (s < P1) {
+        const int k0 = s * B;
+        a = Src{L + i0 + (long)k0 * ldl, ldl, mI, B, false};                 // L_IK
+        if (!LYAP || s > J) {
+            b = Src{X + k0 + (long)j0 * ldx, ldx, B, nJ, false};             // X_KJ
+            tb = false;
+        } else if (s == J) {
+            b = Src{X + j0 + (long)j0 * ldx, ldx, nJ, nJ, true};             // X_JJ (symmetric)
+            tb = false;
+        } else {
+            b = Src{X + j0 + (long)k0 * ldx, ldx, nJ, B, false};             // X_JK, used transposed
+            tb = true;
+        }
+    } else {
+        const int k0 = (s - P1) * B;
+        a = Src{X + i0 + (long)k0 * ldx, ldx, mI, B, false};                 // X_IK
+        if (!LYAP) {
+            b = Src{U + k0 + (long)j0 * ldu, ldu, B, nJ, false};             // U_KJ
+            tb = false;
+        } else {
+            b = Src{L + j0 + (long)k0 * ldl, ldl, nJ, B, false};             // L_JK, used transposed
+            tb = true;
+        }
+    }
+}
+
+// The staged tile of the last phase: U_{J-1,J} (Lyapunov: L_{J,J-1}, used
+// transposed) for J > 0; for Lyapunov block (1, 0): L_10 (not transposed).
+template <int B, bool LYAP>
+__device__ __forceinline__ void last_src_t(int I, int J, int mI, int nJ, const double *L, long ldl,
+                                           const double *U, long ldu, Src &b, bool &tb)
+{
+    const int j0 = J * B;
+    if (J == 0) {
+        b = Src{L + I * B, ldl, mI, B, false};
+        tb = false;
+        return;
+    }
+    const int k0 = (J - 1) * B;
+    b = LYAP ? Src{L + j0 + (long)k0 * ldl, ldl, nJ, B, false} : Src{U + k0 + (long)j0 * ldu, ldu, B, nJ, false};
+    tb = LYAP;
+}
+
+template <int B>
+constexpr int ws_tiles() { return 9; }
+template <int B>
+constexpr size_t ws_smem_bytes() { return (size_t)ws_tiles<B>() * Tile<B>::SZ * sizeof(double) + 32 * sizeof(double); }
+
+// One instance.  Shared tiles: sT[2] (T / X of consecutive blocks), sL, sU,
+// sR (diagonal warp), sA[2], sB[2] (update warps' staging).
+template <int B, int NU, bool LYAP>
+__device__ void syl_ws_instance(int n, const double *L, long ldl, const double *U, long ldu, const double *C,
+                                long ldc, double *X, long ldx, int *info, double *sm)
+{
+    constexpr int LD = Tile<B>::LD, SZ = Tile<B>::SZ;
+    constexpr int TU = 32 * NU, TALL = TU + 32;
+    double *sT0 = sm, *sL = sm + 2 * SZ, *sU = sm + 3 * SZ, *sR = sm + 4 * SZ;
+    double *sA0 = sm + 5 * SZ, *sB0 = sm + 7 * SZ;
+    double *s_red = sm + 9 * SZ;
+    const int nb = (n + B - 1) / B;
+
+    double md = max_abs_diag(L, ldl, n, s_red);
+    if (!LYAP) md = fmax(md, max_abs_diag(U, ldu, n, s_red));
+    const double delta = divisor_delta(n, md);
+
+    if (threadIdx.x < 32) {
+        // ------------------------------------------------ diagonal warp
+        const int lane = threadIdx.x;
+        int bad = 0, t = 0;
+        for (int I = 0; I < nb; ++I) {
+            const int mI = min(B, n - I * B), i0 = I * B;
+            warp_stage_tri<B>(sL, L + i0 + (long)i0 * ldl, ldl, mI, true, lane);
+            const int jend = LYAP ? I + 1 : nb;
+            for (int J = 0; J < jend; ++J, ++t) {
+                const int nJ = min(B, n - J * B), j0 = J * B;
+                if (!LYAP) warp_stage_tri<B>(sU, U + j0 + (long)j0 * ldu, ldu, nJ, false, lane);
+                else       warp_stage_tri<B>(sU, L + j0 + (long)j0 * ldl, ldl, nJ, true, lane);
+                __syncwarp();
+                for (int e = lane; e < mI * nJ; e += 32) {
+                    const int i = e % mI, j = e / mI;
+                    const double dd = sL[i + i * LD] + sU[j + j * LD];
+                    if (!(fabs(dd) > delta)) bad = 1;
+                    sR[i + j * LD] = 1.0 / dd;
+                }
+                __syncwarp();
+                double *sT = sT0 + (t & 1) * SZ;
+                named_sync(kBarT, TALL);                   // T of block t is in sT
+                warp_diag_solve<B, LYAP>(sL, sU, sT, sR, mI, nJ, lane);
+                for (int e = lane; e < mI * nJ; e += 32) {
+                    const int r = e % mI, c = e / mI;
+                    if (!LYAP || I != J || r >= c) X[(i0 + r) + (long)(j0 + c) * ldx] = sT[r + c * LD];
+                }
+                named_arrive(kBarX, TALL);                 // X of block t is final
+            }
+        }
+        bad = __any_sync(0xffffffffu, bad);
+        if (lane == 0) *info = bad ? 1 : 0;
+    } else {
+        // ------------------------------------------------- update warps
+        constexpr int E = B * B / TU;
+        const int ut = threadIdx.x - 32;
+        OutMap<B, TU> om;
+        Prefetch<B, TU> pf;
+        int t = 0;
+        for (int I = 0; I < nb; ++I) {
+            const int mI = min(B, n - I * B), i0 = I * B;
+            const int jend = LYAP ? I + 1 : nb;
+            for (int J = 0; J < jend; ++J, ++t) {
+                const int nJ = min(B, n - J * B), j0 = J * B;
+                om.set(mI, nJ, ut);
+                double ae[E], ao[E];
+#pragma unroll
+                for (int r = 0; r < E; ++r) {
+                    ao[r] = 0.0;
+                    ae[r] = 0.0;
+                    if (om.ok(r)) {
+                        int rr = om.row[r], cc = om.col[r];
+                        if (LYAP && I == J && rr < cc) { const int x = rr; rr = cc; cc = x; }
+                        ae[r] = C[(i0 + rr) + (long)(j0 + cc) * ldc];
+                    }
+                }
+                // Bulk steps, then (J > 0) the staged operand of the last phase.
+                // Lyapunov blocks right after the block whose X they need in
+                // the first sum: the diagonal block (I, I) (term K = I-1) and
+                // block (1, 0) (term K = 0, X_00 solved just before it).
+                const bool ldiag = LYAP && I == J && I > 0;
+                const bool lfirst = LYAP && I == 1 && J == 0;
+                const int P1 = (ldiag || lfirst) ? I - 1 : I;
+                const bool has_last = J > 0 || lfirst;
+                const int nsteps = P1 + (J > 0 ? J - 1 : 0);
+                const int nload = nsteps + (has_last ? 1 : 0);
+                Src sa, sb;
+                bool tb = false, tb_next = false;
+                if (nload > 0) {
+                    if (nsteps > 0) step_src<B, LYAP>(0, P1, I, J, mI, nJ, L, ldl, U, ldu, X, ldx, sa, sb, tb_next);
+                    else last_src_t<B, LYAP>(I, J, mI, nJ, L, ldl, U, ldu, sb, tb_next);
+                    pf.load(sa, sb, nsteps > 0, ut);
+                    pf.store(sA0, sB0, nsteps > 0, ut);
+                    named_sync(kBarUpd, TU);
+                }
+                for (int s = 0; s < nsteps; ++s) {
+                    tb = tb_next;
+                    const int buf = s & 1;
+                    const bool more = s + 1 < nload;
+                    const bool next_bulk = s + 1 < nsteps;
+                    if (more) {
+                        if (next_bulk) step_src<B, LYAP>(s + 1, P1, I, J, mI, nJ, L, ldl, U, ldu, X, ldx, sa, sb, tb_next);
+                        else last_src_t<B, LYAP>(I, J, mI, nJ, L, ldl, U, ldu, sb, tb_next);
+                        pf.load(sa, sb, next_bulk, ut);
+                    }
+                    upd_fma_rt<B, TU>(tb, ae, ao, om, sA0 + buf * SZ, sB0 + buf * SZ);
+                    if (more) pf.store(sA0 + (buf ^ 1) * SZ, sB0 + (buf ^ 1) * SZ, next_bulk, ut);
+                    named_sync(kBarUpd, TU);
+                }
+                if (t > 0) named_sync(kBarX, TALL);        // X of block t-1 is final
+                if (has_last) {
+                    // Last phase: the X block of block t-1 is still in shared
+                    // memory (for block (1, 0) of Lyapunov: all of X_00).
+                    const double *sXp = sT0 + ((t - 1) & 1) * SZ;
+                    const double *sV = sB0 + (nsteps & 1) * SZ;
+                    if (J > 0) {
+                        upd_fma_rt<B, TU>(tb_next, ae, ao, om, sXp, sV);      // X_{I,J-1} U_{J-1,J}
+                        if (ldiag) upd_fma<B, TU, true>(ae, ao, om, sV, sXp); // L_{I,I-1} X_{I,I-1}^T
+                    } else {
+                        upd_fma<B, TU, false>(ae, ao, om, sV, sXp);           // L_10 X_00
+                    }
+                }
+                double *sT = sT0 + (t & 1) * SZ;
+#pragma unroll
+                for (int r = 0; r < E; ++r)
+                    if (om.ok(r)) sT[om.row[r] + om.col[r] * LD] = ae[r] + ao[r];
+                named_sync(kBarUpd, TU);                   // staging tiles free again
+                named_arrive(kBarT, TALL);                 // T of block t is in sT
+            }
+        }
+        named_sync(kBarX, TALL);                           // X of the last block is final
+    }
+}
+
+__device__ __forceinline__ bool next_instance(const Sched &s, int group, int *s_slot, int &b)
+{
+    const int lo = s.meta[META_RANGE + 2 * group], hi = s.meta[META_RANGE + 2 * group + 1];
+    const int w = lo + claim_slot(s.meta + META_HEAD + group, s_slot);
+    if (w >= hi) return false;
+    b = s.perm[w];
+    return true;
+}
+
+// MINB: CTAs per SM the register allocation must allow (the two roles share
+// one register budget, set by the larger of them).
+template <int B, int NU, bool LYAP, int MINB>
+__global__ void __launch_bounds__(32 * NU + 32, MINB) syl_ws_kernel(Operands o, Sched s, int group)
+{
+    extern __shared__ double sm[];
+    __shared__ int s_slot;
+    int b;
+    claim_init(&s_slot);
+    while (next_instance(s, group, &s_slot, b)) {
+        const int n = o.n[b];
+        if (n == 0) { if (threadIdx.x == 0) o.info[b] = 0; continue; }
+        syl_ws_instance<B, NU, LYAP>(n, o.A[b], o.lda[b], LYAP ? nullptr : o.U[b], LYAP ? 0 : o.ldu[b], o.C[b],
+                                     o.ldc[b], o.X[b], o.ldx[b], o.info + b, sm);
+    }
+}
+
+template <typename K>
+cudaError_t launch_ws(K kernel, int threads, size_t smem, int batch, cudaStream_t st, const Operands &o,
+                      const Sched &s, int group)
+{
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    long grid = (long)per_sm * sm_count();
+    if (grid > batch) grid = batch;
+    if (grid < 1) grid = 1;
+    kernel<<<(int)grid, threads, smem, st>>>(o, s, group);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// Warp-specialised configurations: block B, NU update warps (+1 diagonal warp).
+cudaError_t launch_syl_fp64_ws(int block, int nu, bool lyap, const Operands &o, const Sched &s, const Launch &l,
+                               cudaStream_t st)
+{
+#define WS_CASE(BB, NN, MB)                                                                                \
+    if (block == BB && nu == NN)                                                                           \
+        return lyap ? launch_ws(syl_ws_kernel<BB, NN, true, MB>, 32 * NN + 32, ws_smem_bytes<BB>(), l.batch, \
+                                st, o, s, l.group)                                                         \
+                    : launch_ws(syl_ws_kernel<BB, NN, false, MB>, 32 * NN + 32, ws_smem_bytes<BB>(), l.batch, \
+                                st, o, s, l.group);
+    WS_CASE(16, 4, 6)
+    WS_CASE(16, 2, 8)
+    WS_CASE(32, 4, 2)
+#undef WS_CASE
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace ss

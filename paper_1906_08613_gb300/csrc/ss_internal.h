@@ -82,6 +82,11 @@ cudaError_t launch_potrf(const Operands &o, const Sched &s, const Launch &l, cud
 cudaError_t launch_trsyl(const Operands &o, const Sched &s, const Launch &l, cudaStream_t st);
 cudaError_t launch_trlyap(const Operands &o, const Sched &s, const Launch &l, cudaStream_t st);
 
+// FP64 Sylvester / Lyapunov with warp-specialised CTAs (block B, nu update
+// warps plus one diagonal warp).
+cudaError_t launch_syl_fp64_ws(int block, int nu, bool lyap, const Operands &o, const Sched &s, const Launch &l,
+                               cudaStream_t st);
+
 // Number of SMs of the current device (cached per device).
 int sm_count();
 

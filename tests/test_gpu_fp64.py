@@ -27,8 +27,10 @@ def run(op, pk, mode=ss.MODE_FP64, cfg=ss.CFG_DEFAULT, **kw):
 
 
 @pytest.mark.parametrize("op", ["potrf", "trsyl", "trlyap"])
-@pytest.mark.parametrize("cfg", list(range(8)))
+@pytest.mark.parametrize("cfg", list(range(11)))
 def test_fp64_every_config_edge_sizes(op, cfg):
+    if cfg >= ss.ss_config_count(ss.OPS[op], ss.MODE_FP64):
+        pytest.skip("no such configuration for this operation")
     n = np.array(EDGE_SIZES, dtype=np.int32)
     pk = inputs.make_batch(op, n, seed=10 + cfg)
     x, info = run(op, pk, cfg=cfg)
@@ -54,6 +56,31 @@ def test_fp64_mixed_sizes_default_and_table(op):
         ss.ss_set_config_table(o, ss.MODE_FP64, [])
     assert np.array_equal(info, rinfo)
     assert_parity(op, pk, x, ref, sentinel=SENT)
+
+
+WS_CFGS = [c for c in range(11) if c < ss.ss_config_count(ss.OP_TRSYL, ss.MODE_FP64)
+           and ss.ss_config_describe(ss.OP_TRSYL, ss.MODE_FP64, c)[2] == 2]
+
+
+@pytest.mark.parametrize("op", ["trsyl", "trlyap"])
+@pytest.mark.parametrize("cfg", WS_CFGS)
+def test_fp64_warp_specialised_queue_and_in_place(op, cfg):
+    # More instances than resident CTAs (the queue's dynamic phase), sizes
+    # from one block to many with ragged edges, then the same batch in place.
+    n = inputs.sizes_uniform(1100, 1, 160, seed=77)
+    pk = inputs.make_batch(op, n, seed=78)
+    ref, rinfo = oracle_batch(op, pk)
+    x, info = run(op, pk, cfg=cfg)
+    assert np.array_equal(info, rinfo)
+    assert_parity(op, pk, x, ref, sentinel=SENT)
+    from paper_1906_08613_gb300.device import DeviceBatch
+    sub = inputs.make_batch(op, n[:64], seed=79)
+    ref2, _ = oracle_batch(op, sub)
+    db = DeviceBatch(sub.n, sub.off, sub.ops, op, alias_rhs=True)
+    db.solve(cfg=cfg)
+    torch.cuda.synchronize()
+    assert np.all(db.info_host() == 0)
+    assert_parity(op, sub, db.x_host(), ref2)
 
 
 @pytest.mark.parametrize("op", ["potrf", "trsyl", "trlyap"])
