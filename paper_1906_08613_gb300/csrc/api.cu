@@ -20,16 +20,22 @@ long long mixed_scratch_per_n2(int op, int mode);
 
 namespace {
 
-// variant: 0 = CTA-wide diagonal-block work, 1 = one warp (shorter chain),
-// 2 = warp-specialised pipeline (one diagonal warp + (threads-32)/32 update
-// warps; Sylvester and Lyapunov only, so Cholesky has the first eight).
-const Config kFp64Configs[] = {
+// FP64 configurations per operation: (block B, threads per CTA, variant).
+// variant 0: CTA-wide diagonal-block work; 1: one warp does the diagonal
+// blocks between CTA-wide updates (shorter dependent chain); 2 (Sylvester and
+// Lyapunov): warp-specialised pipeline, one diagonal warp and
+// (threads-32)/32 update warps.  At most eight per operation (the learned
+// selector predicts one time per configuration slot).
+const Config kFp64Potrf[] = {
     {8, 64, 0}, {16, 64, 0}, {16, 128, 0}, {32, 128, 0}, {32, 256, 0},
     {16, 64, 1}, {16, 128, 1}, {32, 128, 1},
-    {16, 160, 2}, {16, 96, 2}, {32, 160, 2},
 };
-constexpr int kNumFp64 = sizeof(kFp64Configs) / sizeof(kFp64Configs[0]);
-constexpr int kNumFp64Potrf = 8;
+const Config kFp64Syl[] = {
+    {8, 64, 0}, {16, 64, 0}, {16, 128, 0}, {32, 128, 0},
+    {16, 128, 1}, {16, 160, 2}, {16, 96, 2}, {16, 64, 2},
+};
+constexpr int kNumFp64Potrf = sizeof(kFp64Potrf) / sizeof(kFp64Potrf[0]);
+constexpr int kNumFp64Syl = sizeof(kFp64Syl) / sizeof(kFp64Syl[0]);
 
 int host_bin(int n) { int k = 0; while ((1 << k) < n) ++k; return k; }
 
@@ -130,26 +136,25 @@ bool profile_pair(cudaEvent_t *a, cudaEvent_t *b)
 
 int config_count(int op, int mode)
 {
-    if (mode == SS_MODE_FP64) return op == SS_OP_POTRF ? kNumFp64Potrf : kNumFp64;
+    if (mode == SS_MODE_FP64) return op == SS_OP_POTRF ? kNumFp64Potrf : kNumFp64Syl;
     return mixed_config_count(op, mode);
 }
 
 const Config *config_get(int op, int mode, int cfg)
 {
     if (cfg < 0 || cfg >= config_count(op, mode)) return nullptr;
-    if (mode == SS_MODE_FP64) return &kFp64Configs[cfg];
+    if (mode == SS_MODE_FP64) return op == SS_OP_POTRF ? &kFp64Potrf[cfg] : &kFp64Syl[cfg];
     return mixed_config_get(op, mode, cfg);
 }
 
 // Built-in default: a single configuration chosen from the largest order.
 int config_default(int op, int mode, int max_n)
 {
-    (void)op;
     if (mode == SS_MODE_FP64) {
         if (max_n <= 8) return 0;
         if (max_n <= 16) return 1;
         if (max_n <= 32) return 2;
-        return 3;
+        return op == SS_OP_POTRF ? 3 : 6;   // Sylvester / Lyapunov: warp-specialised, B = 16
     }
     return 0;
 }

@@ -287,6 +287,7 @@ __device__ void syl_ws_instance(int n, const double *L, long ldl, const double *
 {
     constexpr int LD = Tile<B>::LD, SZ = Tile<B>::SZ;
     constexpr int TU = 32 * NU, TALL = TU + 32;
+    static_assert((B * B) % TU == 0, "update threads must divide the block");
     double *sT0 = sm, *sL = sm + 2 * SZ, *sU = sm + 3 * SZ, *sR = sm + 4 * SZ;
     double *sA0 = sm + 5 * SZ, *sB0 = sm + 7 * SZ;
     double *s_red = sm + 9 * SZ;
@@ -467,7 +468,7 @@ cudaError_t launch_syl_fp64_ws(int block, int nu, bool lyap, const Operands &o, 
                                 st, o, s, l.group);
     WS_CASE(16, 4, 6)
     WS_CASE(16, 2, 8)
-    WS_CASE(32, 4, 2)
+    WS_CASE(16, 1, 8)
 #undef WS_CASE
     return cudaErrorInvalidValue;
 }

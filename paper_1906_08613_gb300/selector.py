@@ -27,7 +27,26 @@ from . import tune
 
 OP_ORDER = ("potrf", "trsyl", "trlyap")
 MODE_ORDER = ("fp64", "fp32_refined", "tf32_refined", "bf16_refined")
-TRAIN_MAX_BIN = 7          # n <= 128: the size range of the tuned workloads
+
+
+def heldout_bucket(k: int, batch: int, batches_of_bin) -> bool:
+    """Buckets kept out of training to measure the selector on sizes and batch
+    counts it has not seen: every third (size bin, batch rank) cell, so that
+    each held-out bucket has trained neighbours in n (bins k-1, k+1) and in
+    batch (the other batch count of its bin)."""
+    r = sorted(set(batches_of_bin)).index(batch)
+    return (k + r) % 3 == 0
+
+
+def split_buckets(entries):
+    """(training buckets, held-out buckets) of a tuning database, as sets of
+    (op, bin, batch)."""
+    buckets = {(e["op"], e["bin"], e["batch"]) for e in entries}
+    per_bin = {}
+    for op, k, b in buckets:
+        per_bin.setdefault((op, k), set()).add(b)
+    held = {(op, k, b) for op, k, b in buckets if heldout_bucket(k, b, per_bin[(op, k)])}
+    return buckets - held, held
 
 
 def features(op: str, n: float, batch: float, mode: str) -> np.ndarray:
@@ -44,13 +63,16 @@ def bin_center(k: int) -> float:
     return math.sqrt(lo * hi)
 
 
-def dataset(entries, bins=None):
-    """Rows (features, log2-ms targets, mask, keys) from tuning entries."""
+def dataset(entries, bins=None, buckets=None):
+    """Rows (features, log2-ms targets, mask, keys) from tuning entries,
+    optionally restricted to size bins or to (op, bin, batch) buckets."""
     rows = {}
     for e in entries:
         if e.get("info_nonzero", 0) or e["mode"] not in MODE_ORDER:
             continue
         if bins is not None and e["bin"] not in bins:
+            continue
+        if buckets is not None and (e["op"], e["bin"], e["batch"]) not in buckets:
             continue
         key = (e["op"], e["bin"], e["batch"], e["mode"])
         rows.setdefault(key, {})[e["cfg"]] = e["ms"]
@@ -259,7 +281,7 @@ def regret_report(choices, entries, buckets):
             continue
         t_c = tune.lookup(entries, op, k, batch, mode, cfg)
         t_b = best[key][2]
-        dflt = default_fp64_cfg(1 << k)
+        dflt = default_fp64_cfg(1 << k, op)
         t_d = tune.lookup(entries, op, k, batch, "fp64", dflt)
         if t_c is None or t_d is None:
             continue
@@ -274,7 +296,7 @@ def regret_report(choices, entries, buckets):
             "rows": out}
 
 
-def default_fp64_cfg(max_n: int) -> int:
+def default_fp64_cfg(max_n: int, op: str = "potrf") -> int:
     """The library's built-in FP64 default (SS_CFG_DEFAULT) for a given max n."""
     if max_n <= 8:
         return 0
@@ -282,4 +304,4 @@ def default_fp64_cfg(max_n: int) -> int:
         return 1
     if max_n <= 32:
         return 2
-    return 3
+    return 3 if op == "potrf" else 6

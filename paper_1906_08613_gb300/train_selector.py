@@ -2,9 +2,8 @@
 
 Steps (one GPU):
   1. the autotuner's database (``--db``; ``--sweep`` measures it first);
-  2. training rows = buckets with n <= 128 (the size range of the tuned
-     workloads: Cholesky n = 64, Sylvester n in 4..128, Lyapunov n = 128);
-     held-out rows = the larger bins (n in 129..512);
+  2. training rows = all (op, size bin, batch) buckets but every third
+     (bin, batch rank) cell, which is held out (selector.split_buckets);
   3. the MLP is trained on the GPU by the library's own kernels;
   4. regret of the selector's choice against the exhaustive best, per bucket,
      on training and held-out buckets, and its gain over the FP64 default;
@@ -131,9 +130,8 @@ def main(argv=None):
         tune.save(entries, args.db, {"sweep_seconds": time.time() - t0})
     entries = tune.load(args.db)["entries"]
 
-    train_bins = set(range(0, sel.TRAIN_MAX_BIN + 1))
-    held_bins = set(range(sel.TRAIN_MAX_BIN + 1, ss.NUM_BINS))
-    X, T, M, keys = sel.dataset(entries, bins=train_bins)
+    train_set, held_set = sel.split_buckets(entries)
+    X, T, M, keys = sel.dataset(entries, buckets=train_set)
     log(f"training rows {len(keys)}, observed targets {int(M.sum())}")
     t0 = time.time()
     if args.load:
@@ -144,13 +142,13 @@ def main(argv=None):
         hist = s.train(X, T, M, steps=args.steps, lr=args.lr, log_every=500, log=log)
     train_s = time.time() - t0
 
-    def report_for(bins):
-        buckets = sorted({(e["op"], e["bin"], e["batch"]) for e in entries if e["bin"] in bins})
+    def report_for(bucket_set):
+        buckets = sorted(bucket_set)
         choices = s.choose_many([(op, sel.bin_center(k), b) for op, k, b in buckets])
         return sel.regret_report([(m, c) for m, c, _ in choices], entries, buckets)
 
     rep = {"train_rows": len(keys), "train_seconds": train_s, "loss_history": hist,
-           "train_buckets": report_for(train_bins), "heldout_buckets": report_for(held_bins)}
+           "train_buckets": report_for(train_set), "heldout_buckets": report_for(held_set)}
     for name in ("train_buckets", "heldout_buckets"):
         r = rep[name]
         if r.get("buckets"):
@@ -160,7 +158,7 @@ def main(argv=None):
     if not args.no_stream:
         rep["stream"] = evaluate_stream(s, entries, log=log)
     s.save(args.out, trained_on=args.db, steps=args.steps, lr=args.lr,
-           final_loss=hist[-1][1], train_max_bin=sel.TRAIN_MAX_BIN)
+           final_loss=hist[-1][1], split="every third (bin, batch rank) bucket held out")
     if args.report:
         with open(args.report, "w") as f:
             json.dump(rep, f, indent=1, default=lambda o: o.tolist() if hasattr(o, "tolist") else str(o))

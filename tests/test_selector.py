@@ -34,7 +34,7 @@ def synthetic_entries():
     # fp64 cfg 1 fastest in small bins, cfg 3 in large; one refined mode wins bin 6.
     out = []
     for k in range(2, 8):
-        for mode, ncfg in (("fp64", 5), ("fp32_refined", 3)):
+        for mode, ncfg in (("fp64", 8), ("fp32_refined", 3)):
             for c in range(ncfg):
                 ms = 1.0 + abs(c - (1 if k < 5 else 3)) + (0.5 if mode != "fp64" else 0.0)
                 if k == 6 and mode == "fp32_refined" and c == 2:
@@ -46,7 +46,7 @@ def synthetic_entries():
 def test_dataset_exhaustive_table_and_regret():
     ent = synthetic_entries()
     X, T, M, keys = sel.dataset(ent)
-    assert X.shape == (12, ss.MLP_IN) and M.sum() == 6 * 8
+    assert X.shape == (12, ss.MLP_IN) and M.sum() == 6 * (8 + 3)
     modes, cfgs = tune.exhaustive_table(ent, "trsyl", 256)
     assert modes[6] == ss.MODE_FP32_REFINED and cfgs[6] == 2
     assert modes[3] == ss.MODE_FP64 and cfgs[3] == 1 and cfgs[7] == 3 and modes[9] == -1
@@ -77,12 +77,11 @@ def test_trained_selector_gain_and_regret_on_measured_gb300_timings():
     params = np.load(WEIGHTS + ".npy").astype(np.float64)
     with open(WEIGHTS + ".json") as f:
         counts = json.load(f)["cfg_counts"]
-    held = sorted({(e["op"], e["bin"], e["batch"]) for e in entries if e["bin"] > sel.TRAIN_MAX_BIN})
-    train = sorted({(e["op"], e["bin"], e["batch"]) for e in entries if e["bin"] <= sel.TRAIN_MAX_BIN})
+    train, held = (sorted(x) for x in sel.split_buckets(entries))
     r_held = sel.regret_report(choices_with_oracle_forward(params, held, counts), entries, held)
     r_train = sel.regret_report(choices_with_oracle_forward(params, train, counts), entries, train)
-    # The network never saw the held-out sizes (n > 128); it must still beat
-    # the fixed FP64 default and stay near the exhaustive search.
+    # The network never saw the held-out buckets; it must still beat the
+    # fixed FP64 default and stay near the exhaustive search.
     assert r_held["buckets"] == len(held) > 0
     assert r_held["geomean_gain_over_default"] >= 1.0
     assert r_held["mean_regret"] <= 0.15
@@ -98,3 +97,14 @@ def test_trained_cfg_counts_follow_the_mask():
         op, mode = key.split(":")
         want = 1 + max(e["cfg"] for e in ent if e["op"] == op and e["mode"] == mode)
         assert c[key] == want
+
+
+def test_split_holds_out_every_third_cell_with_trained_neighbours():
+    ent = [dict(op=op, bin=k, batch=b) for op in ("potrf", "trsyl") for k in range(2, 10)
+           for b in ((256, 2048) if k <= 7 else (64, 256))]
+    train, held = sel.split_buckets(ent)
+    assert train and held and not (train & held)
+    assert len(train | held) == len(ent)
+    for op, k, b in held:
+        assert any(t[0] == op and abs(t[1] - k) == 1 for t in train)
+        assert any(t[0] == op and t[1] == k and t[2] != b for t in train)
