@@ -54,8 +54,11 @@ def lib():
             L.oracle_potrf_upper_batch.argtypes = [c_int, ip, llp, dp, dp, ip]
             L.oracle_trsyl_lu_batch.argtypes = [c_int, ip, llp, dp, dp, dp, dp, ip]
             L.oracle_trlyap_l_batch.argtypes = [c_int, ip, llp, dp, dp, dp, ip]
+            L.oracle_trsyl_rect.argtypes = [c_int, c_int, dp, c_int, dp, c_int, dp, c_int, dp, c_int]
+            L.oracle_trsyl_rect.restype = c_int
+            L.oracle_trsyl_rect_batch.argtypes = [c_int, ip, ip, llp, llp, llp, dp, dp, dp, dp, ip]
             for f in (L.oracle_potrf_upper_batch, L.oracle_trsyl_lu_batch,
-                      L.oracle_trlyap_l_batch):
+                      L.oracle_trlyap_l_batch, L.oracle_trsyl_rect_batch):
                 f.restype = None
             _lib = L
     return _lib
@@ -88,6 +91,17 @@ def trsyl_lu(l, u, c):
     n = c.shape[0]
     x = np.zeros((n, n), dtype=np.float64, order="F")
     info = lib().oracle_trsyl_lu(n, _dp(l), n, _dp(u), n, _dp(c), n, _dp(x), n)
+    return x, int(info)
+
+
+def trsyl_rect(l, u, c):
+    """X (m x n) with L X + X U = C, L (m x m) lower, U (n x n) upper
+    triangular; returns (X, info)."""
+    l, u, c = _f64(l), _f64(u), _f64(c)
+    m, n = c.shape
+    x = np.zeros((m, n), dtype=np.float64, order="F")
+    info = lib().oracle_trsyl_rect(m, n, _dp(l), max(m, 1), _dp(u), max(n, 1), _dp(c), max(m, 1),
+                                   _dp(x), max(m, 1))
     return x, int(info)
 
 
@@ -161,3 +175,22 @@ def solve_packed_parallel(op: str, n, off, ops: dict, threads: int, out=None,
     with ThreadPoolExecutor(max_workers=max(1, threads)) as ex:
         list(ex.map(one, idx))
     return out, info
+
+
+def solve_rect_packed(pk, out=None, lo: int = 0, hi=None):
+    """Rectangular Sylvester on instances lo..hi-1 of a RectPacked batch
+    (paper_1906_08613_gb300.inputs.RectPacked), written into ``out`` (laid out
+    like C).  Returns (out, info[lo:hi])."""
+    hi = pk.batch if hi is None else hi
+    if out is None:
+        out = np.zeros_like(pk.ops["C"])
+    cnt = hi - lo
+    info = np.zeros(max(cnt, 1), dtype=np.int32)
+    if cnt <= 0:
+        return out, info[:0]
+    a = lambda v: np.ascontiguousarray(v[lo:hi])
+    m, n = a(pk.m).astype(np.int32), a(pk.n).astype(np.int32)
+    oL, oU, oC = a(pk.offL).astype(np.int64), a(pk.offU).astype(np.int64), a(pk.offC).astype(np.int64)
+    lib().oracle_trsyl_rect_batch(cnt, _ip(m), _ip(n), _llp(oL), _llp(oU), _llp(oC),
+                                  _dp(pk.ops["L"]), _dp(pk.ops["U"]), _dp(pk.ops["C"]), _dp(out), _ip(info))
+    return out, info[:cnt]

@@ -12,7 +12,8 @@
  *   (b) L X_s + X_s L^T = S,  L lower triangular, S and X_s symmetric;
  *   (c) L X + X U = C,        L lower triangular, U upper triangular.
  * All matrices are n x n, double precision (the paper's "Preliminary
- * performance results" paragraph).
+ * performance results" paragraph).  (c) is also given for a rectangular X
+ * (L m x m, U n x n), a generalisation the paper does not state.
  *
  * Each routine is the textbook unblocked recurrence obtained by writing the
  * defining equation out entry by entry and solving for one unknown at a time.
@@ -104,6 +105,42 @@ int oracle_trsyl_lu(int n, const double *L, int ldl, const double *U, int ldu,
     return info;
 }
 
+/*
+ * Rectangular triangular Sylvester: L X + X U = C with L (m x m) lower
+ * triangular, U (n x n) upper triangular, C and X m x n.  The paper states
+ * the Sylvester problem for n x n matrices (Fig. 2 caption); nothing in the
+ * equation needs m = n, and the recurrence is the square one with rows
+ * i = 0..m-1 and columns j = 0..n-1, both ascending:
+ *   x_ij = (c_ij - sum_{k < i} l_ik x_kj - sum_{k < j} x_ik u_kj) / (l_ii + u_jj).
+ * info = 1 if some |l_ii + u_jj| <= max(m, n) * DBL_EPSILON * max(max_i |l_ii|,
+ * max_j |u_jj|) or is NaN (the square threshold with max(m, n) for n).
+ */
+int oracle_trsyl_rect(int m, int n, const double *L, int ldl, const double *U, int ldu,
+                      const double *C, int ldc, double *X, int ldx)
+{
+    double maxdiag = 0.0;
+    for (int i = 0; i < m; ++i)
+        if (fabs(AT(L, ldl, i, i)) > maxdiag) maxdiag = fabs(AT(L, ldl, i, i));
+    for (int j = 0; j < n; ++j)
+        if (fabs(AT(U, ldu, j, j)) > maxdiag) maxdiag = fabs(AT(U, ldu, j, j));
+    const double delta = divisor_threshold(m > n ? m : n, maxdiag);
+    int info = 0;
+    for (int i = 0; i < m; ++i) {
+        for (int j = 0; j < n; ++j) {
+            double s = AT(C, ldc, i, j);
+            for (int k = 0; k < i; ++k)
+                s = s - AT(L, ldl, i, k) * AT(X, ldx, k, j);
+            for (int k = 0; k < j; ++k)
+                s = s - AT(X, ldx, i, k) * AT(U, ldu, k, j);
+            double d = AT(L, ldl, i, i) + AT(U, ldu, j, j);
+            if (!(fabs(d) > delta))
+                info = 1;
+            AT(X, ldx, i, j) = s / d;
+        }
+    }
+    return info;
+}
+
 /* Read element (r, c) of the symmetric X from its stored lower triangle. */
 static double sym_lower(const double *X, int ldx, int r, int c)
 {
@@ -169,4 +206,17 @@ void oracle_trlyap_l_batch(int batch, const int *n, const long long *off,
     for (int b = 0; b < batch; ++b)
         info[b] = oracle_trlyap_l(n[b], L + off[b], n[b], S + off[b], n[b],
                                   X + off[b], n[b]);
+}
+
+/* Rectangular Sylvester batch: instance b has L at offL[b] (ld m[b]), U at
+   offU[b] (ld n[b]), C and X at offC[b] (ld m[b]). */
+void oracle_trsyl_rect_batch(int batch, const int *m, const int *n, const long long *offL,
+                             const long long *offU, const long long *offC, const double *L,
+                             const double *U, const double *C, double *X, int *info)
+{
+    for (int b = 0; b < batch; ++b) {
+        const int mm = m[b] > 0 ? m[b] : 1, nn = n[b] > 0 ? n[b] : 1;
+        info[b] = oracle_trsyl_rect(m[b], n[b], L + offL[b], mm, U + offU[b], nn,
+                                    C + offC[b], mm, X + offC[b], mm);
+    }
 }

@@ -150,6 +150,79 @@ def lyapunov_batch(n, seed: int) -> Packed:
     return _pack(n, ("L", "S", "X0"), lambda nb, b: lyapunov_instance(nb, seed, b))
 
 
+# ---- rectangular Sylvester: L (m x m) lower, U (n x n) upper, C and X m x n ----
+
+@dataclasses.dataclass
+class RectPacked:
+    """A batch of rectangular Sylvester instances.  Instance b has L at
+    ``offL[b]`` (m x m, ld m), U at ``offU[b]`` (n x n, ld n) and C, X0 at
+    ``offC[b]`` (m x n, ld m), each offset a multiple of 32 elements."""
+
+    m: np.ndarray            # int32 [batch]
+    n: np.ndarray            # int32 [batch]
+    offL: np.ndarray         # int64 [batch]
+    offU: np.ndarray
+    offC: np.ndarray
+    ops: dict                # "L", "U", "C", "X0" -> float64 buffers
+
+    @property
+    def batch(self) -> int:
+        return int(self.m.shape[0])
+
+    def view(self, name: str, b: int) -> np.ndarray:
+        mb, nb = int(self.m[b]), int(self.n[b])
+        rows, cols, o = {"L": (mb, mb, self.offL), "U": (nb, nb, self.offU)}.get(name, (mb, nb, self.offC))
+        o = int(o[b])
+        return self.ops[name][o:o + rows * cols].reshape(rows, cols, order="F")
+
+
+def _offsets(elems: np.ndarray, align: int = ALIGN_ELEMS):
+    sizes = ((np.asarray(elems, dtype=np.int64) + align - 1) // align) * align
+    off = np.zeros_like(sizes)
+    if len(sizes) > 1:
+        off[1:] = np.cumsum(sizes)[:-1]
+    return off, max(int(sizes.sum()) if len(sizes) else 0, align)
+
+
+def sylvester_rect_instance(m: int, n: int, seed: int, b: int):
+    """The square Sylvester recipe with an m x n unknown."""
+    rng = _instance_rng(seed, b)
+    l = _tri_factors(rng, m, lower=True)
+    u = _tri_factors(rng, n, lower=False)
+    x0 = rng.standard_normal((m, n))
+    c = l @ x0 + x0 @ u
+    return l, u, c, x0
+
+
+def sylvester_rect_batch(m, n, seed: int) -> RectPacked:
+    m = np.asarray(m, dtype=np.int32)
+    n = np.asarray(n, dtype=np.int32)
+    offL, tL = _offsets(m.astype(np.int64) ** 2)
+    offU, tU = _offsets(n.astype(np.int64) ** 2)
+    offC, tC = _offsets(m.astype(np.int64) * n)
+    ops = {"L": np.zeros(tL), "U": np.zeros(tU), "C": np.zeros(tC), "X0": np.zeros(tC)}
+    for b in range(len(m)):
+        mb, nb = int(m[b]), int(n[b])
+        l, u, c, x0 = sylvester_rect_instance(mb, nb, seed, b)
+        ops["L"][offL[b]:offL[b] + mb * mb] = l.ravel(order="F")
+        ops["U"][offU[b]:offU[b] + nb * nb] = u.ravel(order="F")
+        ops["C"][offC[b]:offC[b] + mb * nb] = c.ravel(order="F")
+        ops["X0"][offC[b]:offC[b] + mb * nb] = x0.ravel(order="F")
+    return RectPacked(m=m, n=n, offL=offL, offU=offU, offC=offC, ops=ops)
+
+
+# Rectangular Sylvester workloads: (m, n) pairs by name.
+RECT_WORKLOADS = {
+    # 4096 instances, m and n independent and uniform in {4..128}
+    "trsyl_rect_4096xU4-128xU4-128": lambda s: (sizes_uniform(4096, 4, 128, s), sizes_uniform(4096, 4, 128, s + 1)),
+}
+
+
+def make_rect_workload(name: str, seed: int = 1234) -> RectPacked:
+    m, n = RECT_WORKLOADS[name](seed)
+    return sylvester_rect_batch(m, n, seed)
+
+
 # The workloads measured and parity-checked by this project, by name.
 WORKLOADS = {
     # plain FP64 upper Cholesky, 1024 instances of order 64
