@@ -136,6 +136,31 @@ int trsyl_lu(int batch, int max_n, const int *d_n,
              int mode, int cfg, void *d_work, size_t work_bytes, void *stream);
 
 /*
+ * Rectangular triangular Sylvester L X + X U = C with L (m x m) lower, U
+ * (n x n) upper, C and X m x n.  The paper states the Sylvester problem for
+ * n x n matrices (Fig. 2c); the equation and its recurrence hold unchanged for
+ * m != n, which this entry point solves (a generalisation, not in the paper).
+ * Per instance: m = d_m[b] rows, n = d_n[b] columns; d_ldl[b] >= max(1, m),
+ * d_ldu[b] >= max(1, n), d_ldc[b] and d_ldx[b] >= max(1, m).  Reads the lower
+ * triangle of L, the upper triangle of U and all of C; writes all of X (X may
+ * alias C with the same leading dimension).  0 <= d_m[b] <= max_m and
+ * 0 <= d_n[b] <= max_n, both bounds <= SS_MAX_N; an instance outside them gets
+ * SS_INFO_BAD_SIZE and is left untouched; m = 0 or n = 0 is empty (info 0).
+ * info = 1 when some |l_ii + u_jj| <= max(m, n) * DBL_EPSILON * max diagonal
+ * magnitude of L and U, or is NaN.  Instances are scheduled longest-first by
+ * max(m, n).  mode must be SS_MODE_FP64 (other modes return -15); cfg as for
+ * trsyl_lu (the Sylvester configurations and tables).  Workspace: the size
+ * ss_workspace_size(SS_OP_TRSYL, batch, max(max_m, max_n), SS_MODE_FP64, ...)
+ * reports.
+ */
+int trsyl_rect(int batch, int max_m, int max_n, const int *d_m, const int *d_n,
+               const double *const *d_L, const int *d_ldl,
+               const double *const *d_U, const int *d_ldu,
+               const double *const *d_C, const int *d_ldc,
+               double *const *d_X, const int *d_ldx, int *d_info,
+               int mode, int cfg, void *d_work, size_t work_bytes, void *stream);
+
+/*
  * Triangular Lyapunov L X + X L^T = S (Fig. 2b).  Reads the lower triangles of
  * L and S; writes the lower triangle of the symmetric X.
  */

@@ -221,9 +221,12 @@ using namespace ss;
 namespace {
 
 // Shared driver of the three entry points.
+// max_n: the host bound of d_n; for the rectangular Sylvester solve (o.m set)
+// also max_m, and sizes are keyed by max(m, n).
 int run(int op, int batch, int max_n, const Operands &o, int mode, int cfg, void *d_work,
-        size_t work_bytes, void *stream, int arg_mode, int arg_work)
+        size_t work_bytes, void *stream, int arg_mode, int arg_work, int max_m = 0)
 {
+    const int max_key = (o.m != nullptr && max_m > max_n) ? max_m : max_n;
     if (!valid_call_mode(mode)) return -arg_mode;
     const bool autom = mode == SS_MODE_AUTO;
     const int ncfg = autom ? 1 : config_count(op, mode);
@@ -231,13 +234,13 @@ int run(int op, int batch, int max_n, const Operands &o, int mode, int cfg, void
     if (!autom && !(cfg == SS_CFG_DEFAULT || cfg == SS_CFG_TABLE || (cfg >= 0 && cfg < ncfg)))
         return -(arg_mode + 1);
     if (batch == 0) return 0;
-    const size_t need = workspace_bytes(op, batch, max_n, mode);
+    const size_t need = workspace_bytes(op, batch, max_key, mode);
     if (d_work == nullptr) return -arg_work;
     if (work_bytes < need) return -(arg_work + 1);
 
     // (mode, configuration) per size bin, then launch groups = runs of equal pairs.
     int mode_of_bin[NUM_BINS], by_bin[NUM_BINS];
-    const int top = host_bin(max_n > 0 ? max_n : 1);
+    const int top = host_bin(max_key > 0 ? max_key : 1);
     for (int k = 0; k < NUM_BINS; ++k) {
         int md = mode, c = -1;
         if (autom) {
@@ -251,7 +254,7 @@ int run(int op, int batch, int max_n, const Operands &o, int mode, int cfg, void
             std::lock_guard<std::mutex> g(tables().mu);
             c = tables().table[op][mode][k];
         }
-        if (c < 0 || c >= config_count(op, md)) c = config_default(op, md, max_n);
+        if (c < 0 || c >= config_count(op, md)) c = config_default(op, md, max_key);
         mode_of_bin[k] = md;
         by_bin[k] = c;
     }
@@ -271,7 +274,7 @@ int run(int op, int batch, int max_n, const Operands &o, int mode, int cfg, void
     }
 
     Sched s;
-    carve_workspace(d_work, batch, max_n, mode, &s);
+    carve_workspace(d_work, batch, max_key, mode, &s);
     const long long per = scratch_per_n2(op, mode);
     if (per > 0) {
         char *p = reinterpret_cast<char *>(const_cast<int *>(s.perm)) + align_up((size_t)batch * sizeof(int), 256);
@@ -281,7 +284,7 @@ int run(int op, int batch, int max_n, const Operands &o, int mode, int cfg, void
         s.scratch_elems = (long long)((d_work == nullptr ? 0 : (static_cast<char *>(d_work) + work_bytes) - p) / sizeof(float));
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e = launch_binning(batch, max_n, o.n, o.info, s, group_of_bin, ngroups, per, st);
+    cudaError_t e = launch_binning(batch, max_n, o.n, o.info, s, group_of_bin, ngroups, per, st, o.m, max_m);
     if (e != cudaSuccess) return SS_ERR_CUDA;
     g_launches.fetch_add(1 + ngroups, std::memory_order_relaxed);
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -299,7 +302,7 @@ int run(int op, int batch, int max_n, const Operands &o, int mode, int cfg, void
                 if (cudaStreamWaitEvent(ap->aux[i], ap->fork, 0) != cudaSuccess) { ap = nullptr; break; }
     }
     for (int g = 0; g < ngroups; ++g) {
-        Launch l{g, group_cfg[g], group_mode[g], max_n, batch};
+        Launch l{g, group_cfg[g], group_mode[g], max_key, batch};
         cudaStream_t gs = (g == 0 || ap == nullptr) ? st : ap->aux[(g - 1) % kAux];
         if (l.mode == SS_MODE_FP64) {
             if (op == SS_OP_POTRF) e = launch_potrf_fp64(o, s, l, gs);
@@ -362,6 +365,32 @@ int trsyl_lu(int batch, int max_n, const int *d_n, const double *const *d_L, con
     }
     Operands o{d_n, d_L, d_ldl, d_U, d_ldu, d_C, d_ldc, d_X, d_ldx, d_info};
     return run(SS_OP_TRSYL, batch, max_n, o, mode, cfg, d_work, work_bytes, stream, 13, 15);
+}
+
+int trsyl_rect(int batch, int max_m, int max_n, const int *d_m, const int *d_n, const double *const *d_L,
+               const int *d_ldl, const double *const *d_U, const int *d_ldu, const double *const *d_C,
+               const int *d_ldc, double *const *d_X, const int *d_ldx, int *d_info, int mode, int cfg,
+               void *d_work, size_t work_bytes, void *stream)
+{
+    if (batch < 0) return -1;
+    if (max_m < 0 || max_m > SS_MAX_N) return -2;
+    if (max_n < 0 || max_n > SS_MAX_N) return -3;
+    if (batch > 0) {
+        if (!d_m) return -4;
+        if (!d_n) return -5;
+        if (!d_L) return -6;
+        if (!d_ldl) return -7;
+        if (!d_U) return -8;
+        if (!d_ldu) return -9;
+        if (!d_C) return -10;
+        if (!d_ldc) return -11;
+        if (!d_X) return -12;
+        if (!d_ldx) return -13;
+        if (!d_info) return -14;
+    }
+    if (mode != SS_MODE_FP64) return -15;
+    Operands o{d_n, d_L, d_ldl, d_U, d_ldu, d_C, d_ldc, d_X, d_ldx, d_info, d_m};
+    return run(SS_OP_TRSYL, batch, max_n, o, mode, cfg, d_work, work_bytes, stream, 15, 17, max_m);
 }
 
 int trlyap_l(int batch, int max_n, const int *d_n, const double *const *d_L, const int *d_ldl,

@@ -7,7 +7,8 @@
 // each size bin bin(n) = ceil(log2 n) starts in the sorted order, the range
 // of every launch group, and the offset of each instance's scratch area, and
 // resets the work-queue heads.  Instances whose device-side order is negative
-// or above max_n get info = SS_INFO_BAD_SIZE and are left out.
+// or above max_n get info = SS_INFO_BAD_SIZE and are left out.  For the
+// rectangular Sylvester solve the order used is max(m, n).
 #include "ss_internal.h"
 
 namespace ss {
@@ -22,10 +23,22 @@ struct GroupMap {
 
 __device__ __forceinline__ int size_bin(int n) { return n <= 1 ? 0 : 32 - __clz(n - 1); }
 
-__global__ void __launch_bounds__(BIN_THREADS)
-bin_kernel(int batch, int max_n, const int *d_n, int *d_info, int *meta, int *perm,
-           long long *scr, long long scr_per_n2, GroupMap gm)
+// Sort key of instance b: its order n; with d_m, max(m, n), or -1 when m or
+// n is out of range.
+__device__ __forceinline__ int size_key(const int *d_n, const int *d_m, int max_n, int max_m, int b)
 {
+    const int n = d_n[b];
+    if (d_m == nullptr) return n;
+    const int m = d_m[b];
+    if (m < 0 || m > max_m || n < 0 || n > max_n) return -1;
+    return m > n ? m : n;
+}
+
+__global__ void __launch_bounds__(BIN_THREADS)
+bin_kernel(int batch, int max_key, const int *d_n, const int *d_m, int max_n_in, int max_m, int *d_info,
+           int *meta, int *perm, long long *scr, long long scr_per_n2, GroupMap gm)
+{
+    const int max_n = max_key;
     extern __shared__ unsigned char raw[];
     const int M = max_n + 1;
     long long *sq = reinterpret_cast<long long *>(raw);          // [M]
@@ -39,7 +52,7 @@ bin_kernel(int batch, int max_n, const int *d_n, int *d_info, int *meta, int *pe
     for (int i = tid; i < M; i += BIN_THREADS) hist[i] = 0;
     __syncthreads();
     for (int b = tid; b < batch; b += BIN_THREADS) {
-        const int n = d_n[b];
+        const int n = size_key(d_n, d_m, max_n_in, max_m, b);
         if (n < 0 || n > max_n) d_info[b] = SS_INFO_BAD_SIZE;
         else atomicAdd(&hist[n], 1);
     }
@@ -99,7 +112,7 @@ bin_kernel(int batch, int max_n, const int *d_n, int *d_info, int *meta, int *pe
     for (int i = tid; i < M; i += BIN_THREADS) hist[i] = pos[i];   // cursors
     __syncthreads();
     for (int b = tid; b < batch; b += BIN_THREADS) {
-        const int n = d_n[b];
+        const int n = size_key(d_n, d_m, max_n_in, max_m, b);
         if (n < 0 || n > max_n) continue;
         const int w = atomicAdd(&hist[n], 1);
         perm[w] = b;
@@ -141,15 +154,16 @@ bin_kernel(int batch, int max_n, const int *d_n, int *d_info, int *meta, int *pe
 
 cudaError_t launch_binning(int batch, int max_n, const int *d_n, int *d_info, const Sched &s,
                            const int *group_of_bin, int ngroups, long long scratch_per_n2,
-                           cudaStream_t st)
+                           cudaStream_t st, const int *d_m, int max_m)
 {
+    const int max_key = d_m != nullptr && max_m > max_n ? max_m : max_n;
     GroupMap gm;
     for (int k = 0; k < NUM_BINS; ++k) gm.group_of_bin[k] = group_of_bin[k];
     gm.ngroups = ngroups;
-    const size_t smem = (size_t)(max_n + 1) * (sizeof(long long) + 2 * sizeof(int));
+    const size_t smem = (size_t)(max_key + 1) * (sizeof(long long) + 2 * sizeof(int));
     cudaError_t e = cudaFuncSetAttribute(bin_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    bin_kernel<<<1, BIN_THREADS, smem, st>>>(batch, max_n, d_n, d_info, s.meta,
+    bin_kernel<<<1, BIN_THREADS, smem, st>>>(batch, max_key, d_n, d_m, max_n, max_m, d_info, s.meta,
                                              const_cast<int *>(s.perm),
                                              const_cast<long long *>(s.scr), scratch_per_n2, gm);
     return cudaGetLastError();

@@ -138,24 +138,25 @@ __device__ int syl_diag_warp(const double *sL, const double *sU, double *sT, dou
 }
 
 // One Sylvester (LYAP = false) or Lyapunov (LYAP = true, U unused) instance.
+// X is m x n (L m x m, U n x n); Lyapunov has m = n.
 template <int B, int T, bool LYAP, int VAR>
-__device__ void syl_instance(int n, const double *L, long ldl, const double *U, long ldu,
+__device__ void syl_instance(int m, int n, const double *L, long ldl, const double *U, long ldu,
                              const double *C, long ldc, double *X, long ldx, int *info,
                              double *sm)
 {
     constexpr int LD = Tile<B>::LD, SZ = Tile<B>::SZ, E = B * B / T;
     double *sA = sm, *sB = sm + SZ, *sT = sm + 2 * SZ, *sL = sm + 3 * SZ, *sU = sm + 4 * SZ;
     double *s_red = sm + 5 * SZ;
-    const int nb = (n + B - 1) / B;
+    const int mb = (m + B - 1) / B, nb = (n + B - 1) / B;
 
-    double md = block_max_abs_diag(L, ldl, n, s_red);
+    double md = block_max_abs_diag(L, ldl, m, s_red);
     if (!LYAP) md = fmax(md, block_max_abs_diag(U, ldu, n, s_red));
-    const double delta = divisor_delta(n, md);
+    const double delta = divisor_delta(max(m, n), md);
 
     int bad = 0;
     Slots<B, T> sl;
-    for (int I = 0; I < nb; ++I) {
-        const int mI = min(B, n - I * B);
+    for (int I = 0; I < mb; ++I) {
+        const int mI = min(B, m - I * B);
         const int i0 = I * B;
         __syncthreads();
         stage_tri<B, T>(sL, L + i0 + (long)i0 * ldl, ldl, mI, true);
@@ -434,9 +435,9 @@ __global__ void __launch_bounds__(T) syl_fp64_kernel(Operands o, Sched s, int gr
     int b;
     claim_init(&s_slot);
     while (next_instance(s, group, &s_slot, b)) {
-        const int n = o.n[b];
-        if (n == 0) { if (threadIdx.x == 0) o.info[b] = 0; continue; }
-        syl_instance<B, T, LYAP, VAR>(n, o.A[b], o.lda[b], LYAP ? nullptr : o.U[b], LYAP ? 0 : o.ldu[b],
+        const int n = o.n[b], m = o.m != nullptr ? o.m[b] : n;
+        if (n == 0 || m == 0) { if (threadIdx.x == 0) o.info[b] = 0; continue; }
+        syl_instance<B, T, LYAP, VAR>(m, n, o.A[b], o.lda[b], LYAP ? nullptr : o.U[b], LYAP ? 0 : o.ldu[b],
                                  o.C[b], o.ldc[b], o.X[b], o.ldx[b], o.info + b, sm);
     }
 }

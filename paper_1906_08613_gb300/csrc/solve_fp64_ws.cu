@@ -258,14 +258,15 @@ __device__ __forceinline__ void step_src(int s, int P1, int I, int J, int mI, in
 }
 
 // The staged tile of the last phase: U_{J-1,J} (Lyapunov: L_{J,J-1}, used
-// transposed) for J > 0; for Lyapunov block (1, 0): L_10 (not transposed).
+// transposed) for J > 0; for J = 0 (a first-sum term, see has_first_last):
+// L_{I,I-1} (not transposed).
 template <int B, bool LYAP>
 __device__ __forceinline__ void last_src_t(int I, int J, int mI, int nJ, const double *L, long ldl,
                                            const double *U, long ldu, Src &b, bool &tb)
 {
     const int j0 = J * B;
     if (J == 0) {
-        b = Src{L + I * B, ldl, mI, B, false};
+        b = Src{L + I * B + (long)(I - 1) * B * ldl, ldl, mI, B, false};
         tb = false;
         return;
     }
@@ -281,9 +282,10 @@ constexpr size_t ws_smem_bytes() { return (size_t)ws_tiles<B>() * Tile<B>::SZ * 
 
 // One instance.  Shared tiles: sT[2] (T / X of consecutive blocks), sL, sU,
 // sR (diagonal warp), sA[2], sB[2] (update warps' staging).
+// X is m x n (L m x m, U n x n); Lyapunov has m = n.
 template <int B, int NU, bool LYAP>
-__device__ void syl_ws_instance(int n, const double *L, long ldl, const double *U, long ldu, const double *C,
-                                long ldc, double *X, long ldx, int *info, double *sm)
+__device__ void syl_ws_instance(int m, int n, const double *L, long ldl, const double *U, long ldu,
+                                const double *C, long ldc, double *X, long ldx, int *info, double *sm)
 {
     constexpr int LD = Tile<B>::LD, SZ = Tile<B>::SZ;
     constexpr int TU = 32 * NU, TALL = TU + 32;
@@ -291,18 +293,18 @@ __device__ void syl_ws_instance(int n, const double *L, long ldl, const double *
     double *sT0 = sm, *sL = sm + 2 * SZ, *sU = sm + 3 * SZ, *sR = sm + 4 * SZ;
     double *sA0 = sm + 5 * SZ, *sB0 = sm + 7 * SZ;
     double *s_red = sm + 9 * SZ;
-    const int nb = (n + B - 1) / B;
+    const int mb = (m + B - 1) / B, nb = (n + B - 1) / B;
 
-    double md = max_abs_diag(L, ldl, n, s_red);
+    double md = max_abs_diag(L, ldl, m, s_red);
     if (!LYAP) md = fmax(md, max_abs_diag(U, ldu, n, s_red));
-    const double delta = divisor_delta(n, md);
+    const double delta = divisor_delta(max(m, n), md);
 
     if (threadIdx.x < 32) {
         // ------------------------------------------------ diagonal warp
         const int lane = threadIdx.x;
         int bad = 0, t = 0;
-        for (int I = 0; I < nb; ++I) {
-            const int mI = min(B, n - I * B), i0 = I * B;
+        for (int I = 0; I < mb; ++I) {
+            const int mI = min(B, m - I * B), i0 = I * B;
             warp_stage_tri<B>(sL, L + i0 + (long)i0 * ldl, ldl, mI, true, lane);
             const int jend = LYAP ? I + 1 : nb;
             for (int J = 0; J < jend; ++J, ++t) {
@@ -336,8 +338,8 @@ __device__ void syl_ws_instance(int n, const double *L, long ldl, const double *
         OutMap<B, TU> om;
         Prefetch<B, TU> pf;
         int t = 0;
-        for (int I = 0; I < nb; ++I) {
-            const int mI = min(B, n - I * B), i0 = I * B;
+        for (int I = 0; I < mb; ++I) {
+            const int mI = min(B, m - I * B), i0 = I * B;
             const int jend = LYAP ? I + 1 : nb;
             for (int J = 0; J < jend; ++J, ++t) {
                 const int nJ = min(B, n - J * B), j0 = J * B;
@@ -354,11 +356,12 @@ __device__ void syl_ws_instance(int n, const double *L, long ldl, const double *
                     }
                 }
                 // Bulk steps, then (J > 0) the staged operand of the last phase.
-                // Lyapunov blocks right after the block whose X they need in
-                // the first sum: the diagonal block (I, I) (term K = I-1) and
-                // block (1, 0) (term K = 0, X_00 solved just before it).
+                // Blocks right after the block whose X they need in the first
+                // sum (term K = I-1): the Lyapunov diagonal block (I, I), and
+                // block (I, 0) when block (I-1, 0) is solved just before it
+                // (Lyapunov I = 1; Sylvester with a single block column).
                 const bool ldiag = LYAP && I == J && I > 0;
-                const bool lfirst = LYAP && I == 1 && J == 0;
+                const bool lfirst = J == 0 && I > 0 && (LYAP ? I == 1 : nb == 1);
                 const int P1 = (ldiag || lfirst) ? I - 1 : I;
                 const bool has_last = J > 0 || lfirst;
                 const int nsteps = P1 + (J > 0 ? J - 1 : 0);
@@ -389,14 +392,14 @@ __device__ void syl_ws_instance(int n, const double *L, long ldl, const double *
                 if (t > 0) named_sync(kBarX, TALL);        // X of block t-1 is final
                 if (has_last) {
                     // Last phase: the X block of block t-1 is still in shared
-                    // memory (for block (1, 0) of Lyapunov: all of X_00).
+                    // memory (for a Lyapunov diagonal block: all of it).
                     const double *sXp = sT0 + ((t - 1) & 1) * SZ;
                     const double *sV = sB0 + (nsteps & 1) * SZ;
                     if (J > 0) {
                         upd_fma_rt<B, TU>(tb_next, ae, ao, om, sXp, sV);      // X_{I,J-1} U_{J-1,J}
                         if (ldiag) upd_fma<B, TU, true>(ae, ao, om, sV, sXp); // L_{I,I-1} X_{I,I-1}^T
                     } else {
-                        upd_fma<B, TU, false>(ae, ao, om, sV, sXp);           // L_10 X_00
+                        upd_fma<B, TU, false>(ae, ao, om, sV, sXp);           // L_{I,I-1} X_{I-1,0}
                     }
                 }
                 double *sT = sT0 + (t & 1) * SZ;
@@ -430,10 +433,10 @@ __global__ void __launch_bounds__(32 * NU + 32, MINB) syl_ws_kernel(Operands o, 
     int b;
     claim_init(&s_slot);
     while (next_instance(s, group, &s_slot, b)) {
-        const int n = o.n[b];
-        if (n == 0) { if (threadIdx.x == 0) o.info[b] = 0; continue; }
-        syl_ws_instance<B, NU, LYAP>(n, o.A[b], o.lda[b], LYAP ? nullptr : o.U[b], LYAP ? 0 : o.ldu[b], o.C[b],
-                                     o.ldc[b], o.X[b], o.ldx[b], o.info + b, sm);
+        const int n = o.n[b], m = o.m != nullptr ? o.m[b] : n;
+        if (n == 0 || m == 0) { if (threadIdx.x == 0) o.info[b] = 0; continue; }
+        syl_ws_instance<B, NU, LYAP>(m, n, o.A[b], o.lda[b], LYAP ? nullptr : o.U[b], LYAP ? 0 : o.ldu[b],
+                                     o.C[b], o.ldc[b], o.X[b], o.ldx[b], o.info + b, sm);
     }
 }
 

@@ -21,6 +21,7 @@ struct Operands {
     double *const *X;
     const int *ldx;
     int *info;
+    const int *m;             // rectangular Sylvester: rows of X (null: m = n)
 };
 
 // Device-side workspace produced by the binning pre-pass.
@@ -63,9 +64,11 @@ void carve_workspace(void *d_work, int batch, int max_n, int mode, Sched *s);
 // scratch offsets and the launch-group ranges, resets the queue heads.
 // group_of_bin[k] is the launch group of size bin k (-1: none, only for bins
 // that cannot hold instances); ngroups groups are used.
+// With d_m (rectangular Sylvester) the sort key of an instance is max(m, n),
+// and m outside [0, max_m] is a bad size too.
 cudaError_t launch_binning(int batch, int max_n, const int *d_n, int *d_info, const Sched &s,
                            const int *group_of_bin, int ngroups, long long scratch_per_n2,
-                           cudaStream_t st);
+                           cudaStream_t st, const int *d_m = nullptr, int max_m = 0);
 
 // Configuration tables.
 struct Config {

@@ -74,3 +74,44 @@ class DeviceBatch:
 
     def info_host(self) -> np.ndarray:
         return self.info[: self.batch].cpu().numpy()
+
+
+class DeviceRectBatch:
+    """Device copy of a rectangular Sylvester batch (inputs.RectPacked) with the
+    pointer and size arrays trsyl_rect takes; X is laid out like C."""
+
+    def __init__(self, pk, device="cuda", alias_rhs: bool = False, x_fill: float = 0.0,
+                 max_m: int | None = None, max_n: int | None = None):
+        self.device = torch.device(device)
+        self.batch = pk.batch
+        m = np.ascontiguousarray(pk.m, dtype=np.int32)
+        n = np.ascontiguousarray(pk.n, dtype=np.int32)
+        self.max_m = int(m.max()) if (max_m is None and self.batch) else int(max_m or 0)
+        self.max_n = int(n.max()) if (max_n is None and self.batch) else int(max_n or 0)
+        to = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(self.device)
+        self.d_m, self.d_n = to(m), to(n)
+        self.d_ldm = to(np.maximum(m, 1).astype(np.int32))
+        self.d_ldn = to(np.maximum(n, 1).astype(np.int32))
+        self.bufs = {k: to(pk.ops[k]) for k in ("L", "U", "C")}
+        self.X = self.bufs["C"] if alias_rhs else torch.full_like(self.bufs["C"], x_fill)
+        off = {"L": pk.offL, "U": pk.offU, "C": pk.offC}
+        self.ptrs = {k: (v.data_ptr() + to(off[k] * 8)).contiguous() for k, v in self.bufs.items()}
+        self.ptrs["X"] = (self.X.data_ptr() + to(pk.offC * 8)).contiguous()
+        self.info = torch.full((max(self.batch, 1),), 12345, dtype=torch.int32, device=self.device)
+        need = ss.ss_workspace_size(ss.OP_TRSYL, self.batch, max(self.max_m, self.max_n), ss.MODE_FP64)
+        self.work = torch.empty(max(need, 256), dtype=torch.uint8, device=self.device)
+
+    def solve(self, cfg: int = ss.CFG_DEFAULT, mode: int = ss.MODE_FP64, stream: int = 0,
+              check: bool = True) -> int:
+        p = self.ptrs
+        return ss.trsyl_rect(self.batch, self.max_m, self.max_n, self.d_m.data_ptr(), self.d_n.data_ptr(),
+                             p["L"].data_ptr(), self.d_ldm.data_ptr(), p["U"].data_ptr(), self.d_ldn.data_ptr(),
+                             p["C"].data_ptr(), self.d_ldm.data_ptr(), p["X"].data_ptr(), self.d_ldm.data_ptr(),
+                             self.info.data_ptr(), mode=mode, cfg=cfg, d_work=self.work.data_ptr(),
+                             work_bytes=int(self.work.numel()), stream=stream, check=check)
+
+    def x_host(self) -> np.ndarray:
+        return self.X.cpu().numpy()
+
+    def info_host(self) -> np.ndarray:
+        return self.info[: self.batch].cpu().numpy()

@@ -72,7 +72,8 @@ def lib():
             L.potrf_upper.argtypes = [i, i, vp, vp, vp, vp, vp, vp, i, i, vp, sz, vp]
             L.trsyl_lu.argtypes = [i, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i, i, vp, sz, vp]
             L.trlyap_l.argtypes = [i, i, vp, vp, vp, vp, vp, vp, vp, vp, i, i, vp, sz, vp]
-            for f in (L.potrf_upper, L.trsyl_lu, L.trlyap_l):
+            L.trsyl_rect.argtypes = [i, i, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i, i, vp, sz, vp]
+            for f in (L.potrf_upper, L.trsyl_lu, L.trlyap_l, L.trsyl_rect):
                 f.restype = i
             L.trsyl_lu_noalloc.argtypes = [i, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
             L.trsyl_lu_noalloc.restype = i
@@ -126,6 +127,14 @@ def trsyl_lu(batch, max_n, d_n, d_L, d_ldl, d_U, d_ldu, d_C, d_ldc, d_X, d_ldx, 
     rc = lib().trsyl_lu(batch, max_n, d_n, d_L, d_ldl, d_U, d_ldu, d_C, d_ldc, d_X, d_ldx,
                         d_info, mode, cfg, d_work or None, work_bytes, stream or None)
     return _check(rc, "trsyl_lu") if check else rc
+
+
+def trsyl_rect(batch, max_m, max_n, d_m, d_n, d_L, d_ldl, d_U, d_ldu, d_C, d_ldc, d_X, d_ldx, d_info,
+               mode=MODE_FP64, cfg=CFG_DEFAULT, d_work=0, work_bytes=0, stream=0, check=True):
+    """Rectangular Sylvester L X + X U = C (L m x m, U n x n, X m x n)."""
+    rc = lib().trsyl_rect(batch, max_m, max_n, d_m, d_n, d_L, d_ldl, d_U, d_ldu, d_C, d_ldc, d_X, d_ldx,
+                          d_info, mode, cfg, d_work, work_bytes, stream)
+    return _check(rc, "trsyl_rect") if check else rc
 
 
 def trsyl_lu_noalloc(batch, max_n, d_n, d_L, d_ldl, d_U, d_ldu, d_C, d_ldc, d_X, d_ldx, d_info,
