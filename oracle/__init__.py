@@ -57,8 +57,11 @@ def lib():
             L.oracle_trsyl_rect.argtypes = [c_int, c_int, dp, c_int, dp, c_int, dp, c_int, dp, c_int]
             L.oracle_trsyl_rect.restype = c_int
             L.oracle_trsyl_rect_batch.argtypes = [c_int, ip, ip, llp, llp, llp, dp, dp, dp, dp, ip]
+            L.oracle_posv_upper.argtypes = [c_int, c_int, dp, c_int, dp, c_int, dp, c_int, dp, c_int]
+            L.oracle_posv_upper.restype = c_int
+            L.oracle_posv_upper_batch.argtypes = [c_int, ip, ip, llp, llp, dp, dp, dp, dp, ip]
             for f in (L.oracle_potrf_upper_batch, L.oracle_trsyl_lu_batch,
-                      L.oracle_trlyap_l_batch, L.oracle_trsyl_rect_batch):
+                      L.oracle_trlyap_l_batch, L.oracle_trsyl_rect_batch, L.oracle_posv_upper_batch):
                 f.restype = None
             _lib = L
     return _lib
@@ -103,6 +106,18 @@ def trsyl_rect(l, u, c):
     info = lib().oracle_trsyl_rect(m, n, _dp(l), max(m, 1), _dp(u), max(n, 1), _dp(c), max(m, 1),
                                    _dp(x), max(m, 1))
     return x, int(info)
+
+
+def posv_upper(a, b):
+    """X with A X = B (A SPD, upper triangle read) through the upper Cholesky
+    factor; returns (X, R, info)."""
+    a, b = _f64(a), _f64(b)
+    n, k = b.shape
+    r = np.zeros((n, n), dtype=np.float64, order="F")
+    x = np.zeros((n, k), dtype=np.float64, order="F")
+    ld = max(n, 1)
+    info = lib().oracle_posv_upper(n, k, _dp(a), ld, _dp(r), ld, _dp(b), ld, _dp(x), ld)
+    return x, r, int(info)
 
 
 def trlyap_l(l, s):
@@ -194,3 +209,21 @@ def solve_rect_packed(pk, out=None, lo: int = 0, hi=None):
     lib().oracle_trsyl_rect_batch(cnt, _ip(m), _ip(n), _llp(oL), _llp(oU), _llp(oC),
                                   _dp(pk.ops["L"]), _dp(pk.ops["U"]), _dp(pk.ops["C"]), _dp(out), _ip(info))
     return out, info[:cnt]
+
+
+def solve_posv_packed(pk, lo: int = 0, hi=None, out_x=None, out_r=None):
+    """SPD solves of instances lo..hi-1 of a PosvPacked batch
+    (paper_1906_08613_gb300.inputs.PosvPacked).  Returns (X, R, info[lo:hi])."""
+    hi = pk.batch if hi is None else hi
+    out_x = np.zeros_like(pk.ops["B"]) if out_x is None else out_x
+    out_r = np.zeros_like(pk.ops["A"]) if out_r is None else out_r
+    cnt = hi - lo
+    info = np.zeros(max(cnt, 1), dtype=np.int32)
+    if cnt <= 0:
+        return out_x, out_r, info[:0]
+    a = lambda v: np.ascontiguousarray(v[lo:hi])
+    n, k = a(pk.n).astype(np.int32), a(pk.k).astype(np.int32)
+    oA, oB = a(pk.offA).astype(np.int64), a(pk.offB).astype(np.int64)
+    lib().oracle_posv_upper_batch(cnt, _ip(n), _ip(k), _llp(oA), _llp(oB), _dp(pk.ops["A"]), _dp(out_r),
+                                  _dp(pk.ops["B"]), _dp(out_x), _ip(info))
+    return out_x, out_r, info[:cnt]

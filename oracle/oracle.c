@@ -13,7 +13,8 @@
  *   (c) L X + X U = C,        L lower triangular, U upper triangular.
  * All matrices are n x n, double precision (the paper's "Preliminary
  * performance results" paragraph).  (c) is also given for a rectangular X
- * (L m x m, U n x n), a generalisation the paper does not state.
+ * (L m x m, U n x n), a generalisation the paper does not state, and (a)
+ * is used to solve A X = B (oracle_posv_upper).
  *
  * Each routine is the textbook unblocked recurrence obtained by writing the
  * defining equation out entry by entry and solving for one unknown at a time.
@@ -64,6 +65,39 @@ int oracle_potrf_upper(int n, const double *A, int lda, double *X, int ldx)
         if (!(d > 0.0))
             return j + 1;
         AT(X, ldx, j, j) = sqrt(d);
+    }
+    return 0;
+}
+
+/*
+ * SPD solve A X = B (A n x n symmetric positive definite, B and X n x k)
+ * through the Cholesky factor: R = the upper factor of A (R^T R = A, the
+ * routine above, written to R), then the two triangular systems
+ *   R^T Y = B:  y_ij = (b_ij - sum_{l < i} r_li y_lj) / r_ii,   i ascending,
+ *   R X = Y:    x_ij = (y_ij - sum_{l > i} r_il x_lj) / r_ii,   i descending,
+ * column by column; Y is held in X.  The paper names the factorisation as a
+ * building block for solving linear systems; this is that use of it.  Returns
+ * the Cholesky info; X is not written when it is nonzero.
+ */
+int oracle_posv_upper(int n, int k, const double *A, int lda, double *R, int ldr,
+                      const double *B, int ldb, double *X, int ldx)
+{
+    const int info = oracle_potrf_upper(n, A, lda, R, ldr);
+    if (info != 0)
+        return info;
+    for (int j = 0; j < k; ++j) {
+        for (int i = 0; i < n; ++i) {
+            double s = AT(B, ldb, i, j);
+            for (int l = 0; l < i; ++l)
+                s = s - AT(R, ldr, l, i) * AT(X, ldx, l, j);
+            AT(X, ldx, i, j) = s / AT(R, ldr, i, i);
+        }
+        for (int i = n - 1; i >= 0; --i) {
+            double s = AT(X, ldx, i, j);
+            for (int l = i + 1; l < n; ++l)
+                s = s - AT(R, ldr, i, l) * AT(X, ldx, l, j);
+            AT(X, ldx, i, j) = s / AT(R, ldr, i, i);
+        }
     }
     return 0;
 }
@@ -218,5 +252,18 @@ void oracle_trsyl_rect_batch(int batch, const int *m, const int *n, const long l
         const int mm = m[b] > 0 ? m[b] : 1, nn = n[b] > 0 ? n[b] : 1;
         info[b] = oracle_trsyl_rect(m[b], n[b], L + offL[b], mm, U + offU[b], nn,
                                     C + offC[b], mm, X + offC[b], mm);
+    }
+}
+
+/* SPD solve batch: instance b has A and R at offA[b] (n x n, ld n), B and X at
+   offB[b] (n x k, ld n). */
+void oracle_posv_upper_batch(int batch, const int *n, const int *k, const long long *offA,
+                             const long long *offB, const double *A, double *R,
+                             const double *B, double *X, int *info)
+{
+    for (int b = 0; b < batch; ++b) {
+        const int ld = n[b] > 0 ? n[b] : 1;
+        info[b] = oracle_posv_upper(n[b], k[b], A + offA[b], ld, R + offA[b], ld,
+                                    B + offB[b], ld, X + offB[b], ld);
     }
 }

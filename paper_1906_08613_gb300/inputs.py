@@ -223,6 +223,65 @@ def make_rect_workload(name: str, seed: int = 1234) -> RectPacked:
     return sylvester_rect_batch(m, n, seed)
 
 
+# ---- SPD solve A X = B through the Cholesky factor: A n x n, B and X n x k ----
+
+@dataclasses.dataclass
+class PosvPacked:
+    """A batch of SPD solves.  Instance b has A at ``offA[b]`` (n x n, ld n) and
+    B, X0 at ``offB[b]`` (n x k, ld n)."""
+
+    n: np.ndarray
+    k: np.ndarray
+    offA: np.ndarray
+    offB: np.ndarray
+    ops: dict                # "A", "B", "X0"
+
+    @property
+    def batch(self) -> int:
+        return int(self.n.shape[0])
+
+    def view(self, name: str, b: int) -> np.ndarray:
+        nb, kb = int(self.n[b]), int(self.k[b])
+        rows, cols, o = (nb, nb, self.offA) if name == "A" else (nb, kb, self.offB)
+        o = int(o[b])
+        return self.ops[name][o:o + rows * cols].reshape(rows, cols, order="F")
+
+
+def posv_instance(n: int, k: int, seed: int, b: int):
+    """The Cholesky recipe's A (X0^T X0 + n I, X0 upper N(0,1)); a solution
+    X0s ~ N(0,1) (n x k) and B = A X0s."""
+    a, _ = cholesky_instance(n, seed, b)
+    rng = np.random.default_rng([seed, 7907, b])
+    xs = rng.standard_normal((n, k))
+    return a, a @ xs, xs
+
+
+def posv_batch(n, k, seed: int) -> PosvPacked:
+    n = np.asarray(n, dtype=np.int32)
+    k = np.asarray(k, dtype=np.int32)
+    offA, tA = _offsets(n.astype(np.int64) ** 2)
+    offB, tB = _offsets(n.astype(np.int64) * k)
+    ops = {"A": np.zeros(tA), "B": np.zeros(tB), "X0": np.zeros(tB)}
+    for b in range(len(n)):
+        nb, kb = int(n[b]), int(k[b])
+        a, bb, xs = posv_instance(nb, kb, seed, b)
+        ops["A"][offA[b]:offA[b] + nb * nb] = a.ravel(order="F")
+        ops["B"][offB[b]:offB[b] + nb * kb] = bb.ravel(order="F")
+        ops["X0"][offB[b]:offB[b] + nb * kb] = xs.ravel(order="F")
+    return PosvPacked(n=n, k=k, offA=offA, offB=offB, ops=ops)
+
+
+POSV_WORKLOADS = {
+    # 4096 SPD systems, n uniform in {8..128}, 16 right-hand sides each
+    "posv_4096xU8-128xk16": lambda s: (sizes_uniform(4096, 8, 128, s), np.full(4096, 16, dtype=np.int32)),
+}
+
+
+def make_posv_workload(name: str, seed: int = 1234) -> PosvPacked:
+    n, k = POSV_WORKLOADS[name](seed)
+    return posv_batch(n, k, seed)
+
+
 # The workloads measured and parity-checked by this project, by name.
 WORKLOADS = {
     # plain FP64 upper Cholesky, 1024 instances of order 64
