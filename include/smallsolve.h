@@ -161,6 +161,31 @@ int trsyl_rect(int batch, int max_m, int max_n, const int *d_m, const int *d_n,
                int mode, int cfg, void *d_work, size_t work_bytes, void *stream);
 
 /*
+ * SPD solve A X = B through the upper Cholesky factor: R with R^T R = A
+ * (Fig. 2a, computed as by potrf_upper), then R^T Y = B and R X = Y.  The
+ * paper names the factorisation as a building block of linear-system solves;
+ * this entry point is that use of it (not a problem the paper states).
+ * Per instance: A is n x n (n = d_n[b], upper triangle read), R is written in
+ * its upper triangle (d_R[b] may alias d_A[b] with the same leading
+ * dimension; the strict lower triangle of R is left untouched), B and X are
+ * n x k (k = d_k[b]; X may alias B with the same leading dimension).
+ * d_ldr[b] >= max(1, n); d_ldb[b], d_ldx[b] >= max(1, n).  0 <= n <= max_n
+ * <= SS_MAX_N and 0 <= k <= max_k.  info: 0 success; j > 0 the factor's
+ * pivot j failed (X untouched); SS_INFO_BAD_SIZE for n or k out of range (X
+ * untouched; for a bad k, R is computed).  mode must be SS_MODE_FP64 (other
+ * modes return -15); cfg selects the Cholesky configuration (as for
+ * potrf_upper).  Workspace: the size ss_workspace_size(SS_OP_POTRF, batch,
+ * max_n, SS_MODE_FP64, ...) reports.  Two launches after the pre-pass: the
+ * factor, then the solves, ordered on `stream`.
+ */
+int posv_upper(int batch, int max_n, int max_k, const int *d_n, const int *d_k,
+               const double *const *d_A, const int *d_lda,
+               double *const *d_R, const int *d_ldr,
+               const double *const *d_B, const int *d_ldb,
+               double *const *d_X, const int *d_ldx, int *d_info,
+               int mode, int cfg, void *d_work, size_t work_bytes, void *stream);
+
+/*
  * Triangular Lyapunov L X + X L^T = S (Fig. 2b).  Reads the lower triangles of
  * L and S; writes the lower triangle of the symmetric X.
  */

@@ -148,15 +148,24 @@ const Config *config_get(int op, int mode, int cfg)
 }
 
 // Built-in default: a single configuration chosen from the largest order.
-int config_default(int op, int mode, int max_n)
+// Built-in FP64 defaults, from the autotuner's timings on GB300 (fastest
+// configuration per size bin, batches 64..2048):
+//   Cholesky: one-warp diagonal blocks (B = 16) up to n = 128, then (32, 256);
+//   Sylvester / Lyapunov: CTA-wide B = 8 / 16 up to n = 32, warp-specialised
+//   with one update warp up to 64, then two (large batches) or four.
+int config_default(int op, int mode, int max_n, int batch)
 {
-    if (mode == SS_MODE_FP64) {
-        if (max_n <= 8) return 0;
-        if (max_n <= 16) return 1;
-        if (max_n <= 32) return 2;
-        return op == SS_OP_POTRF ? 3 : 6;   // Sylvester / Lyapunov: warp-specialised, B = 16
+    if (mode != SS_MODE_FP64) return 0;
+    if (op == SS_OP_POTRF) {
+        if (max_n <= 16) return 5;        // (16, 64, 1)
+        if (max_n <= 128) return 6;       // (16, 128, 1)
+        return 4;                         // (32, 256, 0)
     }
-    return 0;
+    if (max_n <= 8) return 0;             // (8, 64, 0)
+    if (max_n <= 32) return 1;            // (16, 64, 0)
+    if (max_n <= 64) return 7;            // (16, 64, 2)
+    if (max_n <= 128 && batch >= 1024) return 6;   // (16, 96, 2)
+    return 5;                             // (16, 160, 2)
 }
 
 int sm_count()
@@ -254,7 +263,7 @@ int run(int op, int batch, int max_n, const Operands &o, int mode, int cfg, void
             std::lock_guard<std::mutex> g(tables().mu);
             c = tables().table[op][mode][k];
         }
-        if (c < 0 || c >= config_count(op, md)) c = config_default(op, md, max_key);
+        if (c < 0 || c >= config_count(op, md)) c = config_default(op, md, max_key, batch);
         mode_of_bin[k] = md;
         by_bin[k] = c;
     }
@@ -391,6 +400,44 @@ int trsyl_rect(int batch, int max_m, int max_n, const int *d_m, const int *d_n, 
     if (mode != SS_MODE_FP64) return -15;
     Operands o{d_n, d_L, d_ldl, d_U, d_ldu, d_C, d_ldc, d_X, d_ldx, d_info, d_m};
     return run(SS_OP_TRSYL, batch, max_n, o, mode, cfg, d_work, work_bytes, stream, 15, 17, max_m);
+}
+
+int posv_upper(int batch, int max_n, int max_k, const int *d_n, const int *d_k, const double *const *d_A,
+               const int *d_lda, double *const *d_R, const int *d_ldr, const double *const *d_B,
+               const int *d_ldb, double *const *d_X, const int *d_ldx, int *d_info, int mode, int cfg,
+               void *d_work, size_t work_bytes, void *stream)
+{
+    if (batch < 0) return -1;
+    if (max_n < 0 || max_n > SS_MAX_N) return -2;
+    if (max_k < 0) return -3;
+    if (batch > 0) {
+        if (!d_n) return -4;
+        if (!d_k) return -5;
+        if (!d_A) return -6;
+        if (!d_lda) return -7;
+        if (!d_R) return -8;
+        if (!d_ldr) return -9;
+        if (!d_B) return -10;
+        if (!d_ldb) return -11;
+        if (!d_X) return -12;
+        if (!d_ldx) return -13;
+        if (!d_info) return -14;
+    }
+    if (mode != SS_MODE_FP64) return -15;
+    // Stage 1: the factor R (R^T R = A) by the FP64 Cholesky path; it also
+    // sorts the instances by n and leaves the order in the workspace.
+    Operands o{d_n, d_A, d_lda, nullptr, nullptr, nullptr, nullptr, d_R, d_ldr, d_info};
+    const int rc = run(SS_OP_POTRF, batch, max_n, o, mode, cfg, d_work, work_bytes, stream, 15, 17);
+    if (rc != 0 || batch == 0) return rc;
+    // Stage 2: the two triangular solves, on the last queue head (the factor
+    // uses at most NUM_BINS < MAX_GROUPS launch groups).
+    Sched s;
+    carve_workspace(d_work, batch, max_n, mode, &s);
+    cudaError_t e = launch_posv_solve(d_n, d_k, max_k, d_R, d_ldr, d_B, d_ldb, d_X, d_ldx, d_info, s,
+                                      MAX_GROUPS - 1, batch, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return SS_ERR_CUDA;
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return 0;
 }
 
 int trlyap_l(int batch, int max_n, const int *d_n, const double *const *d_L, const int *d_ldl,

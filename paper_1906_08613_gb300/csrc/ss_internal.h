@@ -78,7 +78,7 @@ struct Config {
 };
 int config_count(int op, int mode);
 const Config *config_get(int op, int mode, int cfg);
-int config_default(int op, int mode, int max_n);
+int config_default(int op, int mode, int max_n, int batch);
 
 // Kernel launchers (one per op).  Return cudaSuccess or the launch error.
 cudaError_t launch_potrf(const Operands &o, const Sched &s, const Launch &l, cudaStream_t st);
@@ -89,6 +89,12 @@ cudaError_t launch_trlyap(const Operands &o, const Sched &s, const Launch &l, cu
 // warps plus one diagonal warp).
 cudaError_t launch_syl_fp64_ws(int block, int nu, bool lyap, const Operands &o, const Sched &s, const Launch &l,
                                cudaStream_t st);
+
+// Solve stage of the SPD solve (R^T Y = B, R X = Y) over the valid instances
+// of a binning pass, on queue head `group`.
+cudaError_t launch_posv_solve(const int *d_n, const int *d_k, int max_k, const double *const *d_R, const int *d_ldr,
+                              const double *const *d_B, const int *d_ldb, double *const *d_X, const int *d_ldx,
+                              int *d_info, const Sched &s, int group, int batch, cudaStream_t st);
 
 // Number of SMs of the current device (cached per device).
 int sm_count();

@@ -115,3 +115,47 @@ class DeviceRectBatch:
 
     def info_host(self) -> np.ndarray:
         return self.info[: self.batch].cpu().numpy()
+
+
+class DevicePosvBatch:
+    """Device copy of an SPD-solve batch (inputs.PosvPacked) for posv_upper;
+    R is laid out like A, X like B."""
+
+    def __init__(self, pk, device="cuda", alias: bool = False, x_fill: float = 0.0,
+                 max_n: int | None = None, max_k: int | None = None):
+        self.device = torch.device(device)
+        self.batch = pk.batch
+        n = np.ascontiguousarray(pk.n, dtype=np.int32)
+        k = np.ascontiguousarray(pk.k, dtype=np.int32)
+        self.max_n = int(n.max()) if (max_n is None and self.batch) else int(max_n or 0)
+        self.max_k = int(k.max()) if (max_k is None and self.batch) else int(max_k or 0)
+        to = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(self.device)
+        self.d_n, self.d_k = to(n), to(k)
+        self.d_ld = to(np.maximum(n, 1).astype(np.int32))
+        self.bufs = {"A": to(pk.ops["A"]), "B": to(pk.ops["B"])}
+        self.R = self.bufs["A"] if alias else torch.full_like(self.bufs["A"], x_fill)
+        self.X = self.bufs["B"] if alias else torch.full_like(self.bufs["B"], x_fill)
+        oA, oB = to(pk.offA * 8), to(pk.offB * 8)
+        self.ptrs = {"A": (self.bufs["A"].data_ptr() + oA).contiguous(), "R": (self.R.data_ptr() + oA).contiguous(),
+                     "B": (self.bufs["B"].data_ptr() + oB).contiguous(), "X": (self.X.data_ptr() + oB).contiguous()}
+        self.info = torch.full((max(self.batch, 1),), 12345, dtype=torch.int32, device=self.device)
+        need = ss.ss_workspace_size(ss.OP_POTRF, self.batch, self.max_n, ss.MODE_FP64)
+        self.work = torch.empty(max(need, 256), dtype=torch.uint8, device=self.device)
+
+    def solve(self, cfg: int = ss.CFG_DEFAULT, mode: int = ss.MODE_FP64, stream: int = 0,
+              check: bool = True) -> int:
+        p, ld = self.ptrs, self.d_ld.data_ptr()
+        return ss.posv_upper(self.batch, self.max_n, self.max_k, self.d_n.data_ptr(), self.d_k.data_ptr(),
+                             p["A"].data_ptr(), ld, p["R"].data_ptr(), ld, p["B"].data_ptr(), ld,
+                             p["X"].data_ptr(), ld, self.info.data_ptr(), mode=mode, cfg=cfg,
+                             d_work=self.work.data_ptr(), work_bytes=int(self.work.numel()), stream=stream,
+                             check=check)
+
+    def x_host(self) -> np.ndarray:
+        return self.X.cpu().numpy()
+
+    def r_host(self) -> np.ndarray:
+        return self.R.cpu().numpy()
+
+    def info_host(self) -> np.ndarray:
+        return self.info[: self.batch].cpu().numpy()

@@ -281,7 +281,7 @@ def regret_report(choices, entries, buckets):
             continue
         t_c = tune.lookup(entries, op, k, batch, mode, cfg)
         t_b = best[key][2]
-        dflt = default_fp64_cfg(1 << k, op)
+        dflt = default_fp64_cfg(1 << k, op, batch)
         t_d = tune.lookup(entries, op, k, batch, "fp64", dflt)
         if t_c is None or t_d is None:
             continue
@@ -296,12 +296,15 @@ def regret_report(choices, entries, buckets):
             "rows": out}
 
 
-def default_fp64_cfg(max_n: int, op: str = "potrf") -> int:
-    """The library's built-in FP64 default (SS_CFG_DEFAULT) for a given max n."""
+def default_fp64_cfg(max_n: int, op: str = "potrf", batch: int = 2048) -> int:
+    """The library's built-in FP64 default (SS_CFG_DEFAULT) for a call with
+    this largest order and batch."""
+    if op == "potrf":
+        return 5 if max_n <= 16 else (6 if max_n <= 128 else 4)
     if max_n <= 8:
         return 0
-    if max_n <= 16:
-        return 1
     if max_n <= 32:
-        return 2
-    return 3 if op == "potrf" else 6
+        return 1
+    if max_n <= 64:
+        return 7
+    return 6 if (max_n <= 128 and batch >= 1024) else 5

@@ -73,7 +73,8 @@ def lib():
             L.trsyl_lu.argtypes = [i, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i, i, vp, sz, vp]
             L.trlyap_l.argtypes = [i, i, vp, vp, vp, vp, vp, vp, vp, vp, i, i, vp, sz, vp]
             L.trsyl_rect.argtypes = [i, i, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i, i, vp, sz, vp]
-            for f in (L.potrf_upper, L.trsyl_lu, L.trlyap_l, L.trsyl_rect):
+            L.posv_upper.argtypes = [i, i, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, i, i, vp, sz, vp]
+            for f in (L.potrf_upper, L.trsyl_lu, L.trlyap_l, L.trsyl_rect, L.posv_upper):
                 f.restype = i
             L.trsyl_lu_noalloc.argtypes = [i, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
             L.trsyl_lu_noalloc.restype = i
@@ -135,6 +136,14 @@ def trsyl_rect(batch, max_m, max_n, d_m, d_n, d_L, d_ldl, d_U, d_ldu, d_C, d_ldc
     rc = lib().trsyl_rect(batch, max_m, max_n, d_m, d_n, d_L, d_ldl, d_U, d_ldu, d_C, d_ldc, d_X, d_ldx,
                           d_info, mode, cfg, d_work, work_bytes, stream)
     return _check(rc, "trsyl_rect") if check else rc
+
+
+def posv_upper(batch, max_n, max_k, d_n, d_k, d_A, d_lda, d_R, d_ldr, d_B, d_ldb, d_X, d_ldx, d_info,
+               mode=MODE_FP64, cfg=CFG_DEFAULT, d_work=0, work_bytes=0, stream=0, check=True):
+    """SPD solve A X = B through the upper Cholesky factor R (written to d_R)."""
+    rc = lib().posv_upper(batch, max_n, max_k, d_n, d_k, d_A, d_lda, d_R, d_ldr, d_B, d_ldb, d_X, d_ldx,
+                          d_info, mode, cfg, d_work, work_bytes, stream)
+    return _check(rc, "posv_upper") if check else rc
 
 
 def trsyl_lu_noalloc(batch, max_n, d_n, d_L, d_ldl, d_U, d_ldu, d_C, d_ldc, d_X, d_ldx, d_info,

@@ -83,6 +83,23 @@ def test_rect_argument_errors_before_launch(lib):
     assert ss.trsyl_rect(0, 0, 0, *([0] * 11)) == 0
 
 
+def test_posv_argument_errors_before_launch(lib):
+    r = lambda *a, **k: ss.posv_upper(*a, check=False, **k)
+    ptr = [1] * 11                       # d_n, d_k, d_A, d_lda, ..., d_info: arguments 4..14
+    assert r(-1, 4, 4, *ptr) == -1
+    assert r(1, ss.MAX_N + 1, 4, *ptr) == -2
+    assert r(1, 4, -1, *ptr) == -3
+    for k in range(11):
+        p = list(ptr)
+        p[k] = 0
+        assert r(1, 4, 4, *p) == -(4 + k)
+    assert r(1, 4, 4, *ptr, mode=ss.MODE_TF32_REFINED) == -15
+    assert r(1, 4, 4, *ptr, cfg=999) == -16
+    assert r(1, 4, 4, *ptr, d_work=0) == -17
+    assert r(1, 4, 4, *ptr, d_work=1, work_bytes=1) == -18
+    assert ss.posv_upper(0, 0, 0, *([0] * 11)) == 0
+
+
 def test_config_table_validation(lib):
     with pytest.raises(ss.SmallSolveError):
         ss.ss_set_config_table(ss.OP_TRSYL, ss.MODE_FP64, [999])
