@@ -228,6 +228,62 @@ def launch_groups(table, max_n):
     return runs
 
 
+def e2e_pipelined(dbs, host_in, solve, steps, dist, dev, batch):
+    """End-to-end through the C ABI with host buffers, every step: H2D of the
+    step's inputs from pinned memory, the solve, D2H of X.  Two device copies
+    of the batch alternate between steps; H2D, the solve and D2H each have a
+    stream, so the copies of step s+1 and of step s-1 run under the solve of
+    step s (the GPU's copy engines work beside the SMs).  Returns (solves/s,
+    bytes in per step, bytes out per step, last X on the host)."""
+    import torch
+    names = list(host_in)
+    s_in, s_run, s_out = (torch.cuda.Stream(device=dev) for _ in range(3))
+    host_x = torch.empty_like(dbs[0].X, device="cpu").pin_memory()
+    ev = lambda: torch.cuda.Event()
+    h2d_done = [ev(), ev()]
+    run_done = [ev(), ev()]
+    d2h_done = [ev(), ev()]
+    for e in h2d_done + run_done + d2h_done:
+        e.record(s_run)
+
+    def one(s):
+        b = dbs[s % 2]
+        s_in.wait_event(run_done[s % 2])              # step s-2 finished reading the inputs
+        with torch.cuda.stream(s_in):
+            for k in names:
+                b.bufs[k].copy_(host_in[k], non_blocking=True)
+        h2d_done[s % 2].record(s_in)
+        s_run.wait_event(h2d_done[s % 2])
+        s_run.wait_event(d2h_done[s % 2])             # X of step s-2 has reached the host
+        with torch.cuda.stream(s_run):
+            solve(b, s_run.cuda_stream)
+        run_done[s % 2].record(s_run)
+        s_out.wait_event(run_done[s % 2])
+        with torch.cuda.stream(s_out):
+            host_x.copy_(b.X, non_blocking=True)
+        d2h_done[s % 2].record(s_out)
+
+    for s in range(2):
+        one(s)
+    torch.cuda.synchronize(dev)
+    barrier(dist, dev)
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(s_run)
+    s_in.wait_stream(s_run)
+    s_out.wait_stream(s_run)
+    for s in range(steps):
+        one(s)
+    s_run.wait_stream(s_out)
+    s_run.wait_stream(s_in)
+    f1.record(s_run)
+    torch.cuda.synchronize(dev)
+    ms = max_over_ranks(dist, f0.elapsed_time(f1), dev)
+    value = sum_over_ranks(dist, float(batch * steps), dev) / (ms * 1e-3)
+    h2d = sum(int(host_in[k].numel()) * 8 for k in names)
+    d2h = int(host_x.numel()) * 8
+    return value, h2d, d2h, host_x.numpy()
+
+
 def sample_indices(pk, k, seed=7):
     rng = np.random.default_rng(seed)
     k = min(k, pk.batch)
@@ -353,29 +409,11 @@ def run_extra(args):
     info = db.info_host()
 
     host_in = {k: torch.from_numpy(pk.ops[k]).pin_memory() for k in names}
-    host_x = torch.empty_like(db.X, device="cpu").pin_memory()
-    h2d = sum(int(v.numel()) * 8 for v in host_in.values())
-    d2h = int(host_x.numel()) * 8
-    e2e_steps = max(3, min(args.steps, 50))
-
-    def e2e_step():
-        for k, v in host_in.items():
-            db.bufs[k].copy_(v, non_blocking=True)
-        step()
-        host_x.copy_(db.X, non_blocking=True)
-
-    with torch.cuda.stream(stream):
-        e2e_step()
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        for _ in range(e2e_steps):
-            e2e_step()
-        f1.record(stream)
-    stream.synchronize()
-    e2e_ms = max_over_ranks(dist, f0.elapsed_time(f1), dev)
-    e2e_value = sum_over_ranks(dist, float(pk.batch * e2e_steps), dev) / (e2e_ms * 1e-3)
-    x_gpu = host_x.numpy()
+    _, _, db2, _, _, _, _ = extra_workload(name, args.seed, dev)
+    e2e_value, h2d, d2h, x_gpu = e2e_pipelined(
+        [db, db2], host_in, lambda b, st: b.solve(cfg=cfg, stream=st), max(3, min(args.steps, 50)),
+        dist, dev, pk.batch)
+    del db2
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -529,34 +567,15 @@ def main():
     kern_avg_ms = kern_ms / max(kern_calls, 1)
     info = db.info_host()
 
-    # End to end through the C ABI with host buffers: H2D of the inputs from
-    # pinned memory, the solve, D2H of X, every step.
+    # End to end through the C ABI with host buffers (see e2e_pipelined).
     names = [k for k in ("A", "L", "U", "C", "S") if k in db.bufs]
     host_in = {k: torch.from_numpy(pk.ops[k]).pin_memory() for k in names}
-    host_x = torch.empty_like(db.X, device="cpu").pin_memory()
-    h2d = sum(int(host_in[k].numel()) * 8 for k in names)
-    d2h = int(host_x.numel()) * 8
-    e2e_steps = max(3, min(args.steps, 50))
-
-    def e2e_step():
-        for k in names:
-            db.bufs[k].copy_(host_in[k], non_blocking=True)
-        step()
-        host_x.copy_(db.X, non_blocking=True)
-
-    with torch.cuda.stream(stream):
-        e2e_step()
-        barrier(dist, dev)
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        for _ in range(e2e_steps):
-            e2e_step()
-        f1.record(stream)
-    stream.synchronize()
-    e2e_ms = max_over_ranks(dist, f0.elapsed_time(f1), dev)
-    e2e_value = sum_over_ranks(dist, float(pk.batch * e2e_steps), dev) / (e2e_ms * 1e-3)
-    x_gpu = host_x.numpy()
+    db2 = DeviceBatch(pk.n, pk.off, pk.ops, op, device=dev)
+    db2.ensure_work(mode)
+    e2e_value, h2d, d2h, x_gpu = e2e_pipelined(
+        [db, db2], host_in, lambda b, st: b.solve(mode=mode, cfg=cfg, stream=st),
+        max(3, min(args.steps, 50)), dist, dev, pk.batch)
+    del db2
 
     # Plain FP64 in the same run (the comparator): default configuration, and
     # the autotuner's best FP64 configuration per size bin (FP64-only table).
