@@ -7,10 +7,11 @@
 //
 // One CTA per instance (persistent queue over the same size-sorted order as
 // the factor launch, on a queue head of its own).  Right-hand sides go in
-// chunks of 32 columns.  Per row block I the lazy update
+// chunks of 32 columns (16 when every instance has k <= 16).  Per row block I
+// the lazy update
 //   T = B_I - sum_{K<I} R_KI^T Y_K      (forward)
 //   T = Y_I - sum_{K>I} R_IK X_K        (backward)
-// is a B x 32 block product by all threads from shared tiles; the diagonal
+// is a B x (chunk) block product by all threads from shared tiles; the diagonal
 // block solve R_II^T Y_I = T (R_II X_I = T) is done by one warp, one lane per
 // column, the column's B entries in registers: x_i = t_i / r_ii, then every
 // later entry of the column subtracts its r * x_i at once, so the dependent
@@ -52,21 +53,23 @@ __device__ __forceinline__ void stage(double *S, const double *G, long ld, int r
     }
 }
 
-template <int BS, int T>
+// CW: right-hand-side columns per chunk (16 or 32; the kernel picks 16 when
+// k <= 16 so that no update multiplies padding columns).
+template <int BS, int T, int CW>
 __device__ void posv_instance(int n, int k, const double *R, long ldr, const double *Bm, long ldb, double *X,
                               long ldx, double *sm)
 {
     constexpr int LDR = PTile<BS>::LD, LDK = BS + 1;
-    constexpr int E = BS * KC / T;          // outputs per thread of a BS x KC block
-    static_assert((BS * KC) % T == 0, "threads must divide the block");
+    constexpr int E = BS * CW / T;          // outputs per thread of a BS x CW block
+    static_assert((BS * CW) % T == 0 && CW <= KC, "threads must divide the block");
     double *sR = sm;                          // BS x BS (ld LDR): R_KI or R_IK of a step
     double *sY = sR + BS * LDR;               // BS x KC (ld LDK): Y_K or X_K of a step
     double *sD = sY + KC * LDK;               // BS x BS: R_II
     double *sT = sD + BS * LDR;               // BS x KC: T handed to the diagonal warp
     double *sInv = sT + KC * LDK;             // BS reciprocals 1 / r_ii
     const int nb = (n + BS - 1) / BS;
-    for (int c0 = 0; c0 < k; c0 += KC) {
-        const int kc = min(KC, k - c0);
+    for (int c0 = 0; c0 < k; c0 += CW) {
+        const int kc = min(CW, k - c0);
         for (int pass = 0; pass < 2; ++pass) {
             const bool fwd = pass == 0;
             for (int q = 0; q < nb; ++q) {
@@ -86,14 +89,15 @@ __device__ void posv_instance(int n, int k, const double *R, long ldr, const dou
                     __syncthreads();
                     if (fwd) stage<BS, BS, LDR, T>(sR, R + k0 + (long)i0 * ldr, ldr, mK, mI);   // R_KI
                     else     stage<BS, BS, LDR, T>(sR, R + i0 + (long)k0 * ldr, ldr, mI, mK);   // R_IK
-                    stage<BS, KC, LDK, T>(sY, X + k0 + (long)c0 * ldx, ldx, mK, kc);           // Y_K / X_K
+                    stage<BS, CW, LDK, T>(sY, X + k0 + (long)c0 * ldx, ldx, mK, kc);           // Y_K / X_K
                     __syncthreads();
 #pragma unroll
                     for (int r = 0; r < E; ++r) {
                         const int e = threadIdx.x + T * r, row = e % BS, col = e / BS;
+                        if (col >= kc) continue;    // whole half-warps of padding columns skip
                         double s = acc[r];
 #pragma unroll 4
-                        for (int t = 0; t < BS; ++t) {
+                        for (int t = 0; t < mK; ++t) {
                             // forward: (R_KI^T)(row, t) = R_KI(t, row); backward: R_IK(row, t)
                             const double a = fwd ? sR[t + row * LDR] : sR[row + t * LDR];
                             s = fma(-a, sY[t + col * LDK], s);
@@ -148,6 +152,7 @@ __device__ void posv_instance(int n, int k, const double *R, long ldr, const dou
     }
 }
 
+template <int CW>
 __global__ void __launch_bounds__(128) posv_kernel(PosvOps o, Sched s, int group)
 {
     constexpr int BS = 16, T = 128;
@@ -166,7 +171,7 @@ __global__ void __launch_bounds__(128) posv_kernel(PosvOps o, Sched s, int group
             continue;
         }
         if (n == 0 || k == 0) continue;
-        posv_instance<BS, T>(n, k, o.R[b], o.ldr[b], o.B[b], o.ldb[b], o.X[b], o.ldx[b], sm);
+        posv_instance<BS, T, CW>(n, k, o.R[b], o.ldr[b], o.B[b], o.ldb[b], o.X[b], o.ldx[b], sm);
     }
 }
 
@@ -179,17 +184,18 @@ cudaError_t launch_posv_solve(const int *d_n, const int *d_k, int max_k, const d
 {
     constexpr int BS = 16, T = 128;
     const size_t smem = (size_t)(2 * BS * (BS + 1) + 2 * KC * (BS + 1) + BS) * sizeof(double);
-    cudaError_t e = cudaFuncSetAttribute(posv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kernel = max_k <= 16 ? posv_kernel<16> : posv_kernel<KC>;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, posv_kernel, T, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, T, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     long grid = (long)per_sm * sm_count();
     if (grid > batch) grid = batch;
     if (grid < 1) grid = 1;
     PosvOps o{d_n, d_k, d_R, d_ldr, d_B, d_ldb, d_X, d_ldx, d_info, max_k};
-    posv_kernel<<<(int)grid, T, smem, st>>>(o, s, group);
+    kernel<<<(int)grid, T, smem, st>>>(o, s, group);
     return cudaGetLastError();
 }
 
