@@ -43,3 +43,36 @@ def test_graph_capture_and_replay(op, mode):
             assert_parity(op, pk, db.x_host(), ref)
     finally:
         ss.ss_set_auto_table(o, [], [])
+
+
+def test_graph_capture_rect_and_posv():
+    import oracle
+    from paper_1906_08613_gb300.device import DevicePosvBatch, DeviceRectBatch
+    rk = inputs.sylvester_rect_batch(inputs.sizes_uniform(90, 1, 100, seed=52),
+                                     inputs.sizes_uniform(90, 1, 100, seed=53), seed=54)
+    pv = inputs.posv_batch(inputs.sizes_uniform(90, 1, 100, seed=55), inputs.sizes_uniform(90, 1, 24, seed=56),
+                           seed=57)
+    xr, ri = oracle.solve_rect_packed(rk)
+    xp, _, pi = oracle.solve_posv_packed(pv)
+    dr, dp = DeviceRectBatch(rk), DevicePosvBatch(pv)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        dr.solve(stream=st.cuda_stream)
+        dp.solve(stream=st.cuda_stream)
+    st.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        dr.solve(stream=st.cuda_stream)
+        dp.solve(stream=st.cuda_stream)
+    for _ in range(2):
+        dr.X.fill_(0.5)
+        dp.X.fill_(0.5)
+        dr.info.fill_(99)
+        dp.info.fill_(99)
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(dr.info_host(), ri) and np.array_equal(dp.info_host(), pi)
+        for got, ref, offs, cnt in ((dr.x_host(), xr, rk.offC, rk.m * rk.n), (dp.x_host(), xp, pv.offB, pv.n * pv.k)):
+            for o, c in zip(offs, cnt):
+                gg, rr = got[int(o):int(o) + int(c)], ref[int(o):int(o) + int(c)]
+                assert np.linalg.norm(gg - rr) <= 1e-11 * max(np.linalg.norm(rr), 1e-300)
