@@ -24,11 +24,12 @@ namespace {
 // variant 0: CTA-wide diagonal-block work; 1: one warp does the diagonal
 // blocks between CTA-wide updates (shorter dependent chain); 2 (Sylvester and
 // Lyapunov): warp-specialised pipeline, one diagonal warp and
-// (threads-32)/32 update warps.  At most eight per operation (the learned
+// (threads-32)/32 update warps; 3 (Cholesky): right-looking in shared memory
+// for n <= block (64), the variant-1 blocked path above.  At most eight per operation (the learned
 // selector predicts one time per configuration slot).
 const Config kFp64Potrf[] = {
     {8, 64, 0}, {16, 64, 0}, {16, 128, 0}, {32, 128, 0}, {32, 256, 0},
-    {16, 64, 1}, {16, 128, 1}, {32, 128, 1},
+    {16, 64, 1}, {16, 128, 1}, {64, 128, 3},
 };
 const Config kFp64Syl[] = {
     {8, 64, 0}, {16, 64, 0}, {16, 128, 0}, {32, 128, 0},

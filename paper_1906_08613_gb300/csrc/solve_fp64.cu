@@ -390,6 +390,13 @@ __device__ void potrf_instance(int n, const double *A, long lda, double *X, long
                 __syncthreads();
                 const int f = VAR == 0 ? chol_diag<B, T>(sT, nJ, s_scal) : chol_diag_warp<B, T>(sT, nJ, s_scal);
                 if (f) {
+                    // Rows above the failing pivot are final (both diagonal
+                    // solvers go row by row): write them, i.e. every column
+                    // of the block before the pivot.
+#pragma unroll
+                    for (int r = 0; r < E; ++r)
+                        if (sl.ok(r) && sl.row[r] < f - 1)
+                            X[(i0 + sl.row[r]) + (long)(j0 + sl.col[r]) * ldx] = sT[sl.row[r] + sl.col[r] * LD];
                     if (threadIdx.x == 0) *info = j0 + f;
                     return;     // uniform: every thread saw the same pivot
                 }
@@ -400,6 +407,59 @@ __device__ void potrf_instance(int n, const double *A, long lda, double *X, long
         }
     }
     if (threadIdx.x == 0) *info = 0;
+}
+
+// ------------------------------------- Cholesky, right-looking in shared memory
+//
+// For n <= NMAX the upper triangle of A sits in shared memory and is factored
+// in place column by column (right-looking): pivot k, row k scaled by
+// 1/sqrt(pivot), then the rank-1 update of the trailing upper triangle.  No
+// global traffic inside the factorisation, two CTA barriers per column, and
+// the update's FP64 instructions all carry useful FMAs (a flat map over the
+// trailing triangle).  Returns 0 or the failing pivot + 1; on failure at
+// pivot k the final rows 0..k-1 of X (so every column < k) are written.
+
+// Column c of the flat upper-triangle index e: c(c+1)/2 <= e < (c+1)(c+2)/2.
+__device__ __forceinline__ int tri_col(int e)
+{
+    int c = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+    while (c * (c + 1) / 2 > e) --c;
+    while ((c + 1) * (c + 2) / 2 <= e) ++c;
+    return c;
+}
+
+template <int NMAX, int T>
+__device__ int chol_rl_smem(int n, const double *A, long lda, double *X, long ldx, double *S)
+{
+    constexpr int LD = NMAX + 1;
+    for (int e = threadIdx.x; e < n * n; e += T) {
+        const int i = e % n, j = e / n;
+        if (i <= j) S[i + j * LD] = A[i + (long)j * lda];
+    }
+    __syncthreads();
+    int done = n, fail = 0;
+    for (int k = 0; k < n; ++k) {
+        const double d = S[k + k * LD];
+        if (!(d > 0.0)) { done = k; fail = k + 1; break; }   // every thread read the same pivot
+        const double r = rsqrt(d);
+        for (int j = k + 1 + threadIdx.x; j < n; j += T) S[k + j * LD] *= r;
+        __syncthreads();
+        // The pivot is read by all threads above; it is overwritten only now.
+        if (threadIdx.x == 0) S[k + k * LD] = d * r;
+        const int m = n - k - 1;
+        const int cnt = m * (m + 1) / 2;
+        for (int e = threadIdx.x; e < cnt; e += T) {
+            const int c = tri_col(e);
+            const int i = k + 1 + (e - c * (c + 1) / 2), j = k + 1 + c;
+            S[i + j * LD] = fma(-S[k + i * LD], S[k + j * LD], S[i + j * LD]);
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < n * n; e += T) {
+        const int i = e % n, j = e / n;
+        if (i <= j && i < done) X[i + (long)j * ldx] = S[i + j * LD];
+    }
+    return fail;
 }
 
 // --------------------------------------------------------------- kernels
@@ -424,6 +484,28 @@ __global__ void __launch_bounds__(T) potrf_fp64_kernel(Operands o, Sched s, int 
         const int n = o.n[b];
         if (n == 0) { if (threadIdx.x == 0) o.info[b] = 0; continue; }
         potrf_instance<B, T, VAR>(n, o.A[b], o.lda[b], o.X[b], o.ldx[b], o.info + b, sm);
+    }
+}
+
+// Right-looking shared-memory Cholesky for n <= NMAX; larger n in the same
+// call take the blocked lazy path (B = 16, one-warp diagonal blocks).
+template <int NMAX, int T>
+__global__ void __launch_bounds__(T) potrf_rl_kernel(Operands o, Sched s, int group)
+{
+    extern __shared__ double sm[];
+    __shared__ int s_slot;
+    int b;
+    claim_init(&s_slot);
+    while (next_instance(s, group, &s_slot, b)) {
+        const int n = o.n[b];
+        if (n == 0) { if (threadIdx.x == 0) o.info[b] = 0; continue; }
+        if (n <= NMAX) {
+            const int f = chol_rl_smem<NMAX, T>(n, o.A[b], o.lda[b], o.X[b], o.ldx[b], sm);
+            if (threadIdx.x == 0) o.info[b] = f;
+            __syncthreads();
+        } else {
+            potrf_instance<16, T, 1>(n, o.A[b], o.lda[b], o.X[b], o.ldx[b], o.info + b, sm);
+        }
     }
 }
 
@@ -471,6 +553,11 @@ cudaError_t launch_potrf_fp64(const Operands &o, const Sched &s, const Launch &l
 {
     const Config *c = config_get(SS_OP_POTRF, SS_MODE_FP64, l.cfg);
     if (c == nullptr) return cudaErrorInvalidValue;
+    if (c->variant == 3 && c->block == 64 && c->threads == 128) {
+        constexpr size_t rl = (size_t)64 * 65 * sizeof(double);
+        const size_t smem = rl > smem_bytes<16>() ? rl : smem_bytes<16>();
+        return launch_persistent(potrf_rl_kernel<64, 128>, 128, smem, l.batch, st, o, s, l.group);
+    }
 #define CASE(id, B, T, V) \
     if (c->block == B && c->threads == T && c->variant == V) \
         return launch_persistent(potrf_fp64_kernel<B, T, V>, T, smem_bytes<B>(), l.batch, st, o, s, l.group);

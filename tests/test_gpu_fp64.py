@@ -166,3 +166,28 @@ def test_fp64_full_workloads(name):
     ref, rinfo = oracle_batch(op, pk, threads=16)
     assert np.all(info == 0) and np.all(rinfo == 0)
     assert_parity(op, pk, x, ref, sentinel=SENT)
+
+
+@pytest.mark.parametrize("cfg", list(range(8)))
+def test_potrf_failure_every_config(cfg):
+    # A leading minor that is not positive: info = its order, the columns
+    # before the failing pivot equal the oracle's, the strict lower triangle
+    # of X stays untouched.
+    n = np.array([12, 40, 70, 9], dtype=np.int32)
+    pk = inputs.make_batch("potrf", n, seed=70 + cfg)
+    fails = {0: 5, 1: 30, 2: 66}
+    for b, k in fails.items():
+        a = pk.view("A", b)
+        a[k, k] = -1.0
+    ref, rinfo = oracle_batch("potrf", pk)
+    assert [int(rinfo[b]) for b in fails] == [k + 1 for k in fails.values()]
+    x, info = run("potrf", pk, cfg=cfg)
+    assert np.array_equal(info, rinfo)
+    for b in range(pk.batch):
+        nb, o = int(n[b]), int(pk.off[b])
+        g = x[o:o + nb * nb].reshape(nb, nb, order="F")
+        r = ref[o:o + nb * nb].reshape(nb, nb, order="F")
+        good = fails.get(b, nb)
+        gu, ru = np.triu(g[:, :good]), np.triu(r[:, :good])
+        assert np.linalg.norm(gu - ru) <= 1e-11 * max(np.linalg.norm(ru), 1e-300)
+        assert np.all(g[np.tril_indices(nb, -1)] == SENT)
