@@ -79,14 +79,16 @@ __device__ __forceinline__ void warp_stage_tri(double *S, const double *G, long 
 // sU upper or (UT) the transpose of the lower sU, reciprocal divisors in sR.
 // Anti-diagonal d = i + j at a time; each entry is a dot product of d terms,
 // split over `split` lanes (power of two, at most 32 / entries and at most
-// d) with two partial sums per lane to halve the dependent chain.
-template <int B, bool UT>
+// d) with two partial sums per lane to halve the dependent chain.  SYM (a
+// Lyapunov diagonal block, Ut = Lt^T, Y symmetric): only the entries i >= j
+// are solved and read; y_tj with t < j is read as y_jt.
+template <int B, bool UT, bool SYM>
 __device__ void warp_diag_solve(const double *sL, const double *sU, double *sT, const double *sR, int m,
                                 int nn, int lane)
 {
     constexpr int LD = Tile<B>::LD;
     for (int d = 0; d <= m + nn - 2; ++d) {
-        const int ilo = max(0, d - nn + 1), ihi = min(d, m - 1);
+        const int ilo = SYM ? max((d + 1) / 2, d - nn + 1) : max(0, d - nn + 1), ihi = min(d, m - 1);
         const int cnt = ihi - ilo + 1;
         int split = cnt >= 32 ? 1 : pow2_floor(32 / cnt);
         const int byLen = pow2_floor(d > 1 ? d : 1);
@@ -100,15 +102,18 @@ __device__ void warp_diag_solve(const double *sL, const double *sU, double *sT, 
             for (; t + split < d; t += 2 * split) {
                 const int t1 = t + split;
                 const double a0 = t < i ? sL[i + t * LD] : sT[i + (t - i) * LD];
-                const double b0 = t < i ? sT[t + j * LD] : (UT ? sU[j + (t - i) * LD] : sU[(t - i) + j * LD]);
+                const double b0 = t < i ? (SYM && t < j ? sT[j + t * LD] : sT[t + j * LD])
+                                        : (UT ? sU[j + (t - i) * LD] : sU[(t - i) + j * LD]);
                 const double a1 = t1 < i ? sL[i + t1 * LD] : sT[i + (t1 - i) * LD];
-                const double b1 = t1 < i ? sT[t1 + j * LD] : (UT ? sU[j + (t1 - i) * LD] : sU[(t1 - i) + j * LD]);
+                const double b1 = t1 < i ? (SYM && t1 < j ? sT[j + t1 * LD] : sT[t1 + j * LD])
+                                         : (UT ? sU[j + (t1 - i) * LD] : sU[(t1 - i) + j * LD]);
                 s0 = fma(a0, b0, s0);
                 s1 = fma(a1, b1, s1);
             }
             if (t < d) {
                 const double a0 = t < i ? sL[i + t * LD] : sT[i + (t - i) * LD];
-                const double b0 = t < i ? sT[t + j * LD] : (UT ? sU[j + (t - i) * LD] : sU[(t - i) + j * LD]);
+                const double b0 = t < i ? (SYM && t < j ? sT[j + t * LD] : sT[t + j * LD])
+                                        : (UT ? sU[j + (t - i) * LD] : sU[(t - i) + j * LD]);
                 s0 = fma(a0, b0, s0);
             }
         }
@@ -138,6 +143,26 @@ struct OutMap {
             if (e < m * nn) {
                 row[r] = e % m;
                 col[r] = e / m;
+                valid |= 1u << r;
+            }
+        }
+    }
+    // The m(m+1)/2 entries with row >= col of an m x m block (a Lyapunov
+    // diagonal block, whose upper part is the transpose).
+    __device__ __forceinline__ void set_lower(int m, int ut)
+    {
+        valid = 0u;
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int e = ut + TU * r;
+            row[r] = 0;
+            col[r] = 0;
+            if (e < m * (m + 1) / 2) {
+                int c = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+                while (c * (c + 1) / 2 > e) --c;
+                while ((c + 1) * (c + 2) / 2 <= e) ++c;
+                row[r] = c;
+                col[r] = e - c * (c + 1) / 2;
                 valid |= 1u << r;
             }
         }
@@ -312,8 +337,10 @@ __device__ void syl_ws_instance(int m, int n, const double *L, long ldl, const d
                 if (!LYAP) warp_stage_tri<B>(sU, U + j0 + (long)j0 * ldu, ldu, nJ, false, lane);
                 else       warp_stage_tri<B>(sU, L + j0 + (long)j0 * ldl, ldl, nJ, true, lane);
                 __syncwarp();
+                const bool sym = LYAP && I == J;
                 for (int e = lane; e < mI * nJ; e += 32) {
                     const int i = e % mI, j = e / mI;
+                    if (sym && i < j) continue;
                     const double dd = sL[i + i * LD] + sU[j + j * LD];
                     if (!(fabs(dd) > delta)) bad = 1;
                     sR[i + j * LD] = 1.0 / dd;
@@ -321,7 +348,17 @@ __device__ void syl_ws_instance(int m, int n, const double *L, long ldl, const d
                 __syncwarp();
                 double *sT = sT0 + (t & 1) * SZ;
                 named_sync(kBarT, TALL);                   // T of block t is in sT
-                warp_diag_solve<B, LYAP>(sL, sU, sT, sR, mI, nJ, lane);
+                if (sym) {
+                    warp_diag_solve<B, LYAP, true>(sL, sU, sT, sR, mI, nJ, lane);
+                    // Mirror: the block after X_00 reads it whole from here.
+                    for (int e = lane; e < mI * mI; e += 32) {
+                        const int i = e % mI, j = e / mI;
+                        if (i < j) sT[i + j * LD] = sT[j + i * LD];
+                    }
+                    __syncwarp();
+                } else {
+                    warp_diag_solve<B, LYAP, false>(sL, sU, sT, sR, mI, nJ, lane);
+                }
                 for (int e = lane; e < mI * nJ; e += 32) {
                     const int r = e % mI, c = e / mI;
                     if (!LYAP || I != J || r >= c) X[(i0 + r) + (long)(j0 + c) * ldx] = sT[r + c * LD];
@@ -343,7 +380,8 @@ __device__ void syl_ws_instance(int m, int n, const double *L, long ldl, const d
             const int jend = LYAP ? I + 1 : nb;
             for (int J = 0; J < jend; ++J, ++t) {
                 const int nJ = min(B, n - J * B), j0 = J * B;
-                om.set(mI, nJ, ut);
+                if (LYAP && I == J) om.set_lower(mI, ut);   // symmetric diagonal block: i >= j only
+                else                om.set(mI, nJ, ut);
                 double ae[E], ao[E];
 #pragma unroll
                 for (int r = 0; r < E; ++r) {
