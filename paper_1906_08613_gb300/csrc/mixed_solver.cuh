@@ -363,181 +363,6 @@ __device__ void mixed_instance(int n, const double *L, long ldl, const double *U
     if (threadIdx.x == 0) *info = bad ? 1 : (conv ? 0 : n + 1);
 }
 
-// ------------------------------------------------ shared-memory-resident variant
-//
-// For n <= NMAX the low-precision solves keep the whole problem in shared
-// memory as FP32: L, U (for the Lyapunov form U = L^T, stored explicitly) and
-// the right-hand side / solution D, each n x ld with ld = n | 1 (odd, so the
-// strided reads of a split dot product fall in distinct banks).  The solve is
-// the entry-wise recurrence run as a lazy wavefront over the anti-diagonals
-// d = i + j: the entries of one anti-diagonal are independent, and each is one
-// dot product of exactly d terms (i from row i of L, j from column j of U),
-// split over a power-of-two group of lanes; one barrier per anti-diagonal.
-// The residual reuses the same shared memory for its RB x RB double-float
-// tiles and writes to the scratch W; L and U are then reloaded.  Larger
-// instances fall back to the blocked path with B = 32.
-
-template <int T>
-__device__ void smem_wavefront(float *Xs, const float *Ls, const float *Us, int n, int ld,
-                               const float *Rinv)
-{
-    for (int d = 0; d <= 2 * n - 2; ++d) {
-        const int ilo = max(0, d - n + 1), ihi = min(d, n - 1);
-        const int cnt = ihi - ilo + 1;
-        const int split = pick_split<T>(cnt, d);
-        if (warp_has_work(cnt, split)) {
-            const int idx = threadIdx.x / split, part = threadIdx.x % split;
-            const bool act = idx < cnt;
-            const int i = ilo + (act ? idx : 0), j = d - i;
-            // Issue the divisor's global load first; the dot product hides it.
-            const float r = (act && part == 0) ? Rinv[i + (long)j * n] : 0.0f;
-            float s = 0.0f;
-            if (act) {
-#pragma unroll 4
-                for (int t = part; t < d; t += split) {
-                    const bool lt = t < i;
-                    const int k = t - i;
-                    const float a = lt ? Ls[i + t * ld] : Xs[i + k * ld];
-                    const float b = lt ? Xs[t + j * ld] : Us[k + j * ld];
-                    s = fmaf(a, b, s);
-                }
-            }
-            s = group_sum_f(s, split);
-            if (act && part == 0) Xs[i + j * ld] = (Xs[i + j * ld] - s) * r;
-        }
-        __syncthreads();
-    }
-}
-
-// Residual tile size of the shared-memory variant.
-template <int NMAX>
-struct SmemRB { static constexpr int value = NMAX >= 128 ? 64 : 32; };
-
-template <int NMAX>
-constexpr size_t smem_variant_bytes()
-{
-    // L, U and D (n x ld floats each, ld <= NMAX + 1), which the residual's
-    // two RB x RB tiles of 8-byte elements and the blocked fallback's five
-    // float tiles reuse, plus a reduction buffer.
-    constexpr size_t solve = (size_t)3 * NMAX * (NMAX + 1) * sizeof(float);
-    constexpr size_t res = (size_t)2 * FTile<SmemRB<NMAX>::value>::SZ * 8;
-    constexpr size_t blk = (size_t)5 * FTile<32>::SZ * sizeof(float);
-    constexpr size_t m1 = solve > res ? solve : res;
-    return (m1 > blk ? m1 : blk) + 64 * sizeof(float);
-}
-
-// Load L, U (the strict triangles the wavefront reads) as FP32 into shared
-// memory; with rhs, also load D from C (FP64) or from the float scratch W.
-template <int T, bool LYAP>
-__device__ void smem_load(float *Ls, float *Us, float *Xs, int n, int ld, const double *L, long ldl,
-                          const double *U, long ldu, const double *C, long ldc, const float *W)
-{
-    for (int e = threadIdx.x; e < n * n; e += T) {
-        const int a = e % n, b = e / n;
-        Ls[a + b * ld] = a > b ? d2f_trunc(L[a + (long)b * ldl]) : 0.0f;
-        const double u = LYAP ? L[b + (long)a * ldl] : U[a + (long)b * ldu];
-        Us[a + b * ld] = a < b ? d2f_trunc(u) : 0.0f;
-        if (W) {
-            float w = W[e];
-            if (LYAP && a < b) w = W[b + (long)a * n];    // residual holds the lower blocks
-            Xs[a + b * ld] = w;
-        } else if (C) {
-            const double c = (LYAP && a < b) ? C[b + (long)a * ldc] : C[a + (long)b * ldc];
-            Xs[a + b * ld] = d2f_trunc(c);
-        }
-    }
-    __syncthreads();
-}
-
-template <int NMAX, int T, bool LYAP, int RS>
-__device__ void smem_instance(int n, const double *L, long ldl, const double *U, long ldu,
-                              const double *C, long ldc, double *X, long ldx, int *info,
-                              float *W, bool raw, float *sm)
-{
-    constexpr int RB = SmemRB<NMAX>::value;
-    float *s_red = sm + (smem_variant_bytes<NMAX>() / sizeof(float) - 64);
-    float *Rinv = W + (long)n * n;
-    if (n > NMAX) {
-        // Blocked fallback: its five tiles live at the start of shared memory.
-        const int bad = reciprocal_divisors<T, LYAP>(n, L, ldl, U, ldu, Rinv, s_red);
-        low_solve<32, T, LYAP, P_FP32, true>(n, L, ldl, U, ldu, C, ldc, W, Rinv, sm);
-        const float nx = sqrtf(update_x<T, LYAP>(n, X, ldx, W, n, true, s_red));
-        int conv = nx == 0.0f || raw;
-        float prev = nx;
-        for (int it = 0; it < MAXIT && !conv; ++it) {
-            residual<32, T, LYAP, RS>(n, L, ldl, U, ldu, C, ldc, X, ldx, W, n, sm);
-            low_solve<32, T, LYAP, P_FP32, false>(n, L, ldl, U, ldu, C, ldc, W, Rinv, sm);
-            const float nd = sqrtf(update_x<T, LYAP>(n, X, ldx, W, n, false, s_red));
-            const float pred = prev > 0.0f ? nd * (nd / prev) : nd;
-            conv = (nd <= (float)SS_REFINE_TOL * nx) || (pred <= (float)SS_REFINE_TOL * nx);
-            prev = nd;
-        }
-        if (threadIdx.x == 0) *info = bad ? 1 : (conv ? 0 : n + 1);
-        return;
-    }
-    const int ld = n | 1;
-    float *Ls = sm, *Us = sm + (long)n * ld, *Xs = sm + 2l * n * ld;
-    const int bad = reciprocal_divisors<T, LYAP>(n, L, ldl, U, ldu, Rinv, s_red);
-    smem_load<T, LYAP>(Ls, Us, Xs, n, ld, L, ldl, U, ldu, C, ldc, nullptr);
-    smem_wavefront<T>(Xs, Ls, Us, n, ld, Rinv);
-    const float nx = sqrtf(update_x<T, LYAP>(n, X, ldx, Xs, ld, true, s_red));
-    int conv = nx == 0.0f || raw;
-    float prev = nx;
-    for (int it = 0; it < MAXIT && !conv; ++it) {
-        residual<RB, T, LYAP, RS>(n, L, ldl, U, ldu, C, ldc, X, ldx, W, n, sm);
-        smem_load<T, LYAP>(Ls, Us, Xs, n, ld, L, ldl, U, ldu, nullptr, 0, W);
-        smem_wavefront<T>(Xs, Ls, Us, n, ld, Rinv);
-        const float nd = sqrtf(update_x<T, LYAP>(n, X, ldx, Xs, ld, false, s_red));
-        const float pred = prev > 0.0f ? nd * (nd / prev) : nd;
-        conv = (nd <= (float)SS_REFINE_TOL * nx) || (pred <= (float)SS_REFINE_TOL * nx);
-        prev = nd;
-    }
-    if (threadIdx.x == 0) *info = bad ? 1 : (conv ? 0 : n + 1);
-}
-
-template <int NMAX, int T, bool LYAP, int RS>
-__global__ void __launch_bounds__(T) smem_syl_kernel(Operands o, Sched s, int group, int raw)
-{
-    extern __shared__ __align__(16) float smf[];
-    __shared__ int s_slot;
-    const int lo = s.meta[META_RANGE + 2 * group], hi = s.meta[META_RANGE + 2 * group + 1];
-    claim_init(&s_slot);
-    for (;;) {
-        const int w = lo + claim_slot(s.meta + META_HEAD + group, &s_slot);
-        if (w >= hi) break;
-        const int b = s.perm[w];
-        const int n = o.n[b];
-        if (n == 0) { if (threadIdx.x == 0) o.info[b] = 0; continue; }
-        const long long off = s.scr[w];
-        if (off + 2ll * n * n > s.scratch_elems) {
-            if (threadIdx.x == 0) o.info[b] = SS_INFO_NO_WORK;
-            continue;
-        }
-        float *W = static_cast<float *>(s.scratch) + off;
-        smem_instance<NMAX, T, LYAP, RS>(n, o.A[b], o.lda[b], LYAP ? nullptr : o.U[b],
-                                         LYAP ? 0 : o.ldu[b], o.C[b], o.ldc[b], o.X[b], o.ldx[b],
-                                         o.info + b, W, raw != 0, smf);
-    }
-}
-
-template <int NMAX, int T, bool LYAP, int RS>
-cudaError_t launch_smem_syl(const Operands &o, const Sched &s, const Launch &l, cudaStream_t st, int raw)
-{
-    auto kern = smem_syl_kernel<NMAX, T, LYAP, RS>;
-    const size_t smem = smem_variant_bytes<NMAX>();
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    long grid = (long)per_sm * sm_count();
-    if (grid > l.batch) grid = l.batch;
-    if (grid < 1) grid = 1;
-    kern<<<(int)grid, T, smem, st>>>(o, s, l.group, raw);
-    return cudaGetLastError();
-}
-
 template <int B, int T, bool LYAP, int P, int RS>
 __global__ void __launch_bounds__(T, 1024 / T) mixed_syl_kernel(Operands o, Sched s, int group, int raw)
 {

@@ -544,10 +544,11 @@ cudaError_t launch_persistent(K kernel, int threads, size_t smem, int batch, cud
 }  // namespace
 
 // The (B, T, diagonal variant: 0 CTA-wide, 1 one warp) instantiations the
-// FP64 configuration tables draw from.
-#define SS_FP64_CONFIGS(X)                                                                 \
-    X(0, 8, 64, 0) X(1, 16, 64, 0) X(2, 16, 128, 0) X(3, 32, 128, 0) X(4, 32, 256, 0) \
-    X(5, 16, 64, 1) X(6, 16, 128, 1) X(7, 32, 128, 1)
+// FP64 configuration tables (api.cu) draw from, per operation.
+#define SS_POTRF_CONFIGS(X)                                                    \
+    X(8, 64, 0) X(16, 64, 0) X(16, 128, 0) X(32, 128, 0) X(32, 256, 0) \
+    X(16, 64, 1) X(16, 128, 1)
+#define SS_SYL_CONFIGS(X) X(8, 64, 0) X(16, 64, 0) X(16, 128, 0) X(32, 128, 0) X(16, 128, 1)
 
 cudaError_t launch_potrf_fp64(const Operands &o, const Sched &s, const Launch &l, cudaStream_t st)
 {
@@ -558,10 +559,10 @@ cudaError_t launch_potrf_fp64(const Operands &o, const Sched &s, const Launch &l
         const size_t smem = rl > smem_bytes<16>() ? rl : smem_bytes<16>();
         return launch_persistent(potrf_rl_kernel<64, 128>, 128, smem, l.batch, st, o, s, l.group);
     }
-#define CASE(id, B, T, V) \
+#define CASE(B, T, V) \
     if (c->block == B && c->threads == T && c->variant == V) \
         return launch_persistent(potrf_fp64_kernel<B, T, V>, T, smem_bytes<B>(), l.batch, st, o, s, l.group);
-    SS_FP64_CONFIGS(CASE)
+    SS_POTRF_CONFIGS(CASE)
 #undef CASE
     return cudaErrorInvalidValue;
 }
@@ -571,11 +572,11 @@ cudaError_t launch_syl_fp64(const Operands &o, const Sched &s, const Launch &l, 
     const Config *c = config_get(lyap ? SS_OP_TRLYAP : SS_OP_TRSYL, SS_MODE_FP64, l.cfg);
     if (c == nullptr) return cudaErrorInvalidValue;
     if (c->variant == 2) return launch_syl_fp64_ws(c->block, (c->threads - 32) / 32, lyap, o, s, l, st);
-#define CASE(id, B, T, V)                                                                                \
+#define CASE(B, T, V)                                                                                    \
     if (c->block == B && c->threads == T && c->variant == V)                                             \
         return lyap ? launch_persistent(syl_fp64_kernel<B, T, true, V>, T, smem_bytes<B>(), l.batch, st, o, s, l.group) \
                     : launch_persistent(syl_fp64_kernel<B, T, false, V>, T, smem_bytes<B>(), l.batch, st, o, s, l.group);
-    SS_FP64_CONFIGS(CASE)
+    SS_SYL_CONFIGS(CASE)
 #undef CASE
     return cudaErrorInvalidValue;
 }
