@@ -22,13 +22,13 @@ namespace {
 
 // FP64 configurations per operation: (block B, threads per CTA, variant).
 // variant 0: CTA-wide diagonal-block work; 1: one warp does the diagonal
-// blocks between CTA-wide updates (shorter dependent chain); 2 (Sylvester and
-// Lyapunov): warp-specialised pipeline, one diagonal warp and
-// (threads-32)/32 update warps; 3 (Cholesky): right-looking in shared memory
-// for n <= block (64), the variant-1 blocked path above.  At most eight per operation (the learned
+// blocks between CTA-wide updates (shorter dependent chain); 2: warp-
+// specialised pipeline, one diagonal warp and (threads-32)/32 update warps;
+// 3 (Cholesky): right-looking in shared memory for n <= block (64), the
+// variant-1 blocked path above.  At most eight per operation (the learned
 // selector predicts one time per configuration slot).
 const Config kFp64Potrf[] = {
-    {8, 64, 0}, {16, 64, 0}, {16, 128, 0}, {32, 128, 0}, {32, 256, 0},
+    {16, 96, 2}, {16, 64, 0}, {16, 160, 2}, {32, 128, 0}, {32, 256, 0},
     {16, 64, 1}, {16, 128, 1}, {64, 128, 3},
 };
 const Config kFp64Syl[] = {
@@ -151,16 +151,18 @@ const Config *config_get(int op, int mode, int cfg)
 // Built-in default: a single configuration chosen from the largest order.
 // Built-in FP64 defaults, from the autotuner's timings on GB300 (fastest
 // configuration per size bin, batches 64..2048):
-//   Cholesky: one-warp diagonal blocks (B = 16) up to n = 128, then (32, 256);
+//   Cholesky: one-warp diagonal blocks (B = 16) up to n = 16, then the
+//   warp-specialised pipeline with two update warps (large batches up to
+//   n = 128) or four;
 //   Sylvester / Lyapunov: CTA-wide B = 8 / 16 up to n = 32, warp-specialised
 //   with one update warp up to 64, then two (large batches) or four.
 int config_default(int op, int mode, int max_n, int batch)
 {
     if (mode != SS_MODE_FP64) return 0;
     if (op == SS_OP_POTRF) {
-        if (max_n <= 16) return 5;        // (16, 64, 1)
-        if (max_n <= 128) return 6;       // (16, 128, 1)
-        return 4;                         // (32, 256, 0)
+        if (max_n <= 16) return 5;                       // (16, 64, 1)
+        if (max_n <= 128 && batch >= 1024) return 0;     // (16, 96, 2)
+        return 2;                                        // (16, 160, 2)
     }
     if (max_n <= 8) return 0;             // (8, 64, 0)
     if (max_n <= 32) return 1;            // (16, 64, 0)

@@ -545,15 +545,14 @@ cudaError_t launch_persistent(K kernel, int threads, size_t smem, int batch, cud
 
 // The (B, T, diagonal variant: 0 CTA-wide, 1 one warp) instantiations the
 // FP64 configuration tables (api.cu) draw from, per operation.
-#define SS_POTRF_CONFIGS(X)                                                    \
-    X(8, 64, 0) X(16, 64, 0) X(16, 128, 0) X(32, 128, 0) X(32, 256, 0) \
-    X(16, 64, 1) X(16, 128, 1)
+#define SS_POTRF_CONFIGS(X) X(16, 64, 0) X(32, 128, 0) X(32, 256, 0) X(16, 64, 1) X(16, 128, 1)
 #define SS_SYL_CONFIGS(X) X(8, 64, 0) X(16, 64, 0) X(16, 128, 0) X(32, 128, 0) X(16, 128, 1)
 
 cudaError_t launch_potrf_fp64(const Operands &o, const Sched &s, const Launch &l, cudaStream_t st)
 {
     const Config *c = config_get(SS_OP_POTRF, SS_MODE_FP64, l.cfg);
     if (c == nullptr) return cudaErrorInvalidValue;
+    if (c->variant == 2) return launch_potrf_fp64_ws(c->block, (c->threads - 32) / 32, o, s, l, st);
     if (c->variant == 3 && c->block == 64 && c->threads == 128) {
         constexpr size_t rl = (size_t)64 * 65 * sizeof(double);
         const size_t smem = rl > smem_bytes<16>() ? rl : smem_bytes<16>();

@@ -147,6 +147,18 @@ struct OutMap {
             }
         }
     }
+    // The m(m+1)/2 entries with row <= col of an m x m block (a Cholesky
+    // diagonal block).
+    __device__ __forceinline__ void set_upper(int m, int ut)
+    {
+        set_lower(m, ut);
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int x = row[r];
+            row[r] = col[r];
+            col[r] = x;
+        }
+    }
     // The m(m+1)/2 entries with row >= col of an m x m block (a Lyapunov
     // diagonal block, whose upper part is the transpose).
     __device__ __forceinline__ void set_lower(int m, int ut)
@@ -232,6 +244,26 @@ __device__ __forceinline__ void upd_fma(double (&ae)[B * B / TU], double (&ao)[B
                 const double b1 = TB ? Bm[om.col[r] + (k + 1) * LD] : Bm[k + 1 + om.col[r] * LD];
                 ae[r] = fma(-a0, b0, ae[r]);
                 ao[r] = fma(-a1, b1, ao[r]);
+            }
+        }
+    }
+}
+
+// acc -= A^T * Bm over B terms: A(row, k) read as A[k + row*LD] (the tile
+// holds X_KI, used as X_KI^T), Bm(k, col) = Bm[k + col*LD].
+template <int B, int TU>
+__device__ __forceinline__ void upd_fma_ta(double (&ae)[B * B / TU], double (&ao)[B * B / TU],
+                                           const OutMap<B, TU> &om, const double *A, const double *Bm)
+{
+    constexpr int LD = Tile<B>::LD;
+    constexpr int E = B * B / TU;
+#pragma unroll 2
+    for (int k = 0; k < B; k += 2) {
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            if (om.ok(r)) {
+                ae[r] = fma(-A[k + om.row[r] * LD], Bm[k + om.col[r] * LD], ae[r]);
+                ao[r] = fma(-A[k + 1 + om.row[r] * LD], Bm[k + 1 + om.col[r] * LD], ao[r]);
             }
         }
     }
@@ -452,6 +484,180 @@ __device__ void syl_ws_instance(int m, int n, const double *L, long ldl, const d
     }
 }
 
+// ------------------------------------------------ Cholesky, warp-specialised
+//
+// The lazy blocked Cholesky (X^T X = A, X upper), blocks (I, J) by columns,
+// I = 0..J: T_IJ = A_IJ - sum_{K<I} X_KI^T X_KJ, then X_JJ = chol(T_JJ) or
+// X_IJ = X_II^{-T} T_IJ.  Warp 0 factors diagonal blocks and runs the panel
+// solves (latency-bound); the update warps form T.  The term K = I-1 needs
+// X_{I-1,J}, the block solved just before, so it is added from shared memory
+// once that block is final (its other operand X_{I-1,I} is in an earlier
+// column, or for I = J the same tile); the other terms overlap the diagonal
+// warp's previous block.  Same two named barriers per block as the Sylvester
+// pipeline.  After a failing pivot both roles finish the schedule (columns
+// from the failing one on are undefined) so that every barrier phase
+// completes; info is the first failure.
+
+// Factor the m x m upper block in sT in place (rows in order, 32/B lanes per
+// column, one FP64 rsqrt per row).  Returns 0 or the failing pivot + 1.
+template <int B>
+__device__ int warp_chol_diag(double *sT, int m, int lane)
+{
+    constexpr int LD = Tile<B>::LD;
+    constexpr int S = 32 / B;
+    const int idx = lane / S, part = lane % S;
+    for (int i = 0; i < m; ++i) {
+        const int j = i + idx;
+        const bool act = j < m;
+        double s = 0.0;
+        if (act)
+            for (int k = part; k < i; k += S) s = fma(sT[k + i * LD], sT[k + j * LD], s);
+        for (int o = S >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        const double t = act ? sT[i + j * LD] - s : 0.0;
+        const double d = __shfl_sync(0xffffffffu, t, 0);
+        if (!(d > 0.0)) return i + 1;
+        const double r = rsqrt(d);
+        if (act && part == 0) sT[i + j * LD] = (j == i) ? d * r : t * r;
+        __syncwarp();
+    }
+    return 0;
+}
+
+// X_II^T Y = T in place for the B x nn block in sT (X_II upper in sD,
+// reciprocal diagonal in sR): rows in order, 32/B lanes per column.
+template <int B>
+__device__ void warp_trsm_ut(const double *sD, const double *sR, double *sT, int nn, int lane)
+{
+    constexpr int LD = Tile<B>::LD;
+    constexpr int S = 32 / B;
+    const int idx = lane / S, part = lane % S;
+    const bool act = idx < nn;
+    for (int i = 0; i < B; ++i) {
+        double s = 0.0;
+        if (act)
+            for (int k = part; k < i; k += S) s = fma(sD[k + i * LD], sT[k + idx * LD], s);
+        for (int o = S >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (act && part == 0) sT[i + idx * LD] = (sT[i + idx * LD] - s) * sR[i];
+        __syncwarp();
+    }
+}
+
+template <int B, int NU>
+__device__ void chol_ws_instance(int n, const double *A, long lda, double *X, long ldx, int *info, double *sm)
+{
+    constexpr int LD = Tile<B>::LD, SZ = Tile<B>::SZ;
+    constexpr int TU = 32 * NU, TALL = TU + 32;
+    static_assert((B * B) % TU == 0, "update threads must divide the block");
+    double *sT0 = sm, *sD = sm + 2 * SZ, *sR = sm + 3 * SZ;
+    double *sA0 = sm + 5 * SZ, *sB0 = sm + 7 * SZ;
+    const int nb = (n + B - 1) / B;
+
+    if (threadIdx.x < 32) {
+        // ------------------------------------------------ diagonal warp
+        const int lane = threadIdx.x;
+        int fail = 0, t = 0;
+        for (int J = 0; J < nb; ++J) {
+            const int nJ = min(B, n - J * B), j0 = J * B;
+            for (int I = 0; I <= J; ++I, ++t) {
+                const int i0 = I * B;
+                if (I < J) {
+                    warp_stage_tri<B>(sD, X + i0 + (long)i0 * ldx, ldx, B, false, lane);
+                    __syncwarp();
+                    if (lane < B) sR[lane] = 1.0 / sD[lane * (LD + 1)];
+                    __syncwarp();
+                }
+                double *sT = sT0 + (t & 1) * SZ;
+                named_sync(kBarT, TALL);                   // T of block t is in sT
+                int f = 0;
+                if (I < J) warp_trsm_ut<B>(sD, sR, sT, nJ, lane);
+                else       f = warp_chol_diag<B>(sT, nJ, lane);
+                if (f && !fail) fail = j0 + f;
+                const int mI = I < J ? B : nJ;
+                for (int e = lane; e < mI * nJ; e += 32) {
+                    const int r = e % mI, c = e / mI;
+                    // diagonal block: upper part; after a failing pivot only
+                    // the rows above it are final.
+                    if (I < J || (r <= c && (!f || r < f - 1)))
+                        X[(i0 + r) + (long)(j0 + c) * ldx] = sT[r + c * LD];
+                }
+                named_arrive(kBarX, TALL);                 // X of block t is final
+            }
+        }
+        if (lane == 0) *info = fail;
+    } else {
+        // ------------------------------------------------- update warps
+        constexpr int E = B * B / TU;
+        const int ut = threadIdx.x - 32;
+        OutMap<B, TU> om;
+        Prefetch<B, TU> pf;
+        int t = 0;
+        for (int J = 0; J < nb; ++J) {
+            const int nJ = min(B, n - J * B), j0 = J * B;
+            for (int I = 0; I <= J; ++I, ++t) {
+                const int i0 = I * B;
+                const bool diag = I == J;
+                const int mI = diag ? nJ : B;
+                if (diag) om.set_upper(nJ, ut);
+                else      om.set(mI, nJ, ut);
+                // Bulk K = 0..I-2; then, for I < J, the staged X_{I-1,I} of the last term.
+                const int nsteps = I > 1 ? I - 1 : 0;
+                const bool has_last = I >= 1;
+                const int nload = nsteps + (has_last && !diag ? 1 : 0);
+                auto bulk_src = [&](int K, Src &sa, Src &sb) {
+                    const int k0 = K * B;
+                    sa = Src{X + k0 + (long)i0 * ldx, ldx, B, mI, false};   // X_KI (used transposed)
+                    sb = Src{X + k0 + (long)j0 * ldx, ldx, B, nJ, false};   // X_KJ
+                };
+                Src sa, sb;
+                if (nload > 0) {
+                    if (nsteps > 0) {
+                        bulk_src(0, sa, sb);
+                        pf.load(sa, sb, true, ut);
+                    } else {
+                        sb = Src{X + (long)(I - 1) * B + (long)i0 * ldx, ldx, B, mI, false};   // X_{I-1,I}
+                        pf.load(sa, sb, false, ut);
+                    }
+                    pf.store(sA0, sB0, nsteps > 0, ut);
+                    named_sync(kBarUpd, TU);
+                }
+                double ae[E], ao[E];
+#pragma unroll
+                for (int r = 0; r < E; ++r) {
+                    ao[r] = 0.0;
+                    ae[r] = om.ok(r) ? A[(i0 + om.row[r]) + (long)(j0 + om.col[r]) * lda] : 0.0;
+                }
+                for (int s = 0; s < nsteps; ++s) {
+                    const int buf = s & 1;
+                    const bool more = s + 1 < nload, next_bulk = s + 1 < nsteps;
+                    if (more) {
+                        if (next_bulk) bulk_src(s + 1, sa, sb);
+                        else sb = Src{X + (long)(I - 1) * B + (long)i0 * ldx, ldx, B, mI, false};
+                        pf.load(sa, sb, next_bulk, ut);
+                    }
+                    upd_fma_ta<B, TU>(ae, ao, om, sA0 + buf * SZ, sB0 + buf * SZ);
+                    if (more) pf.store(sA0 + (buf ^ 1) * SZ, sB0 + (buf ^ 1) * SZ, next_bulk, ut);
+                    named_sync(kBarUpd, TU);
+                }
+                if (t > 0) named_sync(kBarX, TALL);        // X of block t-1 is final
+                if (has_last) {
+                    // K = I-1: X_{I-1,J} is block t-1, in shared memory; X_{I-1,I}
+                    // is the staged tile, or for I = J that same block.
+                    const double *sXp = sT0 + ((t - 1) & 1) * SZ;
+                    const double *sV = diag ? sXp : sB0 + (nsteps & 1) * SZ;
+                    upd_fma_ta<B, TU>(ae, ao, om, sV, sXp);
+                }
+                double *sT = sT0 + (t & 1) * SZ;
+#pragma unroll
+                for (int r = 0; r < E; ++r)
+                    if (om.ok(r)) sT[om.row[r] + om.col[r] * LD] = ae[r] + ao[r];
+                named_sync(kBarUpd, TU);                   // staging tiles free again
+                named_arrive(kBarT, TALL);                 // T of block t is in sT
+            }
+        }
+        named_sync(kBarX, TALL);                           // X of the last block is final
+    }
+}
+
 __device__ __forceinline__ bool next_instance(const Sched &s, int group, int *s_slot, int &b)
 {
     const int lo = s.meta[META_RANGE + 2 * group], hi = s.meta[META_RANGE + 2 * group + 1];
@@ -496,6 +702,34 @@ cudaError_t launch_ws(K kernel, int threads, size_t smem, int batch, cudaStream_
 }
 
 }  // namespace
+
+template <int B, int NU, int MINB>
+__global__ void __launch_bounds__(32 * NU + 32, MINB) chol_ws_kernel(Operands o, Sched s, int group)
+{
+    extern __shared__ double sm[];
+    __shared__ int s_slot;
+    int b;
+    claim_init(&s_slot);
+    while (next_instance(s, group, &s_slot, b)) {
+        const int n = o.n[b];
+        if (n == 0) { if (threadIdx.x == 0) o.info[b] = 0; continue; }
+        chol_ws_instance<B, NU>(n, o.A[b], o.lda[b], o.X[b], o.ldx[b], o.info + b, sm);
+    }
+}
+
+// Warp-specialised Cholesky configurations: block B, NU update warps.
+cudaError_t launch_potrf_fp64_ws(int block, int nu, const Operands &o, const Sched &s, const Launch &l,
+                                 cudaStream_t st)
+{
+#define CWS_CASE(BB, NN, MB)                                                                              \
+    if (block == BB && nu == NN)                                                                          \
+        return launch_ws(chol_ws_kernel<BB, NN, MB>, 32 * NN + 32, ws_smem_bytes<BB>(), l.batch, st, o, s, \
+                         l.group);
+    CWS_CASE(16, 2, 8)
+    CWS_CASE(16, 4, 6)
+#undef CWS_CASE
+    return cudaErrorInvalidValue;
+}
 
 // Warp-specialised configurations: block B, NU update warps (+1 diagonal warp).
 cudaError_t launch_syl_fp64_ws(int block, int nu, bool lyap, const Operands &o, const Sched &s, const Launch &l,

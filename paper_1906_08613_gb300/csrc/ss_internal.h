@@ -90,6 +90,11 @@ cudaError_t launch_trlyap(const Operands &o, const Sched &s, const Launch &l, cu
 cudaError_t launch_syl_fp64_ws(int block, int nu, bool lyap, const Operands &o, const Sched &s, const Launch &l,
                                cudaStream_t st);
 
+// FP64 Cholesky with warp-specialised CTAs (block B, nu update warps plus one
+// diagonal warp).
+cudaError_t launch_potrf_fp64_ws(int block, int nu, const Operands &o, const Sched &s, const Launch &l,
+                                 cudaStream_t st);
+
 // Solve stage of the SPD solve (R^T Y = B, R X = Y) over the valid instances
 // of a binning pass, on queue head `group`.
 cudaError_t launch_posv_solve(const int *d_n, const int *d_k, int max_k, const double *const *d_R, const int *d_ldr,

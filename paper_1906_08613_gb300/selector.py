@@ -300,7 +300,9 @@ def default_fp64_cfg(max_n: int, op: str = "potrf", batch: int = 2048) -> int:
     """The library's built-in FP64 default (SS_CFG_DEFAULT) for a call with
     this largest order and batch."""
     if op == "potrf":
-        return 5 if max_n <= 16 else (6 if max_n <= 128 else 4)
+        if max_n <= 16:
+            return 5
+        return 0 if (max_n <= 128 and batch >= 1024) else 2
     if max_n <= 8:
         return 0
     if max_n <= 32:
