@@ -380,6 +380,7 @@ def run_extra(args):
     name = args.workload
     cfg = ss.CFG_DEFAULT if args.cfg is None else args.cfg
     opname, pk, db, F, Balg, names, oracle_one = extra_workload(name, args.seed, dev)
+    torch.cuda.synchronize(dev)         # buffer fills (default stream) before the side streams
 
     def step():
         db.solve(cfg=cfg, stream=sh)
@@ -410,6 +411,7 @@ def run_extra(args):
 
     host_in = {k: torch.from_numpy(pk.ops[k]).pin_memory() for k in names}
     _, _, db2, _, _, _, _ = extra_workload(name, args.seed, dev)
+    torch.cuda.synchronize(dev)
     e2e_value, h2d, d2h, x_gpu = e2e_pipelined(
         [db, db2], host_in, lambda b, st: b.solve(cfg=cfg, stream=st), max(3, min(args.steps, 50)),
         dist, dev, pk.batch)
@@ -514,6 +516,7 @@ def main():
 
     db = DeviceBatch(pk.n, pk.off, pk.ops, op, device=dev)
     db.ensure_work(mode)
+    torch.cuda.synchronize(dev)         # buffer fills (default stream) before the side streams
     F = flops_paper(op, pk.n)
     Falg = flops_algorithmic(op, pk.n)
     Balg = bytes_algorithmic(op, pk.n)
@@ -572,6 +575,7 @@ def main():
     host_in = {k: torch.from_numpy(pk.ops[k]).pin_memory() for k in names}
     db2 = DeviceBatch(pk.n, pk.off, pk.ops, op, device=dev)
     db2.ensure_work(mode)
+    torch.cuda.synchronize(dev)
     e2e_value, h2d, d2h, x_gpu = e2e_pipelined(
         [db, db2], host_in, lambda b, st: b.solve(mode=mode, cfg=cfg, stream=st),
         max(3, min(args.steps, 50)), dist, dev, pk.batch)

@@ -27,6 +27,7 @@ def test_graph_capture_and_replay(op, mode):
     try:
         db = DeviceBatch(pk.n, pk.off, pk.ops, op)
         db.ensure_work(mode)
+        torch.cuda.synchronize()            # buffer fills (default stream) before the side stream
         st = torch.cuda.Stream()
         with torch.cuda.stream(st):
             db.solve(mode=mode, stream=st.cuda_stream)      # warm-up outside capture
@@ -55,6 +56,7 @@ def test_graph_capture_rect_and_posv():
     xr, ri = oracle.solve_rect_packed(rk)
     xp, _, pi = oracle.solve_posv_packed(pv)
     dr, dp = DeviceRectBatch(rk), DevicePosvBatch(pv)
+    torch.cuda.synchronize()
     st = torch.cuda.Stream()
     with torch.cuda.stream(st):
         dr.solve(stream=st.cuda_stream)
