@@ -21,7 +21,6 @@ struct GroupMap {
     int ngroups;
 };
 
-__device__ __forceinline__ int size_bin(int n) { return n <= 1 ? 0 : 32 - __clz(n - 1); }
 
 // Sort key of instance b: its order n; with d_m, max(m, n), or -1 when m or
 // n is out of range.
