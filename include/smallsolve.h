@@ -27,7 +27,11 @@
  * X and the lower triangle of the Lyapunov X are written; the other strict
  * triangle of X is left untouched.  The Sylvester X is written in full.
  * X may alias the right-hand side (X == A, X == C or X == S per instance with
- * the same leading dimension); it must not overlap anything else.
+ * the same leading dimension) in SS_MODE_FP64 and the *_RAW modes; it must not
+ * overlap anything else.  The *_REFINED modes read the original right-hand
+ * side at every refinement step, so they need X separate from it (as
+ * mixed-precision LAPACK drivers take B and X separately); an aliased
+ * instance gets info = SS_INFO_ALIASED and is left untouched.
  *
  * Sizes.  0 <= d_n[b] <= max_n <= SS_MAX_N.  max_n is a host-side bound used to
  * size the launch; an instance whose device-side n violates it is skipped and
@@ -65,7 +69,8 @@
  *   n + 1  (refined modes) refinement did not reach SS_REFINE_TOL within
  *                      SS_REFINE_MAXIT steps; X holds the last iterate;
  *   SS_INFO_BAD_SIZE   d_n[b] < 0 or d_n[b] > max_n; X untouched;
- *   SS_INFO_NO_WORK    the workspace was too small for this instance.
+ *   SS_INFO_NO_WORK    the workspace was too small for this instance;
+ *   SS_INFO_ALIASED    (refined modes) X aliases the right-hand side; X untouched.
  *
  * Streams.  `stream` is a cudaStream_t (NULL: the legacy default stream).
  * Every call is asynchronous with respect to the host.  When a call uses
@@ -111,6 +116,7 @@ extern "C" {
 #define SS_ERR_SCRATCH_LIMIT (-101)
 #define SS_INFO_BAD_SIZE  (-1)
 #define SS_INFO_NO_WORK   (-2)
+#define SS_INFO_ALIASED   (-3)
 
 #define SS_REFINE_MAXIT 10
 #define SS_REFINE_TOL   1e-13

@@ -376,6 +376,9 @@ __global__ void __launch_bounds__(T, 1024 / T) mixed_syl_kernel(Operands o, Sche
         const int b = s.perm[w];
         const int n = o.n[b];
         if (n == 0) { if (threadIdx.x == 0) o.info[b] = 0; continue; }
+        // The refinement reads the original right-hand side at every step,
+        // so it cannot run in place: an aliased X is left untouched.
+        if (!raw && o.X[b] == o.C[b]) { if (threadIdx.x == 0) o.info[b] = SS_INFO_ALIASED; continue; }
         const long long off = s.scr[w];
         if (off + 2ll * n * n > s.scratch_elems) {
             if (threadIdx.x == 0) o.info[b] = SS_INFO_NO_WORK;

@@ -41,6 +41,7 @@ CFG_TABLE = -2
 ERR_CUDA = -100
 ERR_SCRATCH_LIMIT = -101
 INFO_BAD_SIZE = -1
+INFO_ALIASED = -3
 INFO_NO_WORK = -2
 MAX_N = 4096
 MLP_IN, MLP_HIDDEN, MLP_OUT = 9, 64, 8

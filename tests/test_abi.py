@@ -37,6 +37,13 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, name), f"{name} declared in smallsolve.h but not exported"
 
 
+def test_info_codes_match_header():
+    import re
+    text = open(HEADER).read()
+    codes = dict(re.findall(r"#define SS_(INFO_[A-Z_]+)\s+\((-?\d+)\)", text))
+    assert codes and all(getattr(ss, k) == int(v) for k, v in codes.items())
+
+
 def test_host_side_queries(lib):
     assert ss.ss_version() >= 1
     for op in (ss.OP_POTRF, ss.OP_TRSYL, ss.OP_TRLYAP):
