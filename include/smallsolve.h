@@ -27,7 +27,7 @@
  * X and the lower triangle of the Lyapunov X are written; the other strict
  * triangle of X is left untouched.  The Sylvester X is written in full.
  * X may alias the right-hand side (X == A, X == C or X == S per instance with
- * the same leading dimension) in SS_MODE_FP64 and the *_RAW modes; it must not
+ * the same leading dimension) in SS_MODE_FP64, SS_MODE_DF and the *_RAW modes; it must not
  * overlap anything else.  The *_REFINED modes read the original right-hand
  * side at every refinement step, so they need X separate from it (as
  * mixed-precision LAPACK drivers take B and X separately); an aliased
@@ -45,9 +45,20 @@
  * SS_REFINE_MAXIT steps ran.  The *_RAW modes stop after the low-precision
  * solve.  Refined and raw modes need workspace (see ss_workspace_size).
  *
+ * SS_MODE_DF (trsyl_lu, trlyap_l, trsyl_rect): the warp-specialised FP64
+ * pipeline with its block updates T = C - sum L X - sum X U in double-float
+ * arithmetic (each FP64 operand split into two floats, about 48 significant
+ * bits; error-free products and sums on the FP32 pipe).  The diagonal blocks,
+ * the divisions l_ii + u_jj and X stay FP64; no refinement and no workspace
+ * beyond FP64's.  Accuracy is that of FP64 up to the split's 2^-47 relative
+ * representation error per operand.  Values must lie in FP32's normal range
+ * (magnitude about 1.2e-38 to 3.4e38); outside it the split loses the
+ * double-float accuracy.
+ *
  * SS_MODE_AUTO solves each size bin in the (mode, cfg) pair given by
  * ss_set_auto_table (the autotuner's or the learned selector's choice among
- * FP64 and the refined modes, all of which meet the same accuracy); bins the
+ * FP64, SS_MODE_DF and the refined modes, all of which meet the same
+ * accuracy); bins the
  * table leaves unset run in SS_MODE_FP64 with the default configuration, and
  * `cfg` is ignored.
  *
@@ -104,8 +115,9 @@ extern "C" {
 #define SS_MODE_FP32_RAW      4
 #define SS_MODE_TF32_RAW      5
 #define SS_MODE_BF16_RAW      6
-#define SS_NUM_MODES          7
+#define SS_NUM_MODES          7   /* modes 0..6 above; SS_MODE_DF is numbered after SS_MODE_AUTO */
 #define SS_MODE_AUTO          7   /* per-size (mode, cfg) table, see ss_set_auto_table */
+#define SS_MODE_DF            8   /* double-float block updates, FP64 diagonal blocks */
 
 /* configuration selectors */
 #define SS_CFG_DEFAULT (-1)
@@ -154,7 +166,7 @@ int trsyl_lu(int batch, int max_n, const int *d_n,
  * SS_INFO_BAD_SIZE and is left untouched; m = 0 or n = 0 is empty (info 0).
  * info = 1 when some |l_ii + u_jj| <= max(m, n) * DBL_EPSILON * max diagonal
  * magnitude of L and U, or is NaN.  Instances are scheduled longest-first by
- * max(m, n).  mode must be SS_MODE_FP64 (other modes return -15); cfg as for
+ * max(m, n).  mode must be SS_MODE_FP64 or SS_MODE_DF (other modes return -15); cfg as for
  * trsyl_lu (the Sylvester configurations and tables).  Workspace: the size
  * ss_workspace_size(SS_OP_TRSYL, batch, max(max_m, max_n), SS_MODE_FP64, ...)
  * reports.

@@ -13,6 +13,8 @@ namespace ss {
 
 cudaError_t launch_potrf_fp64(const Operands &o, const Sched &s, const Launch &l, cudaStream_t st);
 cudaError_t launch_syl_fp64(const Operands &o, const Sched &s, const Launch &l, cudaStream_t st, bool lyap);
+cudaError_t launch_syl_ws(int block, int nu, bool lyap, bool df, const Operands &o, const Sched &s, const Launch &l,
+                          cudaStream_t st);
 cudaError_t launch_mixed(int op, const Operands &o, const Sched &s, const Launch &l, cudaStream_t st);
 int mixed_config_count(int op, int mode);
 const Config *mixed_config_get(int op, int mode, int cfg);
@@ -37,21 +39,27 @@ const Config kFp64Syl[] = {
 };
 constexpr int kNumFp64Potrf = sizeof(kFp64Potrf) / sizeof(kFp64Potrf[0]);
 constexpr int kNumFp64Syl = sizeof(kFp64Syl) / sizeof(kFp64Syl[0]);
+// SS_MODE_DF (Sylvester / Lyapunov): variant 4, the warp-specialised pipeline
+// with double-float update warps.
+const Config kDfSyl[] = {{16, 64, 4}, {16, 96, 4}, {16, 160, 4}};
+constexpr int kNumDfSyl = sizeof(kDfSyl) / sizeof(kDfSyl[0]);
+// Mode ids 0..SS_MODE_DF index the per-mode tables (SS_MODE_AUTO's slot unused).
+constexpr int kModeSlots = SS_MODE_DF + 1;
 
 int host_bin(int n) { int k = 0; while ((1 << k) < n) ++k; return k; }
 
 bool valid_op(int op) { return op == SS_OP_POTRF || op == SS_OP_TRSYL || op == SS_OP_TRLYAP; }
-bool valid_mode(int m) { return m >= 0 && m < SS_NUM_MODES; }
+bool valid_mode(int m) { return (m >= 0 && m < SS_NUM_MODES) || m == SS_MODE_DF; }
 bool valid_call_mode(int m) { return valid_mode(m) || m == SS_MODE_AUTO; }
 bool refined_or_fp64(int m)
 {
     return m == SS_MODE_FP64 || m == SS_MODE_FP32_REFINED || m == SS_MODE_TF32_REFINED ||
-           m == SS_MODE_BF16_REFINED;
+           m == SS_MODE_BF16_REFINED || m == SS_MODE_DF;
 }
 
 struct TableState {
     std::mutex mu;
-    int table[3][SS_NUM_MODES][NUM_BINS];
+    int table[3][kModeSlots][NUM_BINS];
     int auto_mode[3][NUM_BINS];
     int auto_cfg[3][NUM_BINS];
     TableState()
@@ -138,6 +146,7 @@ bool profile_pair(cudaEvent_t *a, cudaEvent_t *b)
 int config_count(int op, int mode)
 {
     if (mode == SS_MODE_FP64) return op == SS_OP_POTRF ? kNumFp64Potrf : kNumFp64Syl;
+    if (mode == SS_MODE_DF) return op == SS_OP_POTRF ? 0 : kNumDfSyl;
     return mixed_config_count(op, mode);
 }
 
@@ -145,6 +154,7 @@ const Config *config_get(int op, int mode, int cfg)
 {
     if (cfg < 0 || cfg >= config_count(op, mode)) return nullptr;
     if (mode == SS_MODE_FP64) return op == SS_OP_POTRF ? &kFp64Potrf[cfg] : &kFp64Syl[cfg];
+    if (mode == SS_MODE_DF) return &kDfSyl[cfg];
     return mixed_config_get(op, mode, cfg);
 }
 
@@ -158,6 +168,7 @@ const Config *config_get(int op, int mode, int cfg)
 //   with one update warp up to 64, then two (large batches) or four.
 int config_default(int op, int mode, int max_n, int batch)
 {
+    if (mode == SS_MODE_DF) return 1;                    // (16, 96, 4)
     if (mode != SS_MODE_FP64) return 0;
     if (op == SS_OP_POTRF) {
         if (max_n <= 16) return 5;                       // (16, 64, 1)
@@ -319,6 +330,10 @@ int run(int op, int batch, int max_n, const Operands &o, int mode, int cfg, void
         if (l.mode == SS_MODE_FP64) {
             if (op == SS_OP_POTRF) e = launch_potrf_fp64(o, s, l, gs);
             else e = launch_syl_fp64(o, s, l, gs, op == SS_OP_TRLYAP);
+        } else if (l.mode == SS_MODE_DF) {
+            const Config *c = config_get(op, SS_MODE_DF, l.cfg);
+            e = c ? launch_syl_ws(c->block, (c->threads - 32) / 32, op == SS_OP_TRLYAP, true, o, s, l, gs)
+                  : cudaErrorInvalidValue;
         } else {
             e = launch_mixed(op, o, s, l, gs);
         }
@@ -400,7 +415,7 @@ int trsyl_rect(int batch, int max_m, int max_n, const int *d_m, const int *d_n, 
         if (!d_ldx) return -13;
         if (!d_info) return -14;
     }
-    if (mode != SS_MODE_FP64) return -15;
+    if (mode != SS_MODE_FP64 && mode != SS_MODE_DF) return -15;
     Operands o{d_n, d_L, d_ldl, d_U, d_ldu, d_C, d_ldc, d_X, d_ldx, d_info, d_m};
     return run(SS_OP_TRSYL, batch, max_n, o, mode, cfg, d_work, work_bytes, stream, 15, 17, max_m);
 }

@@ -15,14 +15,12 @@
 //      |D|^2 / |D_prev| (or |D| itself) is below SS_REFINE_TOL * |X|.
 // The Lyapunov form is the Sylvester one with U = L^T over the lower blocks.
 //
-// Double-float values are unevaluated sums hi + lo of two floats (about 48
-// significant bits).  FP64 operands are split into hi (the leading 24 bits,
-// truncated) and lo (the rest, rounded) with integer operations only, so the
-// split does not use the FP64 pipe.
+// Double-float arithmetic (split, TwoProduct / TwoSum updates) is in df.cuh.
 #pragma once
 
 #include <cuda_bf16.h>
 
+#include "df.cuh"
 #include "ss_device.cuh"
 #include "ss_internal.h"
 
@@ -33,35 +31,6 @@ enum Prec { P_FP32 = 0, P_TF32 = 1, P_BF16 = 2 };
 enum Res { R_DF = 0, R_FP64 = 1 };
 
 constexpr int MAXIT = SS_REFINE_MAXIT;
-
-// ------------------------------------------------------------------ split
-
-__device__ __forceinline__ void split_df(double x, float &hi, float &lo)
-{
-    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-    const unsigned sgn = (unsigned)(u >> 32) & 0x80000000u;
-    const int e = (int)((u >> 52) & 0x7FF);
-    const int ef = e - 896;                       // e - 1023 + 127
-    if (ef >= 1 && ef <= 254) {
-        hi = __uint_as_float(sgn | ((unsigned)ef << 23) | (unsigned)((u >> 29) & 0x7FFFFFu));
-        const unsigned ml = (unsigned)(u & 0x1FFFFFFFu);
-        if (ml == 0u) { lo = 0.0f; return; }
-        const int lz = __clz(ml);                 // 3..31
-        const int el = e - 1075 + (31 - lz) + 127;
-        if (el >= 1) {
-            const unsigned mant = (unsigned)((((unsigned long long)ml) << (lz + 1)) >> 9) & 0x7FFFFFu;
-            lo = __uint_as_float(sgn | ((unsigned)el << 23) | mant);
-        } else {
-            lo = 0.0f;
-        }
-    } else if ((u << 1) == 0ull) {
-        hi = 0.0f;
-        lo = 0.0f;
-    } else {
-        hi = __double2float_rz(x);
-        lo = __double2float_rn(x - (double)hi);
-    }
-}
 
 // FP64 -> FP32 by truncating the significand, integer operations only (the
 // low-precision solve does not need round-to-nearest; values outside the FP32
@@ -77,21 +46,6 @@ __device__ __forceinline__ float d2f_trunc(double x)
     return __double2float_rz(x);
 }
 
-// FP32 -> FP64 exactly, integer operations only (subnormal, infinite and NaN
-// inputs take the hardware conversion).
-__device__ __forceinline__ double f2d_exact(float f)
-{
-    const unsigned v = __float_as_uint(f);
-    const unsigned e = (v >> 23) & 0xFFu;
-    if (e >= 1u && e <= 254u) {
-        const unsigned long long u = ((unsigned long long)(v & 0x80000000u) << 32) |
-                                     ((unsigned long long)(e + 896u) << 52) |
-                                     ((unsigned long long)(v & 0x7FFFFFu) << 29);
-        return __longlong_as_double((long long)u);
-    }
-    if ((v << 1) == 0u) return __longlong_as_double((long long)((unsigned long long)(v & 0x80000000u) << 32));
-    return (double)f;
-}
 
 template <typename Src>
 __device__ __forceinline__ float to_f(Src v) { return (float)v; }
@@ -114,19 +68,6 @@ __device__ __forceinline__ float2 cvt_elem<float2, double>(double v)
     return r;
 }
 
-// acc -= x * y in double-float (acc, x, y each hi + lo); the steps are never
-// contracted into FMAs, so the error-free transformations stay exact.
-__device__ __forceinline__ void df_msub(float &ah, float &al, float xh, float xl, float yh, float yl)
-{
-    const float p = __fmul_rn(xh, yh);
-    float pe = __fmaf_rn(xh, yh, -p);                      // p + pe = xh * yh exactly
-    pe = __fadd_rn(pe, __fmaf_rn(xh, yl, __fmul_rn(xl, yh)));
-    const float s = __fsub_rn(ah, p);                      // TwoSum(ah, -p)
-    const float bb = __fsub_rn(s, ah);
-    const float err = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bb)), __fsub_rn(-p, bb));
-    ah = s;
-    al = __fadd_rn(al, __fsub_rn(err, pe));
-}
 
 // ------------------------------------------------------------------ tiles
 

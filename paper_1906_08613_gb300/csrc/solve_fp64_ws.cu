@@ -26,6 +26,9 @@
 // warps wait once more after their last block), so the phases of a barrier
 // never overlap.  Barrier 1 synchronises the update warps' tile staging.
 // T and X of consecutive blocks alternate between two shared tiles.
+#include <type_traits>
+
+#include "df.cuh"
 #include "ss_internal.h"
 #include "ss_device.cuh"
 
@@ -44,6 +47,10 @@ __device__ __forceinline__ void named_arrive(int id, int count)
     __threadfence_block();
     asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
+
+// A double tile's memory as double-float pairs (same size per element).
+__device__ __forceinline__ float2 *df2(double *p) { return reinterpret_cast<float2 *>(p); }
+__device__ __forceinline__ const float2 *df2(const double *p) { return reinterpret_cast<const float2 *>(p); }
 
 // Largest |p_ii| over i < n (all threads of the CTA take part).
 __device__ __forceinline__ double max_abs_diag(const double *P, long ld, int n, double *s_red)
@@ -223,6 +230,23 @@ struct Prefetch {
             tB[r + c * LD] = b[q];
         }
     }
+    // The same tiles as double-float pairs (DF update warps); a float2 slot
+    // has the size of a double, so the tile layout is unchanged.
+    __device__ __forceinline__ void store_df(float2 *tA, float2 *tB, bool has_a, int ut) const
+    {
+        constexpr int LD = Tile<B>::LD;
+#pragma unroll
+        for (int q = 0; q < PE; ++q) {
+            const int e = ut + TU * q, r = e % B, c = e / B;
+            float2 v;
+            if (has_a) {
+                split_df(a[q], v.x, v.y);
+                tA[r + c * LD] = v;
+            }
+            split_df(b[q], v.x, v.y);
+            tB[r + c * LD] = v;
+        }
+    }
 };
 
 // acc -= A * op(Bm) over B terms, A(row, k) = A[row + k*LD],
@@ -275,6 +299,69 @@ __device__ __forceinline__ void upd_fma_rt(bool tb, double (&ae)[B * B / TU], do
 {
     if (tb) upd_fma<B, TU, true>(ae, ao, om, A, Bm);
     else    upd_fma<B, TU, false>(ae, ao, om, A, Bm);
+}
+
+// Double-float forms of the three products above: (ah, al) -= A op(Bm) with
+// A and Bm tiles of double-float pairs; one TwoProduct / TwoSum update per
+// term on the FP32 pipe.
+template <int B, int TU, bool TB>
+__device__ __forceinline__ void upd_df(float (&ah)[B * B / TU], float (&al)[B * B / TU], const OutMap<B, TU> &om,
+                                       const float2 *A, const float2 *Bm)
+{
+    constexpr int LD = Tile<B>::LD;
+    constexpr int E = B * B / TU;
+#pragma unroll 2
+    for (int k = 0; k < B; ++k) {
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            if (om.ok(r)) {
+                const float2 a = A[om.row[r] + k * LD];
+                const float2 b = TB ? Bm[om.col[r] + k * LD] : Bm[k + om.col[r] * LD];
+                df_msub(ah[r], al[r], a.x, a.y, b.x, b.y);
+            }
+        }
+    }
+}
+
+template <int B, int TU>
+__device__ __forceinline__ void upd_df_ta(float (&ah)[B * B / TU], float (&al)[B * B / TU], const OutMap<B, TU> &om,
+                                          const float2 *A, const float2 *Bm)
+{
+    constexpr int LD = Tile<B>::LD;
+    constexpr int E = B * B / TU;
+#pragma unroll 2
+    for (int k = 0; k < B; ++k) {
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            if (om.ok(r)) {
+                const float2 a = A[k + om.row[r] * LD];
+                const float2 b = Bm[k + om.col[r] * LD];
+                df_msub(ah[r], al[r], a.x, a.y, b.x, b.y);
+            }
+        }
+    }
+}
+
+template <int B, int TU>
+__device__ __forceinline__ void upd_df_rt(bool tb, float (&ah)[B * B / TU], float (&al)[B * B / TU],
+                                          const OutMap<B, TU> &om, const float2 *A, const float2 *Bm)
+{
+    if (tb) upd_df<B, TU, true>(ah, al, om, A, Bm);
+    else    upd_df<B, TU, false>(ah, al, om, A, Bm);
+}
+
+// All update threads: the B x B double tile S as double-float pairs into D.
+template <int B, int TU>
+__device__ __forceinline__ void tile_to_df(float2 *D, const double *S, int ut)
+{
+    constexpr int LD = Tile<B>::LD;
+#pragma unroll
+    for (int e = ut; e < B * B; e += TU) {
+        const int r = e % B, c = e / B;
+        float2 v;
+        split_df(S[r + c * LD], v.x, v.y);
+        D[r + c * LD] = v;
+    }
 }
 
 // Operands of bulk step s of block (I, J): s < P1 is K = s of the first sum,
@@ -340,7 +427,12 @@ constexpr size_t ws_smem_bytes() { return (size_t)ws_tiles<B>() * Tile<B>::SZ * 
 // One instance.  Shared tiles: sT[2] (T / X of consecutive blocks), sL, sU,
 // sR (diagonal warp), sA[2], sB[2] (update warps' staging).
 // X is m x n (L m x m, U n x n); Lyapunov has m = n.
-template <int B, int NU, bool LYAP>
+// DF: the update warps form T in double-float arithmetic on the FP32 pipe
+// (operands split on staging, T rounded to FP64 for the diagonal warp); the
+// diagonal warp, its divisions and X stay FP64.  In the last phase the X
+// block of block t-1 is first split into the free staging tile sA[nsteps & 1]
+// (the last step stages no A operand).
+template <int B, int NU, bool LYAP, bool DF>
 __device__ void syl_ws_instance(int m, int n, const double *L, long ldl, const double *U, long ldu,
                                 const double *C, long ldc, double *X, long ldx, int *info, double *sm)
 {
@@ -405,6 +497,7 @@ __device__ void syl_ws_instance(int m, int n, const double *L, long ldl, const d
         constexpr int E = B * B / TU;
         const int ut = threadIdx.x - 32;
         OutMap<B, TU> om;
+        using Acc = typename std::conditional<DF, float, double>::type;
         Prefetch<B, TU> pf;
         int t = 0;
         for (int I = 0; I < mb; ++I) {
@@ -414,15 +507,18 @@ __device__ void syl_ws_instance(int m, int n, const double *L, long ldl, const d
                 const int nJ = min(B, n - J * B), j0 = J * B;
                 if (LYAP && I == J) om.set_lower(mI, ut);   // symmetric diagonal block: i >= j only
                 else                om.set(mI, nJ, ut);
-                double ae[E], ao[E];
+                // FP64: even / odd terms; DF: hi / lo of one double-float sum.
+                Acc ae[E], ao[E];
 #pragma unroll
                 for (int r = 0; r < E; ++r) {
-                    ao[r] = 0.0;
-                    ae[r] = 0.0;
+                    ao[r] = 0;
+                    ae[r] = 0;
                     if (om.ok(r)) {
                         int rr = om.row[r], cc = om.col[r];
                         if (LYAP && I == J && rr < cc) { const int x = rr; rr = cc; cc = x; }
-                        ae[r] = C[(i0 + rr) + (long)(j0 + cc) * ldc];
+                        const double c = C[(i0 + rr) + (long)(j0 + cc) * ldc];
+                        if constexpr (DF) split_df(c, ae[r], ao[r]);
+                        else ae[r] = c;
                     }
                 }
                 // Bulk steps, then (J > 0) the staged operand of the last phase.
@@ -442,7 +538,8 @@ __device__ void syl_ws_instance(int m, int n, const double *L, long ldl, const d
                     if (nsteps > 0) step_src<B, LYAP>(0, P1, I, J, mI, nJ, L, ldl, U, ldu, X, ldx, sa, sb, tb_next);
                     else last_src_t<B, LYAP>(I, J, mI, nJ, L, ldl, U, ldu, sb, tb_next);
                     pf.load(sa, sb, nsteps > 0, ut);
-                    pf.store(sA0, sB0, nsteps > 0, ut);
+                    if constexpr (DF) pf.store_df(df2(sA0), df2(sB0), nsteps > 0, ut);
+                    else pf.store(sA0, sB0, nsteps > 0, ut);
                     named_sync(kBarUpd, TU);
                 }
                 for (int s = 0; s < nsteps; ++s) {
@@ -455,8 +552,13 @@ __device__ void syl_ws_instance(int m, int n, const double *L, long ldl, const d
                         else last_src_t<B, LYAP>(I, J, mI, nJ, L, ldl, U, ldu, sb, tb_next);
                         pf.load(sa, sb, next_bulk, ut);
                     }
-                    upd_fma_rt<B, TU>(tb, ae, ao, om, sA0 + buf * SZ, sB0 + buf * SZ);
-                    if (more) pf.store(sA0 + (buf ^ 1) * SZ, sB0 + (buf ^ 1) * SZ, next_bulk, ut);
+                    if constexpr (DF) {
+                        upd_df_rt<B, TU>(tb, ae, ao, om, df2(sA0 + buf * SZ), df2(sB0 + buf * SZ));
+                        if (more) pf.store_df(df2(sA0 + (buf ^ 1) * SZ), df2(sB0 + (buf ^ 1) * SZ), next_bulk, ut);
+                    } else {
+                        upd_fma_rt<B, TU>(tb, ae, ao, om, sA0 + buf * SZ, sB0 + buf * SZ);
+                        if (more) pf.store(sA0 + (buf ^ 1) * SZ, sB0 + (buf ^ 1) * SZ, next_bulk, ut);
+                    }
                     named_sync(kBarUpd, TU);
                 }
                 if (t > 0) named_sync(kBarX, TALL);        // X of block t-1 is final
@@ -465,7 +567,18 @@ __device__ void syl_ws_instance(int m, int n, const double *L, long ldl, const d
                     // memory (for a Lyapunov diagonal block: all of it).
                     const double *sXp = sT0 + ((t - 1) & 1) * SZ;
                     const double *sV = sB0 + (nsteps & 1) * SZ;
-                    if (J > 0) {
+                    if constexpr (DF) {
+                        float2 *dX = df2(sA0 + (nsteps & 1) * SZ);
+                        tile_to_df<B, TU>(dX, sXp, ut);
+                        named_sync(kBarUpd, TU);
+                        const float2 *dV = df2(sV);
+                        if (J > 0) {
+                            upd_df_rt<B, TU>(tb_next, ae, ao, om, dX, dV);
+                            if (ldiag) upd_df<B, TU, true>(ae, ao, om, dV, dX);
+                        } else {
+                            upd_df<B, TU, false>(ae, ao, om, dV, dX);
+                        }
+                    } else if (J > 0) {
                         upd_fma_rt<B, TU>(tb_next, ae, ao, om, sXp, sV);      // X_{I,J-1} U_{J-1,J}
                         if (ldiag) upd_fma<B, TU, true>(ae, ao, om, sV, sXp); // L_{I,I-1} X_{I,I-1}^T
                     } else {
@@ -474,8 +587,12 @@ __device__ void syl_ws_instance(int m, int n, const double *L, long ldl, const d
                 }
                 double *sT = sT0 + (t & 1) * SZ;
 #pragma unroll
-                for (int r = 0; r < E; ++r)
-                    if (om.ok(r)) sT[om.row[r] + om.col[r] * LD] = ae[r] + ao[r];
+                for (int r = 0; r < E; ++r) {
+                    if (om.ok(r)) {
+                        if constexpr (DF) sT[om.row[r] + om.col[r] * LD] = df_to_double(ae[r], ao[r]);
+                        else sT[om.row[r] + om.col[r] * LD] = ae[r] + ao[r];
+                    }
+                }
                 named_sync(kBarUpd, TU);                   // staging tiles free again
                 named_arrive(kBarT, TALL);                 // T of block t is in sT
             }
@@ -669,7 +786,7 @@ __device__ __forceinline__ bool next_instance(const Sched &s, int group, int *s_
 
 // MINB: CTAs per SM the register allocation must allow (the two roles share
 // one register budget, set by the larger of them).
-template <int B, int NU, bool LYAP, int MINB>
+template <int B, int NU, bool LYAP, int MINB, bool DF>
 __global__ void __launch_bounds__(32 * NU + 32, MINB) syl_ws_kernel(Operands o, Sched s, int group)
 {
     extern __shared__ double sm[];
@@ -679,7 +796,7 @@ __global__ void __launch_bounds__(32 * NU + 32, MINB) syl_ws_kernel(Operands o, 
     while (next_instance(s, group, &s_slot, b)) {
         const int n = o.n[b], m = o.m != nullptr ? o.m[b] : n;
         if (n == 0 || m == 0) { if (threadIdx.x == 0) o.info[b] = 0; continue; }
-        syl_ws_instance<B, NU, LYAP>(m, n, o.A[b], o.lda[b], LYAP ? nullptr : o.U[b], LYAP ? 0 : o.ldu[b],
+        syl_ws_instance<B, NU, LYAP, DF>(m, n, o.A[b], o.lda[b], LYAP ? nullptr : o.U[b], LYAP ? 0 : o.ldu[b],
                                      o.C[b], o.ldc[b], o.X[b], o.ldx[b], o.info + b, sm);
     }
 }
@@ -731,20 +848,22 @@ cudaError_t launch_potrf_fp64_ws(int block, int nu, const Operands &o, const Sch
     return cudaErrorInvalidValue;
 }
 
-// Warp-specialised configurations: block B, NU update warps (+1 diagonal warp).
-cudaError_t launch_syl_fp64_ws(int block, int nu, bool lyap, const Operands &o, const Sched &s, const Launch &l,
-                               cudaStream_t st)
+// Warp-specialised configurations: block B, NU update warps (+1 diagonal warp);
+// df: double-float update warps.
+cudaError_t launch_syl_ws(int block, int nu, bool lyap, bool df, const Operands &o, const Sched &s, const Launch &l,
+                          cudaStream_t st)
 {
+#define WS_ONE(BB, NN, MB, LY, D)                                                                          \
+    launch_ws(syl_ws_kernel<BB, NN, LY, MB, D>, 32 * NN + 32, ws_smem_bytes<BB>(), l.batch, st, o, s, l.group)
 #define WS_CASE(BB, NN, MB)                                                                                \
     if (block == BB && nu == NN)                                                                           \
-        return lyap ? launch_ws(syl_ws_kernel<BB, NN, true, MB>, 32 * NN + 32, ws_smem_bytes<BB>(), l.batch, \
-                                st, o, s, l.group)                                                         \
-                    : launch_ws(syl_ws_kernel<BB, NN, false, MB>, 32 * NN + 32, ws_smem_bytes<BB>(), l.batch, \
-                                st, o, s, l.group);
+        return df ? (lyap ? WS_ONE(BB, NN, MB, true, true) : WS_ONE(BB, NN, MB, false, true))              \
+                  : (lyap ? WS_ONE(BB, NN, MB, true, false) : WS_ONE(BB, NN, MB, false, false));
     WS_CASE(16, 4, 6)
     WS_CASE(16, 2, 8)
     WS_CASE(16, 1, 8)
 #undef WS_CASE
+#undef WS_ONE
     return cudaErrorInvalidValue;
 }
 

@@ -85,10 +85,11 @@ cudaError_t launch_potrf(const Operands &o, const Sched &s, const Launch &l, cud
 cudaError_t launch_trsyl(const Operands &o, const Sched &s, const Launch &l, cudaStream_t st);
 cudaError_t launch_trlyap(const Operands &o, const Sched &s, const Launch &l, cudaStream_t st);
 
-// FP64 Sylvester / Lyapunov with warp-specialised CTAs (block B, nu update
-// warps plus one diagonal warp).
-cudaError_t launch_syl_fp64_ws(int block, int nu, bool lyap, const Operands &o, const Sched &s, const Launch &l,
-                               cudaStream_t st);
+// Sylvester / Lyapunov with warp-specialised CTAs (block B, nu update warps
+// plus one diagonal warp); df: the update warps compute in double-float on the
+// FP32 pipe (SS_MODE_DF), otherwise in FP64.
+cudaError_t launch_syl_ws(int block, int nu, bool lyap, bool df, const Operands &o, const Sched &s, const Launch &l,
+                          cudaStream_t st);
 
 // FP64 Cholesky with warp-specialised CTAs (block B, nu update warps plus one
 // diagonal warp).

@@ -29,8 +29,9 @@ MODE_BF16_REFINED = 3
 MODE_FP32_RAW = 4
 MODE_TF32_RAW = 5
 MODE_BF16_RAW = 6
+MODE_DF = 8
 MODES = {"fp64": 0, "fp32_refined": 1, "tf32_refined": 2, "bf16_refined": 3,
-         "fp32_raw": 4, "tf32_raw": 5, "bf16_raw": 6}
+         "fp32_raw": 4, "tf32_raw": 5, "bf16_raw": 6, "df": MODE_DF}
 
 MODE_AUTO = 7
 REFINED_MODES = (MODE_FP32_REFINED, MODE_TF32_REFINED, MODE_BF16_REFINED)

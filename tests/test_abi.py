@@ -107,6 +107,29 @@ def test_posv_argument_errors_before_launch(lib):
     assert ss.posv_upper(0, 0, 0, *([0] * 11)) == 0
 
 
+def test_df_mode_host_side(lib):
+    import re
+    text = open(HEADER).read()
+    assert int(re.search(r"#define SS_MODE_DF\s+(\d+)", text).group(1)) == ss.MODE_DF
+    assert ss.MODES["df"] == ss.MODE_DF
+    for op in (ss.OP_TRSYL, ss.OP_TRLYAP):
+        cnt = ss.ss_config_count(op, ss.MODE_DF)
+        assert cnt == 3
+        assert all(ss.ss_config_describe(op, ss.MODE_DF, c)[2] == 4 for c in range(cnt))
+        # No scratch beyond FP64's.
+        assert ss.ss_workspace_size(op, 1000, 128, ss.MODE_DF) == ss.ss_workspace_size(op, 1000, 128, ss.MODE_FP64)
+    assert ss.ss_config_count(ss.OP_POTRF, ss.MODE_DF) == 0
+    # Cholesky and the SPD solve have no DF form: rejected before any launch.
+    assert ss.potrf_upper(1, 4, 1, 1, 1, 1, 1, 1, mode=ss.MODE_DF, check=False) == -9
+    assert ss.posv_upper(1, 4, 4, *([1] * 11), mode=ss.MODE_DF, check=False) == -15
+    ss.ss_set_auto_table(ss.OP_TRSYL, [ss.MODE_DF, ss.MODE_FP64], [2, 0])
+    ss.ss_set_auto_table(ss.OP_TRSYL, [], [])
+    with pytest.raises(ss.SmallSolveError):
+        ss.ss_set_auto_table(ss.OP_POTRF, [ss.MODE_DF], [0])
+    with pytest.raises(ss.SmallSolveError):
+        ss.ss_set_config_table(ss.OP_TRLYAP, ss.MODE_DF, [3])
+
+
 def test_config_table_validation(lib):
     with pytest.raises(ss.SmallSolveError):
         ss.ss_set_config_table(ss.OP_TRSYL, ss.MODE_FP64, [999])
