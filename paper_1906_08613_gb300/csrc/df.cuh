@@ -78,4 +78,47 @@ __device__ __forceinline__ void df_msub(float &ah, float &al, float xh, float xl
 // hi + lo rounded to FP64 (one FP64 addition).
 __device__ __forceinline__ double df_to_double(float hi, float lo) { return f2d_exact(hi) + f2d_exact(lo); }
 
+// a += b (TwoSum of the high parts, low parts added).
+__device__ __forceinline__ void df_add(float &ah, float &al, float bh, float bl)
+{
+    const float s = __fadd_rn(ah, bh);
+    const float bb = __fsub_rn(s, ah);
+    const float err = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+    ah = s;
+    al = __fadd_rn(al, __fadd_rn(bl, err));
+}
+
+// (h, l) -> the same sum with |l| <= ulp(h) / 2 (TwoSum of h and l).
+__device__ __forceinline__ void df_norm(float &h, float &l)
+{
+    const float s = __fadd_rn(h, l);
+    const float bb = __fsub_rn(s, h);
+    l = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(l, bb));
+    h = s;
+}
+
+// x = v * r for normalised v and r: TwoProduct of the high parts plus the two
+// cross terms, then Fast2Sum (|p| >= |e|) to normalise.
+__device__ __forceinline__ void df_mul(float vh, float vl, float rh, float rl, float &xh, float &xl)
+{
+    const float p = __fmul_rn(vh, rh);
+    float e = __fmaf_rn(vh, rh, -p);
+    e = __fmaf_rn(vh, rl, e);
+    e = __fmaf_rn(vl, rh, e);
+    const float s = __fadd_rn(p, e);
+    xl = __fsub_rn(e, __fsub_rn(s, p));
+    xh = s;
+}
+
+// Sum of (h, l) over the `split` consecutive lanes of a group (split a power
+// of two dividing 32); every lane of the group gets the sum.
+__device__ __forceinline__ void df_group_sum(float &h, float &l, int split)
+{
+    for (int o = split >> 1; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, h, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, l, o);
+        df_add(h, l, h2, l2);
+    }
+}
+
 }  // namespace ss

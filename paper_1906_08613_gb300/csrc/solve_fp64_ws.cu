@@ -130,6 +130,61 @@ __device__ void warp_diag_solve(const double *sL, const double *sU, double *sT, 
     }
 }
 
+// Double-float form of warp_diag_solve for the DF pipeline: T and X in sT,
+// the strict lower triangle of Lt and the strict upper triangle of Ut in one
+// tile sLU, reciprocal divisors in sR, all as (hi, lo) float pairs with
+// leading dimension LDT.  The lane that finishes entry (i, j) starts its sum at
+// t_ij; x_ij = (t_ij - sum) * r_ij is a normalised double-float product.  Only
+// the FP32 pipe is used.
+template <int B, int LDT, bool SYM>
+__device__ void warp_diag_solve_df(const float2 *sLU, float2 *sT, const float2 *sR, int m, int nn, int lane)
+{
+    for (int d = 0; d <= m + nn - 2; ++d) {
+        const int ilo = SYM ? max((d + 1) / 2, d - nn + 1) : max(0, d - nn + 1), ihi = min(d, m - 1);
+        const int cnt = ihi - ilo + 1;
+        int split = cnt >= 32 ? 1 : pow2_floor(32 / cnt);
+        const int byLen = pow2_floor(d > 1 ? d : 1);
+        split = split < byLen ? split : byLen;
+        const int idx = lane / split, part = lane % split;
+        const bool act = idx < cnt;
+        const int i = ilo + (act ? idx : 0), j = d - i;
+        float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+        if (act) {
+            if (part == 0) {
+                const float2 tv = sT[i + j * LDT];
+                h0 = tv.x;
+                l0 = tv.y;
+            }
+            int t = part;
+            for (; t + split < d; t += 2 * split) {
+                const int t1 = t + split;
+                const float2 a0 = t < i ? sLU[i + t * LDT] : sT[i + (t - i) * LDT];
+                const float2 b0 = t < i ? (SYM && t < j ? sT[j + t * LDT] : sT[t + j * LDT]) : sLU[(t - i) + j * LDT];
+                const float2 a1 = t1 < i ? sLU[i + t1 * LDT] : sT[i + (t1 - i) * LDT];
+                const float2 b1 = t1 < i ? (SYM && t1 < j ? sT[j + t1 * LDT] : sT[t1 + j * LDT])
+                                         : sLU[(t1 - i) + j * LDT];
+                df_msub(h0, l0, a0.x, a0.y, b0.x, b0.y);
+                df_msub(h1, l1, a1.x, a1.y, b1.x, b1.y);
+            }
+            if (t < d) {
+                const float2 a0 = t < i ? sLU[i + t * LDT] : sT[i + (t - i) * LDT];
+                const float2 b0 = t < i ? (SYM && t < j ? sT[j + t * LDT] : sT[t + j * LDT]) : sLU[(t - i) + j * LDT];
+                df_msub(h0, l0, a0.x, a0.y, b0.x, b0.y);
+            }
+        }
+        df_add(h0, l0, h1, l1);
+        df_group_sum(h0, l0, split);
+        if (act && part == 0) {
+            df_norm(h0, l0);
+            const float2 r = sR[i + j * LDT];
+            float2 x;
+            df_mul(h0, l0, r.x, r.y, x.x, x.y);
+            sT[i + j * LDT] = x;
+        }
+        __syncwarp();
+    }
+}
+
 // ------------------------------------------------------------- update warps
 
 // Outputs of one update thread: flat index e = ut + TU*r over the m x nn
@@ -230,11 +285,12 @@ struct Prefetch {
             tB[r + c * LD] = b[q];
         }
     }
-    // The same tiles as double-float pairs (DF update warps); a float2 slot
-    // has the size of a double, so the tile layout is unchanged.
+    // The same tiles as double-float pairs (DF update warps), leading
+    // dimension LDT.
+    template <int LDT>
     __device__ __forceinline__ void store_df(float2 *tA, float2 *tB, bool has_a, int ut) const
     {
-        constexpr int LD = Tile<B>::LD;
+        constexpr int LD = LDT;
 #pragma unroll
         for (int q = 0; q < PE; ++q) {
             const int e = ut + TU * q, r = e % B, c = e / B;
@@ -302,66 +358,32 @@ __device__ __forceinline__ void upd_fma_rt(bool tb, double (&ae)[B * B / TU], do
 }
 
 // Double-float forms of the three products above: (ah, al) -= A op(Bm) with
-// A and Bm tiles of double-float pairs; one TwoProduct / TwoSum update per
-// term on the FP32 pipe.
-template <int B, int TU, bool TB>
+// A and Bm tiles of double-float pairs (leading dimension LDT); one
+// TwoProduct / TwoSum update per term on the FP32 pipe.
+template <int B, int TU, int LDT, bool TB>
 __device__ __forceinline__ void upd_df(float (&ah)[B * B / TU], float (&al)[B * B / TU], const OutMap<B, TU> &om,
                                        const float2 *A, const float2 *Bm)
 {
-    constexpr int LD = Tile<B>::LD;
     constexpr int E = B * B / TU;
 #pragma unroll 2
     for (int k = 0; k < B; ++k) {
 #pragma unroll
         for (int r = 0; r < E; ++r) {
             if (om.ok(r)) {
-                const float2 a = A[om.row[r] + k * LD];
-                const float2 b = TB ? Bm[om.col[r] + k * LD] : Bm[k + om.col[r] * LD];
+                const float2 a = A[om.row[r] + k * LDT];
+                const float2 b = TB ? Bm[om.col[r] + k * LDT] : Bm[k + om.col[r] * LDT];
                 df_msub(ah[r], al[r], a.x, a.y, b.x, b.y);
             }
         }
     }
 }
 
-template <int B, int TU>
-__device__ __forceinline__ void upd_df_ta(float (&ah)[B * B / TU], float (&al)[B * B / TU], const OutMap<B, TU> &om,
-                                          const float2 *A, const float2 *Bm)
-{
-    constexpr int LD = Tile<B>::LD;
-    constexpr int E = B * B / TU;
-#pragma unroll 2
-    for (int k = 0; k < B; ++k) {
-#pragma unroll
-        for (int r = 0; r < E; ++r) {
-            if (om.ok(r)) {
-                const float2 a = A[k + om.row[r] * LD];
-                const float2 b = Bm[k + om.col[r] * LD];
-                df_msub(ah[r], al[r], a.x, a.y, b.x, b.y);
-            }
-        }
-    }
-}
-
-template <int B, int TU>
+template <int B, int TU, int LDT>
 __device__ __forceinline__ void upd_df_rt(bool tb, float (&ah)[B * B / TU], float (&al)[B * B / TU],
                                           const OutMap<B, TU> &om, const float2 *A, const float2 *Bm)
 {
-    if (tb) upd_df<B, TU, true>(ah, al, om, A, Bm);
-    else    upd_df<B, TU, false>(ah, al, om, A, Bm);
-}
-
-// All update threads: the B x B double tile S as double-float pairs into D.
-template <int B, int TU>
-__device__ __forceinline__ void tile_to_df(float2 *D, const double *S, int ut)
-{
-    constexpr int LD = Tile<B>::LD;
-#pragma unroll
-    for (int e = ut; e < B * B; e += TU) {
-        const int r = e % B, c = e / B;
-        float2 v;
-        split_df(S[r + c * LD], v.x, v.y);
-        D[r + c * LD] = v;
-    }
+    if (tb) upd_df<B, TU, LDT, true>(ah, al, om, A, Bm);
+    else    upd_df<B, TU, LDT, false>(ah, al, om, A, Bm);
 }
 
 // Operands of bulk step s of block (I, J): s < P1 is K = s of the first sum,
@@ -419,31 +441,50 @@ __device__ __forceinline__ void last_src_t(int I, int J, int mI, int nJ, const d
     tb = LYAP;
 }
 
-template <int B>
-constexpr int ws_tiles() { return 9; }
-template <int B>
-constexpr size_t ws_smem_bytes() { return (size_t)ws_tiles<B>() * Tile<B>::SZ * sizeof(double) + 32 * sizeof(double); }
+// Shared tiles of the warp-specialised kernels: FP64 uses nine tiles of
+// Tile<B>; DF uses ten tiles of B x (B + 2) double-float pairs (an even
+// leading dimension of 8-byte elements puts the entries of an anti-diagonal,
+// which the wavefront reads together, in distinct banks).
+template <int B, bool DF>
+struct WsTile {
+    static constexpr int LD = DF ? B + 2 : Tile<B>::LD;
+    static constexpr int SZ = B * LD;
+    static constexpr int N = DF ? 10 : 9;
+};
+template <int B, bool DF = false>
+constexpr size_t ws_smem_bytes() { return (size_t)WsTile<B, DF>::N * WsTile<B, DF>::SZ * sizeof(double) + 32 * sizeof(double); }
 
-// One instance.  Shared tiles: sT[2] (T / X of consecutive blocks), sL, sU,
-// sR (diagonal warp), sA[2], sB[2] (update warps' staging).
-// X is m x n (L m x m, U n x n); Lyapunov has m = n.
+// One instance.  X is m x n (L m x m, U n x n); Lyapunov has m = n.
+// FP64 shared tiles: sT[2] (T / X of consecutive blocks), sL, sU, sR
+// (diagonal warp), sA[2], sB[2] (update warps' staging).
 // DF: the update warps form T in double-float arithmetic on the FP32 pipe
-// (operands split on staging, T rounded to FP64 for the diagonal warp); the
-// diagonal warp, its divisions and X stay FP64.  In the last phase the X
-// block of block t-1 is first split into the free staging tile sA[nsteps & 1]
-// (the last step stages no A operand).
+// (operands split on staging) and, for each block, also prepare the diagonal
+// warp's operands in double-buffered tiles: sLU[t & 1] (strict lower L_II,
+// strict upper U_JJ or L_JJ^T) and sR[t & 1] (1 / (l_ii + u_jj), divided in
+// FP64, then split).  The diagonal warp then solves on the FP32 pipe only
+// (warp_diag_solve_df) and writes X rounded to FP64.  sT holds T and X as
+// double-float pairs, so the update warps' last phase reads X of block t-1
+// without conversion.  Buffer t & 1 is free when block t starts: the diagonal
+// warp last read it for block t-2, before the "X ready" arrival the update
+// warps waited for in block t-1.
 template <int B, int NU, bool LYAP, bool DF>
 __device__ void syl_ws_instance(int m, int n, const double *L, long ldl, const double *U, long ldu,
                                 const double *C, long ldc, double *X, long ldx, int *info, double *sm)
 {
-    constexpr int LD = Tile<B>::LD, SZ = Tile<B>::SZ;
+    constexpr int LD = WsTile<B, DF>::LD, SZ = WsTile<B, DF>::SZ;
     constexpr int TU = 32 * NU, TALL = TU + 32;
     static_assert((B * B) % TU == 0, "update threads must divide the block");
     double *sT0 = sm, *sL = sm + 2 * SZ, *sU = sm + 3 * SZ, *sR = sm + 4 * SZ;
     double *sA0 = sm + 5 * SZ, *sB0 = sm + 7 * SZ;
-    double *s_red = sm + 9 * SZ;
+    if constexpr (DF) {
+        sA0 = sm + 6 * SZ;
+        sB0 = sm + 8 * SZ;
+    }
+    double *s_red = sm + WsTile<B, DF>::N * SZ;
+    int *s_bad = reinterpret_cast<int *>(s_red + 24);     // DF: a divisor check failed
     const int mb = (m + B - 1) / B, nb = (n + B - 1) / B;
 
+    if (DF && threadIdx.x == 0) *s_bad = 0;
     double md = max_abs_diag(L, ldl, m, s_red);
     if (!LYAP) md = fmax(md, max_abs_diag(U, ldu, n, s_red));
     const double delta = divisor_delta(max(m, n), md);
@@ -454,42 +495,67 @@ __device__ void syl_ws_instance(int m, int n, const double *L, long ldl, const d
         int bad = 0, t = 0;
         for (int I = 0; I < mb; ++I) {
             const int mI = min(B, m - I * B), i0 = I * B;
-            warp_stage_tri<B>(sL, L + i0 + (long)i0 * ldl, ldl, mI, true, lane);
+            if constexpr (!DF) warp_stage_tri<B>(sL, L + i0 + (long)i0 * ldl, ldl, mI, true, lane);
             const int jend = LYAP ? I + 1 : nb;
             for (int J = 0; J < jend; ++J, ++t) {
                 const int nJ = min(B, n - J * B), j0 = J * B;
-                if (!LYAP) warp_stage_tri<B>(sU, U + j0 + (long)j0 * ldu, ldu, nJ, false, lane);
-                else       warp_stage_tri<B>(sU, L + j0 + (long)j0 * ldl, ldl, nJ, true, lane);
-                __syncwarp();
                 const bool sym = LYAP && I == J;
-                for (int e = lane; e < mI * nJ; e += 32) {
-                    const int i = e % mI, j = e / mI;
-                    if (sym && i < j) continue;
-                    const double dd = sL[i + i * LD] + sU[j + j * LD];
-                    if (!(fabs(dd) > delta)) bad = 1;
-                    sR[i + j * LD] = 1.0 / dd;
-                }
-                __syncwarp();
                 double *sT = sT0 + (t & 1) * SZ;
-                named_sync(kBarT, TALL);                   // T of block t is in sT
-                if (sym) {
-                    warp_diag_solve<B, LYAP, true>(sL, sU, sT, sR, mI, nJ, lane);
-                    // Mirror: the block after X_00 reads it whole from here.
-                    for (int e = lane; e < mI * mI; e += 32) {
+                if constexpr (DF) {
+                    named_sync(kBarT, TALL);               // T and the diagonal operands of block t
+                    float2 *dT = df2(sT);
+                    const float2 *dLU = df2(sL + (t & 1) * SZ), *dR = df2(sR + (t & 1) * SZ);
+                    if (sym) {
+                        warp_diag_solve_df<B, LD, true>(dLU, dT, dR, mI, nJ, lane);
+                        for (int e = lane; e < mI * mI; e += 32) {
+                            const int i = e % mI, j = e / mI;
+                            if (i < j) dT[i + j * LD] = dT[j + i * LD];
+                        }
+                        __syncwarp();
+                    } else {
+                        warp_diag_solve_df<B, LD, false>(dLU, dT, dR, mI, nJ, lane);
+                    }
+                    for (int e = lane; e < mI * nJ; e += 32) {
+                        const int r = e % mI, c = e / mI;
+                        if (!LYAP || I != J || r >= c) {
+                            const float2 v = dT[r + c * LD];
+                            X[(i0 + r) + (long)(j0 + c) * ldx] = df_to_double(v.x, v.y);
+                        }
+                    }
+                } else {
+                    if (!LYAP) warp_stage_tri<B>(sU, U + j0 + (long)j0 * ldu, ldu, nJ, false, lane);
+                    else       warp_stage_tri<B>(sU, L + j0 + (long)j0 * ldl, ldl, nJ, true, lane);
+                    __syncwarp();
+                    for (int e = lane; e < mI * nJ; e += 32) {
                         const int i = e % mI, j = e / mI;
-                        if (i < j) sT[i + j * LD] = sT[j + i * LD];
+                        if (sym && i < j) continue;
+                        const double dd = sL[i + i * LD] + sU[j + j * LD];
+                        if (!(fabs(dd) > delta)) bad = 1;
+                        sR[i + j * LD] = 1.0 / dd;
                     }
                     __syncwarp();
-                } else {
-                    warp_diag_solve<B, LYAP, false>(sL, sU, sT, sR, mI, nJ, lane);
-                }
-                for (int e = lane; e < mI * nJ; e += 32) {
-                    const int r = e % mI, c = e / mI;
-                    if (!LYAP || I != J || r >= c) X[(i0 + r) + (long)(j0 + c) * ldx] = sT[r + c * LD];
+                    named_sync(kBarT, TALL);               // T of block t is in sT
+                    if (sym) {
+                        warp_diag_solve<B, LYAP, true>(sL, sU, sT, sR, mI, nJ, lane);
+                        // Mirror: the block after X_00 reads it whole from here.
+                        for (int e = lane; e < mI * mI; e += 32) {
+                            const int i = e % mI, j = e / mI;
+                            if (i < j) sT[i + j * LD] = sT[j + i * LD];
+                        }
+                        __syncwarp();
+                    } else {
+                        warp_diag_solve<B, LYAP, false>(sL, sU, sT, sR, mI, nJ, lane);
+                    }
+                    for (int e = lane; e < mI * nJ; e += 32) {
+                        const int r = e % mI, c = e / mI;
+                        if (!LYAP || I != J || r >= c) X[(i0 + r) + (long)(j0 + c) * ldx] = sT[r + c * LD];
+                    }
                 }
                 named_arrive(kBarX, TALL);                 // X of block t is final
             }
         }
+        // DF: the update warps set s_bad before their last "T ready" arrival.
+        if (DF) bad = *s_bad;
         bad = __any_sync(0xffffffffu, bad);
         if (lane == 0) *info = bad ? 1 : 0;
     } else {
@@ -507,6 +573,31 @@ __device__ void syl_ws_instance(int m, int n, const double *L, long ldl, const d
                 const int nJ = min(B, n - J * B), j0 = J * B;
                 if (LYAP && I == J) om.set_lower(mI, ut);   // symmetric diagonal block: i >= j only
                 else                om.set(mI, nJ, ut);
+                if constexpr (DF) {
+                    // The diagonal warp's operands of block t (see above).
+                    float2 *pLU = df2(sL + (t & 1) * SZ), *pR = df2(sR + (t & 1) * SZ);
+                    const bool sym = LYAP && I == J;
+                    int bad = 0;
+                    for (int e = ut; e < B * B; e += TU) {
+                        const int r = e % B, c = e / B;
+                        float2 v = make_float2(0.f, 0.f), w = make_float2(0.f, 0.f);
+                        if (r > c && r < mI) {
+                            split_df(L[(i0 + r) + (long)(i0 + c) * ldl], v.x, v.y);
+                        } else if (r < c && c < nJ) {
+                            const double u = LYAP ? L[(j0 + c) + (long)(j0 + r) * ldl] : U[(j0 + r) + (long)(j0 + c) * ldu];
+                            split_df(u, v.x, v.y);
+                        }
+                        if (r < mI && c < nJ && !(sym && r < c)) {
+                            const double dd = L[(i0 + r) + (long)(i0 + r) * ldl] +
+                                              (LYAP ? L[(j0 + c) + (long)(j0 + c) * ldl] : U[(j0 + c) + (long)(j0 + c) * ldu]);
+                            if (!(fabs(dd) > delta)) bad = 1;
+                            split_df(1.0 / dd, w.x, w.y);
+                        }
+                        pLU[r + c * LD] = v;
+                        pR[r + c * LD] = w;
+                    }
+                    if (bad) *s_bad = 1;
+                }
                 // FP64: even / odd terms; DF: hi / lo of one double-float sum.
                 Acc ae[E], ao[E];
 #pragma unroll
@@ -538,7 +629,7 @@ __device__ void syl_ws_instance(int m, int n, const double *L, long ldl, const d
                     if (nsteps > 0) step_src<B, LYAP>(0, P1, I, J, mI, nJ, L, ldl, U, ldu, X, ldx, sa, sb, tb_next);
                     else last_src_t<B, LYAP>(I, J, mI, nJ, L, ldl, U, ldu, sb, tb_next);
                     pf.load(sa, sb, nsteps > 0, ut);
-                    if constexpr (DF) pf.store_df(df2(sA0), df2(sB0), nsteps > 0, ut);
+                    if constexpr (DF) pf.template store_df<LD>(df2(sA0), df2(sB0), nsteps > 0, ut);
                     else pf.store(sA0, sB0, nsteps > 0, ut);
                     named_sync(kBarUpd, TU);
                 }
@@ -553,8 +644,9 @@ __device__ void syl_ws_instance(int m, int n, const double *L, long ldl, const d
                         pf.load(sa, sb, next_bulk, ut);
                     }
                     if constexpr (DF) {
-                        upd_df_rt<B, TU>(tb, ae, ao, om, df2(sA0 + buf * SZ), df2(sB0 + buf * SZ));
-                        if (more) pf.store_df(df2(sA0 + (buf ^ 1) * SZ), df2(sB0 + (buf ^ 1) * SZ), next_bulk, ut);
+                        upd_df_rt<B, TU, LD>(tb, ae, ao, om, df2(sA0 + buf * SZ), df2(sB0 + buf * SZ));
+                        if (more)
+                            pf.template store_df<LD>(df2(sA0 + (buf ^ 1) * SZ), df2(sB0 + (buf ^ 1) * SZ), next_bulk, ut);
                     } else {
                         upd_fma_rt<B, TU>(tb, ae, ao, om, sA0 + buf * SZ, sB0 + buf * SZ);
                         if (more) pf.store(sA0 + (buf ^ 1) * SZ, sB0 + (buf ^ 1) * SZ, next_bulk, ut);
@@ -568,15 +660,12 @@ __device__ void syl_ws_instance(int m, int n, const double *L, long ldl, const d
                     const double *sXp = sT0 + ((t - 1) & 1) * SZ;
                     const double *sV = sB0 + (nsteps & 1) * SZ;
                     if constexpr (DF) {
-                        float2 *dX = df2(sA0 + (nsteps & 1) * SZ);
-                        tile_to_df<B, TU>(dX, sXp, ut);
-                        named_sync(kBarUpd, TU);
-                        const float2 *dV = df2(sV);
+                        const float2 *dX = df2(sXp), *dV = df2(sV);
                         if (J > 0) {
-                            upd_df_rt<B, TU>(tb_next, ae, ao, om, dX, dV);
-                            if (ldiag) upd_df<B, TU, true>(ae, ao, om, dV, dX);
+                            upd_df_rt<B, TU, LD>(tb_next, ae, ao, om, dX, dV);
+                            if (ldiag) upd_df<B, TU, LD, true>(ae, ao, om, dV, dX);
                         } else {
-                            upd_df<B, TU, false>(ae, ao, om, dV, dX);
+                            upd_df<B, TU, LD, false>(ae, ao, om, dV, dX);
                         }
                     } else if (J > 0) {
                         upd_fma_rt<B, TU>(tb_next, ae, ao, om, sXp, sV);      // X_{I,J-1} U_{J-1,J}
@@ -589,7 +678,7 @@ __device__ void syl_ws_instance(int m, int n, const double *L, long ldl, const d
 #pragma unroll
                 for (int r = 0; r < E; ++r) {
                     if (om.ok(r)) {
-                        if constexpr (DF) sT[om.row[r] + om.col[r] * LD] = df_to_double(ae[r], ao[r]);
+                        if constexpr (DF) df2(sT)[om.row[r] + om.col[r] * LD] = make_float2(ae[r], ao[r]);
                         else sT[om.row[r] + om.col[r] * LD] = ae[r] + ao[r];
                     }
                 }
@@ -854,7 +943,7 @@ cudaError_t launch_syl_ws(int block, int nu, bool lyap, bool df, const Operands 
                           cudaStream_t st)
 {
 #define WS_ONE(BB, NN, MB, LY, D)                                                                          \
-    launch_ws(syl_ws_kernel<BB, NN, LY, MB, D>, 32 * NN + 32, ws_smem_bytes<BB>(), l.batch, st, o, s, l.group)
+    launch_ws(syl_ws_kernel<BB, NN, LY, MB, D>, 32 * NN + 32, ws_smem_bytes<BB, D>(), l.batch, st, o, s, l.group)
 #define WS_CASE(BB, NN, MB)                                                                                \
     if (block == BB && nu == NN)                                                                           \
         return df ? (lyap ? WS_ONE(BB, NN, MB, true, true) : WS_ONE(BB, NN, MB, false, true))              \
