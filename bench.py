@@ -39,7 +39,25 @@ if ROOT not in sys.path:
 
 METRIC = "batched solves/s and % roofline, mixed+learned vs plain FP64 GPU at 1e-11 error"
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07   # SMs x DFMA/clk/SM x flop/FMA x GHz = 1258.6
+# Double-float ceiling of SS_MODE_DF: the FP32 pipe's instruction rate
+# (152 SMs x 128 lanes x 2.07 GHz) over the 13 FP32 instructions of one
+# double-float multiply-add (TwoProduct with cross terms, TwoSum, low-part
+# update), counted as the 2 flops of the FP64 operation it replaces.
+DF_OPS_PER_TERM = 13
+DF_PEAK_GFLOPS = 152 * 128 * 2.07 / DF_OPS_PER_TERM * 2   # = 6189.6
 GATE = 1e-11
+
+
+# Arithmetic each precision mode computes in (the JSON line's dtype).
+DTYPE_OF_MODE = {"fp64": "f64", "df": "f32x2 double-float block updates, f64 divisions / pivots",
+                 "fp32_refined": "f32 solve + f32x2 double-float refinement",
+                 "tf32_refined": "tf32 tensor-core updates + f32x2 refinement",
+                 "bf16_refined": "bf16 tensor-core updates + f32x2 refinement"}
+
+
+def inv_mode(m):
+    from paper_1906_08613_gb300 import smallsolve as ss
+    return {v: k for k, v in ss.MODES.items()}.get(int(m), str(m))
 
 
 def flops_paper(op, n):
@@ -368,7 +386,7 @@ def extra_workload(name, seed, device):
 
 def run_extra(args):
     """Rectangular Sylvester (trsyl_rect) or SPD solve (posv_upper) workload,
-    FP64 with one explicit or the default configuration."""
+    FP64 or DF (--mode), with one explicit or the default configuration."""
     import torch
     from paper_1906_08613_gb300 import smallsolve as ss
 
@@ -379,11 +397,14 @@ def run_extra(args):
     sh = stream.cuda_stream
     name = args.workload
     cfg = ss.CFG_DEFAULT if args.cfg is None else args.cfg
+    mode = ss.MODES[args.mode]
+    if mode not in (ss.MODE_FP64, ss.MODE_DF):
+        raise SystemExit("trsyl_rect / posv_upper workloads run in fp64 or df")
     opname, pk, db, F, Balg, names, oracle_one = extra_workload(name, args.seed, dev)
     torch.cuda.synchronize(dev)         # buffer fills (default stream) before the side streams
 
     def step():
-        db.solve(cfg=cfg, stream=sh)
+        db.solve(cfg=cfg, mode=mode, stream=sh)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -413,27 +434,34 @@ def run_extra(args):
     _, _, db2, _, _, _, _ = extra_workload(name, args.seed, dev)
     torch.cuda.synchronize(dev)
     e2e_value, h2d, d2h, x_gpu = e2e_pipelined(
-        [db, db2], host_in, lambda b, st: b.solve(cfg=cfg, stream=st), max(3, min(args.steps, 50)),
+        [db, db2], host_in, lambda b, st: b.solve(cfg=cfg, mode=mode, stream=st), max(3, min(args.steps, 50)),
         dist, dev, pk.batch)
     del db2
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return 0
-    # Whole call (pre-pass + solve launches) against the FP64 peak.
+    # Whole call (pre-pass + solve launches) against the peak of the mode's
+    # arithmetic.
     achieved = F / (ms_step * 1e-3) / 1e9
+    if args.mode == "df":
+        peak, peak_source = DF_PEAK_GFLOPS, ("derived: 152 SMs x 128 FP32 lanes x 2.07 GHz / 13 FP32 "
+                                             "instructions per double-float multiply-add x 2 flop (of derived)")
+    else:
+        peak, peak_source = FP64_PEAK_GFLOPS, "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (of derived)"
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": name, "op": opname, "batch": pk.batch, "path": "fp64", "cfg": cfg,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": DTYPE_OF_MODE[args.mode] + " (X in f64)", "data": "synthetic",
+        "config": {"workload": name, "op": opname, "batch": pk.batch, "path": args.mode, "cfg": cfg,
                    "l2": f"operands {sum(int(v.numel()) * 8 for v in db.bufs.values()) / 1e6:.0f} MB "
                          "> 129 MB L2; no flush"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                     "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "fp64_equivalent_frac": achieved / FP64_PEAK_GFLOPS,
                      "kernel": f"{opname}: whole call (pre-pass and solve launches)", "call_ms": ms_step,
                      "algorithmic_bytes": Balg, "flops": F,
-                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (of derived)"},
+                     "peak_source": peak_source},
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches), "launches_per_step": launches / args.steps, "clocks": clk,
         "info_nonzero": int((info != 0).sum()),
@@ -630,21 +658,32 @@ def main():
     else:
         dominant_key = f"{name}:{op}:{args.mode}:{cfg}"
     achieved = Falg / (kern_avg_ms * 1e-3) / 1e9
-    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-            "frac": achieved / FP64_PEAK_GFLOPS,
+    df_dominant = dominant_key.split(":")[2] == "df"
+    if df_dominant:
+        peak, peak_source = DF_PEAK_GFLOPS, (
+            "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz / 13 FP32 instructions per double-float "
+            "multiply-add x 2 flop (of derived; an FFMA probe measured 72 TFLOP/s, 89 % of the nominal "
+            "FP32 rate)")
+    else:
+        peak, peak_source = FP64_PEAK_GFLOPS, ("derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz "
+                                               "(of derived; a DFMA probe measured 1248 GFLOP/s)")
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
+            "frac": achieved / peak,
             "traffic": read_traffic(dominant_key),
             "kernel": f"{op} persistent solve kernels ({'selector tables' if learned else args.mode})",
             "dominant": dominant_key,
-            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (of derived; "
-                           "a DFMA probe measured 1248 GFLOP/s)",
+            "peak_source": peak_source,
+            "fp64_equivalent_frac": achieved / FP64_PEAK_GFLOPS,
             "kernel_ms": kern_avg_ms, "algorithmic_bytes": Balg,
             "hbm_frac": Balg / (kern_avg_ms * 1e-3) / 6801.3e9}
+    used = sorted({inv_mode(m) for m in table[0] if m >= 0}) if table else [args.mode]
+    dtype = " + ".join(DTYPE_OF_MODE.get(m, m) for m in used) + " (X in f64)"
 
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if (not learned and args.mode == "fp64") else "f64 out (f64 / f32+df64-refined per size bin)",
+        "dtype": dtype,
         "data": "synthetic",
         "config": {"workload": name, "op": op, "batch": pk.batch,
                    "sizes": f"n in [{int(pk.n.min())}, {int(pk.n.max())}], mean {float(pk.n.mean()):.1f}",

@@ -45,15 +45,18 @@
  * SS_REFINE_MAXIT steps ran.  The *_RAW modes stop after the low-precision
  * solve.  Refined and raw modes need workspace (see ss_workspace_size).
  *
- * SS_MODE_DF (trsyl_lu, trlyap_l, trsyl_rect): the warp-specialised FP64
- * pipeline with its block updates T = C - sum L X - sum X U in double-float
- * arithmetic (each FP64 operand split into two floats, about 48 significant
- * bits; error-free products and sums on the FP32 pipe).  The diagonal blocks,
- * the divisions l_ii + u_jj and X stay FP64; no refinement and no workspace
- * beyond FP64's.  Accuracy is that of FP64 up to the split's 2^-47 relative
- * representation error per operand.  Values must lie in FP32's normal range
- * (magnitude about 1.2e-38 to 3.4e38); outside it the split loses the
- * double-float accuracy.
+ * SS_MODE_DF: the warp-specialised pipeline with its block updates in
+ * double-float arithmetic (each FP64 operand split into two floats, about 48
+ * significant bits; error-free products and sums on the FP32 pipe).
+ * trsyl_lu, trlyap_l, trsyl_rect: T = C - sum L X - sum X U and the
+ * diagonal-block recurrences in double-float; the divisors l_ii + u_jj and
+ * their reciprocals are computed in FP64; X is rounded to FP64.  potrf_upper,
+ * posv_upper (factor stage): T = A - sum X^T X in double-float; the diagonal
+ * blocks (square roots, pivots, panel solves) stay FP64.  No refinement and no
+ * workspace beyond FP64's.  Accuracy is that of FP64 up to the split's 2^-47
+ * relative representation error per operand.  Values must lie in FP32's
+ * normal range (magnitude about 1.2e-38 to 3.4e38); outside it the split
+ * loses the double-float accuracy.
  *
  * SS_MODE_AUTO solves each size bin in the (mode, cfg) pair given by
  * ss_set_auto_table (the autotuner's or the learned selector's choice among
@@ -190,9 +193,10 @@ int trsyl_rect(int batch, int max_m, int max_n, const int *d_m, const int *d_n,
  * d_ldr[b] >= max(1, n); d_ldb[b], d_ldx[b] >= max(1, n).  0 <= n <= max_n
  * <= SS_MAX_N and 0 <= k <= max_k.  info: 0 success; j > 0 the factor's
  * pivot j failed (X untouched); SS_INFO_BAD_SIZE for n or k out of range (X
- * untouched; for a bad k, R is computed).  mode must be SS_MODE_FP64 (other
+ * untouched; for a bad k, R is computed).  mode must be SS_MODE_FP64 or
+ * SS_MODE_DF (the factor stage's mode; the triangular solves are FP64; other
  * modes return -15); cfg selects the Cholesky configuration (as for
- * potrf_upper).  Workspace: the size ss_workspace_size(SS_OP_POTRF, batch,
+ * potrf_upper in that mode).  Workspace: the size ss_workspace_size(SS_OP_POTRF, batch,
  * max_n, SS_MODE_FP64, ...) reports.  Two launches after the pre-pass: the
  * factor, then the solves, ordered on `stream`.
  */
@@ -271,7 +275,7 @@ int ss_set_auto_table(int op, int nbins, const int *mode_by_bin, const int *cfg_
  * work" paragraph: replace the autotuning loops with a model-based approach).
  * A fixed MLP  h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), y = W3 h2 + b3
  * maps SS_MLP_IN features (op one-hot [3], log2 n, log2 batch, mode one-hot
- * [FP64, FP32, TF32, BF16 refined]) to SS_MLP_OUT predicted log2 run times,
+ * [FP64, FP32, TF32, BF16 refined, DF]) to SS_MLP_OUT predicted log2 run times,
  * one per kernel configuration id.  Parameters: one device float array of
  * SS_MLP_PARAMS values laid out W1 (H x IN, row-major), b1, W2 (H x H), b2,
  * W3 (OUT x H), b3.  All arrays are device pointers, row-major per row.
@@ -285,7 +289,7 @@ int ss_set_auto_table(int op, int nbins, const int *mode_by_bin, const int *cfg_
  *   and the moment arrays d_m, d_v (each SS_MLP_PARAMS floats, zero at start).
  * Return 0, -k for an invalid argument k, or SS_ERR_CUDA.
  */
-#define SS_MLP_IN 9
+#define SS_MLP_IN 10
 #define SS_MLP_HIDDEN 64
 #define SS_MLP_OUT 8
 #define SS_MLP_PARAMS (SS_MLP_HIDDEN * SS_MLP_IN + SS_MLP_HIDDEN + SS_MLP_HIDDEN * SS_MLP_HIDDEN + \

@@ -10,7 +10,7 @@ are mathematical: finite differences, closed forms, special cases.
 """
 import numpy as np
 
-IN, H, OUT = 9, 64, 8
+IN, H, OUT = 10, 64, 8      # inputs: op one-hot [3], log2 n, log2 batch, mode one-hot [5]
 NPARAM = H * IN + H + H * H + H + OUT * H + OUT
 
 

@@ -15,6 +15,8 @@ cudaError_t launch_potrf_fp64(const Operands &o, const Sched &s, const Launch &l
 cudaError_t launch_syl_fp64(const Operands &o, const Sched &s, const Launch &l, cudaStream_t st, bool lyap);
 cudaError_t launch_syl_ws(int block, int nu, bool lyap, bool df, const Operands &o, const Sched &s, const Launch &l,
                           cudaStream_t st);
+cudaError_t launch_potrf_ws(int block, int nu, bool df, const Operands &o, const Sched &s, const Launch &l,
+                            cudaStream_t st);
 cudaError_t launch_mixed(int op, const Operands &o, const Sched &s, const Launch &l, cudaStream_t st);
 int mixed_config_count(int op, int mode);
 const Config *mixed_config_get(int op, int mode, int cfg);
@@ -39,10 +41,13 @@ const Config kFp64Syl[] = {
 };
 constexpr int kNumFp64Potrf = sizeof(kFp64Potrf) / sizeof(kFp64Potrf[0]);
 constexpr int kNumFp64Syl = sizeof(kFp64Syl) / sizeof(kFp64Syl[0]);
-// SS_MODE_DF (Sylvester / Lyapunov): variant 4, the warp-specialised pipeline
-// with double-float update warps.
+// SS_MODE_DF: variant 4, the warp-specialised pipeline with double-float
+// update warps (Sylvester / Lyapunov: double-float diagonal blocks too;
+// Cholesky: FP64 diagonal warp).
 const Config kDfSyl[] = {{16, 64, 4}, {16, 96, 4}, {16, 160, 4}};
+const Config kDfPotrf[] = {{16, 96, 4}, {16, 160, 4}};
 constexpr int kNumDfSyl = sizeof(kDfSyl) / sizeof(kDfSyl[0]);
+constexpr int kNumDfPotrf = sizeof(kDfPotrf) / sizeof(kDfPotrf[0]);
 // Mode ids 0..SS_MODE_DF index the per-mode tables (SS_MODE_AUTO's slot unused).
 constexpr int kModeSlots = SS_MODE_DF + 1;
 
@@ -146,7 +151,7 @@ bool profile_pair(cudaEvent_t *a, cudaEvent_t *b)
 int config_count(int op, int mode)
 {
     if (mode == SS_MODE_FP64) return op == SS_OP_POTRF ? kNumFp64Potrf : kNumFp64Syl;
-    if (mode == SS_MODE_DF) return op == SS_OP_POTRF ? 0 : kNumDfSyl;
+    if (mode == SS_MODE_DF) return op == SS_OP_POTRF ? kNumDfPotrf : kNumDfSyl;
     return mixed_config_count(op, mode);
 }
 
@@ -154,7 +159,7 @@ const Config *config_get(int op, int mode, int cfg)
 {
     if (cfg < 0 || cfg >= config_count(op, mode)) return nullptr;
     if (mode == SS_MODE_FP64) return op == SS_OP_POTRF ? &kFp64Potrf[cfg] : &kFp64Syl[cfg];
-    if (mode == SS_MODE_DF) return &kDfSyl[cfg];
+    if (mode == SS_MODE_DF) return op == SS_OP_POTRF ? &kDfPotrf[cfg] : &kDfSyl[cfg];
     return mixed_config_get(op, mode, cfg);
 }
 
@@ -168,7 +173,7 @@ const Config *config_get(int op, int mode, int cfg)
 //   with one update warp up to 64, then two (large batches) or four.
 int config_default(int op, int mode, int max_n, int batch)
 {
-    if (mode == SS_MODE_DF) return 1;                    // (16, 96, 4)
+    if (mode == SS_MODE_DF) return op == SS_OP_POTRF ? 0 : 2;   // (16, 96, 4) / (16, 160, 4)
     if (mode != SS_MODE_FP64) return 0;
     if (op == SS_OP_POTRF) {
         if (max_n <= 16) return 5;                       // (16, 64, 1)
@@ -332,8 +337,9 @@ int run(int op, int batch, int max_n, const Operands &o, int mode, int cfg, void
             else e = launch_syl_fp64(o, s, l, gs, op == SS_OP_TRLYAP);
         } else if (l.mode == SS_MODE_DF) {
             const Config *c = config_get(op, SS_MODE_DF, l.cfg);
-            e = c ? launch_syl_ws(c->block, (c->threads - 32) / 32, op == SS_OP_TRLYAP, true, o, s, l, gs)
-                  : cudaErrorInvalidValue;
+            if (!c) e = cudaErrorInvalidValue;
+            else if (op == SS_OP_POTRF) e = launch_potrf_ws(c->block, (c->threads - 32) / 32, true, o, s, l, gs);
+            else e = launch_syl_ws(c->block, (c->threads - 32) / 32, op == SS_OP_TRLYAP, true, o, s, l, gs);
         } else {
             e = launch_mixed(op, o, s, l, gs);
         }
@@ -441,8 +447,8 @@ int posv_upper(int batch, int max_n, int max_k, const int *d_n, const int *d_k, 
         if (!d_ldx) return -13;
         if (!d_info) return -14;
     }
-    if (mode != SS_MODE_FP64) return -15;
-    // Stage 1: the factor R (R^T R = A) by the FP64 Cholesky path; it also
+    if (mode != SS_MODE_FP64 && mode != SS_MODE_DF) return -15;
+    // Stage 1: the factor R (R^T R = A) by the Cholesky path (FP64 or DF); it also
     // sorts the instances by n and leaves the order in the workspace.
     Operands o{d_n, d_A, d_lda, nullptr, nullptr, nullptr, nullptr, d_R, d_ldr, d_info};
     const int rc = run(SS_OP_POTRF, batch, max_n, o, mode, cfg, d_work, work_bytes, stream, 15, 17);

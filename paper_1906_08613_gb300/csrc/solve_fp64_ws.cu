@@ -379,6 +379,38 @@ __device__ __forceinline__ void upd_df(float (&ah)[B * B / TU], float (&al)[B * 
 }
 
 template <int B, int TU, int LDT>
+__device__ __forceinline__ void upd_df_ta(float (&ah)[B * B / TU], float (&al)[B * B / TU], const OutMap<B, TU> &om,
+                                          const float2 *A, const float2 *Bm)
+{
+    constexpr int E = B * B / TU;
+#pragma unroll 2
+    for (int k = 0; k < B; ++k) {
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            if (om.ok(r)) {
+                const float2 a = A[k + om.row[r] * LDT];
+                const float2 b = Bm[k + om.col[r] * LDT];
+                df_msub(ah[r], al[r], a.x, a.y, b.x, b.y);
+            }
+        }
+    }
+}
+
+// All update threads: the B x B double tile S as double-float pairs into D
+// (both leading dimension LDT).
+template <int B, int TU, int LDT>
+__device__ __forceinline__ void tile_to_df(float2 *D, const double *S, int ut)
+{
+#pragma unroll
+    for (int e = ut; e < B * B; e += TU) {
+        const int r = e % B, c = e / B;
+        float2 v;
+        split_df(S[r + c * LDT], v.x, v.y);
+        D[r + c * LDT] = v;
+    }
+}
+
+template <int B, int TU, int LDT>
 __device__ __forceinline__ void upd_df_rt(bool tb, float (&ah)[B * B / TU], float (&al)[B * B / TU],
                                           const OutMap<B, TU> &om, const float2 *A, const float2 *Bm)
 {
@@ -748,7 +780,7 @@ __device__ void warp_trsm_ut(const double *sD, const double *sR, double *sT, int
     }
 }
 
-template <int B, int NU>
+template <int B, int NU, bool DF>
 __device__ void chol_ws_instance(int n, const double *A, long lda, double *X, long ldx, int *info, double *sm)
 {
     constexpr int LD = Tile<B>::LD, SZ = Tile<B>::SZ;
@@ -796,6 +828,7 @@ __device__ void chol_ws_instance(int n, const double *A, long lda, double *X, lo
         const int ut = threadIdx.x - 32;
         OutMap<B, TU> om;
         Prefetch<B, TU> pf;
+        using Acc = typename std::conditional<DF, float, double>::type;
         int t = 0;
         for (int J = 0; J < nb; ++J) {
             const int nJ = min(B, n - J * B), j0 = J * B;
@@ -823,14 +856,21 @@ __device__ void chol_ws_instance(int n, const double *A, long lda, double *X, lo
                         sb = Src{X + (long)(I - 1) * B + (long)i0 * ldx, ldx, B, mI, false};   // X_{I-1,I}
                         pf.load(sa, sb, false, ut);
                     }
-                    pf.store(sA0, sB0, nsteps > 0, ut);
+                    if constexpr (DF) pf.template store_df<LD>(df2(sA0), df2(sB0), nsteps > 0, ut);
+                    else pf.store(sA0, sB0, nsteps > 0, ut);
                     named_sync(kBarUpd, TU);
                 }
-                double ae[E], ao[E];
+                // FP64: even / odd terms; DF: hi / lo of one double-float sum.
+                Acc ae[E], ao[E];
 #pragma unroll
                 for (int r = 0; r < E; ++r) {
-                    ao[r] = 0.0;
-                    ae[r] = om.ok(r) ? A[(i0 + om.row[r]) + (long)(j0 + om.col[r]) * lda] : 0.0;
+                    ao[r] = 0;
+                    ae[r] = 0;
+                    if (om.ok(r)) {
+                        const double a = A[(i0 + om.row[r]) + (long)(j0 + om.col[r]) * lda];
+                        if constexpr (DF) split_df(a, ae[r], ao[r]);
+                        else ae[r] = a;
+                    }
                 }
                 for (int s = 0; s < nsteps; ++s) {
                     const int buf = s & 1;
@@ -840,8 +880,14 @@ __device__ void chol_ws_instance(int n, const double *A, long lda, double *X, lo
                         else sb = Src{X + (long)(I - 1) * B + (long)i0 * ldx, ldx, B, mI, false};
                         pf.load(sa, sb, next_bulk, ut);
                     }
-                    upd_fma_ta<B, TU>(ae, ao, om, sA0 + buf * SZ, sB0 + buf * SZ);
-                    if (more) pf.store(sA0 + (buf ^ 1) * SZ, sB0 + (buf ^ 1) * SZ, next_bulk, ut);
+                    if constexpr (DF) {
+                        upd_df_ta<B, TU, LD>(ae, ao, om, df2(sA0 + buf * SZ), df2(sB0 + buf * SZ));
+                        if (more)
+                            pf.template store_df<LD>(df2(sA0 + (buf ^ 1) * SZ), df2(sB0 + (buf ^ 1) * SZ), next_bulk, ut);
+                    } else {
+                        upd_fma_ta<B, TU>(ae, ao, om, sA0 + buf * SZ, sB0 + buf * SZ);
+                        if (more) pf.store(sA0 + (buf ^ 1) * SZ, sB0 + (buf ^ 1) * SZ, next_bulk, ut);
+                    }
                     named_sync(kBarUpd, TU);
                 }
                 if (t > 0) named_sync(kBarX, TALL);        // X of block t-1 is final
@@ -850,12 +896,25 @@ __device__ void chol_ws_instance(int n, const double *A, long lda, double *X, lo
                     // is the staged tile, or for I = J that same block.
                     const double *sXp = sT0 + ((t - 1) & 1) * SZ;
                     const double *sV = diag ? sXp : sB0 + (nsteps & 1) * SZ;
-                    upd_fma_ta<B, TU>(ae, ao, om, sV, sXp);
+                    if constexpr (DF) {
+                        // X_{I-1,J} split into the free staging tile sA[nsteps & 1]
+                        // (the last step stages no A operand).
+                        float2 *dX = df2(sA0 + (nsteps & 1) * SZ);
+                        tile_to_df<B, TU, LD>(dX, sXp, ut);
+                        named_sync(kBarUpd, TU);
+                        upd_df_ta<B, TU, LD>(ae, ao, om, diag ? dX : df2(sV), dX);
+                    } else {
+                        upd_fma_ta<B, TU>(ae, ao, om, sV, sXp);
+                    }
                 }
                 double *sT = sT0 + (t & 1) * SZ;
 #pragma unroll
-                for (int r = 0; r < E; ++r)
-                    if (om.ok(r)) sT[om.row[r] + om.col[r] * LD] = ae[r] + ao[r];
+                for (int r = 0; r < E; ++r) {
+                    if (om.ok(r)) {
+                        if constexpr (DF) sT[om.row[r] + om.col[r] * LD] = df_to_double(ae[r], ao[r]);
+                        else sT[om.row[r] + om.col[r] * LD] = ae[r] + ao[r];
+                    }
+                }
                 named_sync(kBarUpd, TU);                   // staging tiles free again
                 named_arrive(kBarT, TALL);                 // T of block t is in sT
             }
@@ -909,7 +968,7 @@ cudaError_t launch_ws(K kernel, int threads, size_t smem, int batch, cudaStream_
 
 }  // namespace
 
-template <int B, int NU, int MINB>
+template <int B, int NU, int MINB, bool DF>
 __global__ void __launch_bounds__(32 * NU + 32, MINB) chol_ws_kernel(Operands o, Sched s, int group)
 {
     extern __shared__ double sm[];
@@ -919,18 +978,21 @@ __global__ void __launch_bounds__(32 * NU + 32, MINB) chol_ws_kernel(Operands o,
     while (next_instance(s, group, &s_slot, b)) {
         const int n = o.n[b];
         if (n == 0) { if (threadIdx.x == 0) o.info[b] = 0; continue; }
-        chol_ws_instance<B, NU>(n, o.A[b], o.lda[b], o.X[b], o.ldx[b], o.info + b, sm);
+        chol_ws_instance<B, NU, DF>(n, o.A[b], o.lda[b], o.X[b], o.ldx[b], o.info + b, sm);
     }
 }
 
-// Warp-specialised Cholesky configurations: block B, NU update warps.
-cudaError_t launch_potrf_fp64_ws(int block, int nu, const Operands &o, const Sched &s, const Launch &l,
-                                 cudaStream_t st)
+// Warp-specialised Cholesky configurations: block B, NU update warps; df:
+// double-float update warps (the diagonal warp stays FP64).
+cudaError_t launch_potrf_ws(int block, int nu, bool df, const Operands &o, const Sched &s, const Launch &l,
+                            cudaStream_t st)
 {
 #define CWS_CASE(BB, NN, MB)                                                                              \
     if (block == BB && nu == NN)                                                                          \
-        return launch_ws(chol_ws_kernel<BB, NN, MB>, 32 * NN + 32, ws_smem_bytes<BB>(), l.batch, st, o, s, \
-                         l.group);
+        return df ? launch_ws(chol_ws_kernel<BB, NN, MB, true>, 32 * NN + 32, ws_smem_bytes<BB>(), l.batch, st, o, \
+                              s, l.group)                                                                 \
+                  : launch_ws(chol_ws_kernel<BB, NN, MB, false>, 32 * NN + 32, ws_smem_bytes<BB>(), l.batch, st, \
+                              o, s, l.group);
     CWS_CASE(16, 2, 8)
     CWS_CASE(16, 4, 6)
 #undef CWS_CASE

@@ -91,10 +91,10 @@ cudaError_t launch_trlyap(const Operands &o, const Sched &s, const Launch &l, cu
 cudaError_t launch_syl_ws(int block, int nu, bool lyap, bool df, const Operands &o, const Sched &s, const Launch &l,
                           cudaStream_t st);
 
-// FP64 Cholesky with warp-specialised CTAs (block B, nu update warps plus one
-// diagonal warp).
-cudaError_t launch_potrf_fp64_ws(int block, int nu, const Operands &o, const Sched &s, const Launch &l,
-                                 cudaStream_t st);
+// Cholesky with warp-specialised CTAs (block B, nu update warps plus one
+// diagonal warp); df: double-float update warps (SS_MODE_DF).
+cudaError_t launch_potrf_ws(int block, int nu, bool df, const Operands &o, const Sched &s, const Launch &l,
+                            cudaStream_t st);
 
 // Solve stage of the SPD solve (R^T Y = B, R X = Y) over the valid instances
 // of a binning pass, on queue head `group`.

@@ -9,8 +9,9 @@ and its training run in the library's CUDA kernels (``ss_mlp_forward``,
 arrays and picks the argmin.  The exhaustive autotuner (``tune.py``) produces
 the training table, stays the fallback, and judges the selector's regret.
 
-Features (SS_MLP_IN = 9): op one-hot (potrf, trsyl, trlyap), log2(n)/9,
-log2(batch)/14, mode one-hot (fp64, fp32_refined, tf32_refined, bf16_refined).
+Features (SS_MLP_IN = 10): op one-hot (potrf, trsyl, trlyap), log2(n)/9,
+log2(batch)/14, mode one-hot (fp64, fp32_refined, tf32_refined, bf16_refined,
+df).
 Targets: log2(milliseconds) per configuration id (SS_MLP_OUT = 8 slots, masked
 to the configurations the mode has).
 """
@@ -26,7 +27,7 @@ from . import smallsolve as ss
 from . import tune
 
 OP_ORDER = ("potrf", "trsyl", "trlyap")
-MODE_ORDER = ("fp64", "fp32_refined", "tf32_refined", "bf16_refined")
+MODE_ORDER = ("fp64", "fp32_refined", "tf32_refined", "bf16_refined", "df")
 
 
 def heldout_bucket(k: int, batch: int, batches_of_bin) -> bool:
@@ -110,6 +111,12 @@ class Selector:
         # that never had a target carries no information, so choices stay
         # within these (None: the library's count).
         self.cfg_counts = None
+        # "op:bin:mode" -> the largest batch the network was trained on for
+        # that size bin and mode.  Beyond it a prediction is taken at that
+        # batch and scaled by count / batch (throughput-bound kernels), a
+        # regime the network, trained on smaller batches there, does not
+        # extrapolate to.
+        self.batch_max = None
 
     def n_cfgs(self, op: str, mode: str) -> int:
         cnt = ss.ss_config_count(ss.OPS[op], ss.MODES[mode])
@@ -133,6 +140,7 @@ class Selector:
         W = torch.empty(max(wb, 4), dtype=torch.uint8, device=dev)
         total = float(M.sum())
         self.cfg_counts = trained_cfg_counts(X, M)
+        self.batch_max = trained_batch_max(X)
         hist = []
         for step in range(1, steps + 1):
             ss.ss_mlp_grad(P.data_ptr(), rows, dX.data_ptr(), dT.data_ptr(), dM.data_ptr(), total,
@@ -160,6 +168,15 @@ class Selector:
         torch.cuda.synchronize(dev)
         return Y.cpu().numpy()
 
+    def query_batch(self, op: str, n: float, batch: float, mode: str):
+        """(batch fed to the network, factor on its prediction) for `batch`
+        instances of order n in `mode` (see batch_max)."""
+        if self.batch_max:
+            bmax = self.batch_max.get(f"{op}:{ss.size_bin(int(round(n)))}:{mode}")
+            if bmax and batch > bmax:
+                return float(bmax), batch / float(bmax)
+        return batch, 1.0
+
     def choose_many(self, queries):
         """queries: list of (op, n, batch) -> list of (mode, cfg, predicted ms)."""
         rows, idx = [], []
@@ -168,14 +185,16 @@ class Selector:
                 cnt = self.n_cfgs(op, mode)
                 if cnt <= 0:
                     continue
-                rows.append(features(op, n, batch, mode))
-                idx.append((qi, mode, cnt))
+                fb, scale = self.query_batch(op, n, batch, mode)
+                rows.append(features(op, n, fb, mode))
+                idx.append((qi, mode, cnt, scale))
         Y = self.predict(np.array(rows)) if rows else np.zeros((0, ss.MLP_OUT))
         best = [None] * len(queries)
-        for (qi, mode, cnt), y in zip(idx, Y):
+        for (qi, mode, cnt, scale), y in zip(idx, Y):
             c = int(np.argmin(y[:cnt]))
-            if best[qi] is None or y[c] < best[qi][2]:
-                best[qi] = (mode, c, float(y[c]))
+            v = float(y[c]) + math.log2(scale)
+            if best[qi] is None or v < best[qi][2]:
+                best[qi] = (mode, c, v)
         return [(m, c, 2.0 ** v) for (m, c, v) in best]
 
     def auto_table(self, op: str, batch, nbins: int = ss.NUM_BINS):
@@ -198,20 +217,22 @@ class Selector:
         split the call into serialized launches, each with its own tail."""
         counts = list(batch) if hasattr(batch, "__len__") else [batch] * nbins
         want = [k for k in range(nbins) if counts[k] > 0]
-        rows, cand = [], []
+        rows, cand, scales = [], [], []
         for mode in MODE_ORDER:
             cnt = self.n_cfgs(op, mode)
             if cnt <= 0:
                 continue
             cand.append((mode, cnt))
             for k in want:
-                rows.append(features(op, bin_center(k), counts[k], mode))
+                fb, scale = self.query_batch(op, bin_center(k), counts[k], mode)
+                rows.append(features(op, bin_center(k), fb, mode))
+                scales.append(scale)
         Y = self.predict(np.array(rows)) if rows else np.zeros((0, ss.MLP_OUT))
         best, i = None, 0
         for mode, cnt in cand:
             tot = np.zeros(cnt)
             for _ in want:
-                tot += 2.0 ** Y[i, :cnt]
+                tot += scales[i] * 2.0 ** Y[i, :cnt]
                 i += 1
             c = int(np.argmin(tot))
             if best is None or tot[c] < best[2]:
@@ -236,7 +257,7 @@ class Selector:
             json.dump({"params": os.path.basename(path) + ".npy", "n_params": int(self.params.size),
                        "features": "op one-hot, log2(n)/9, log2(batch)/14, mode one-hot",
                        "op_order": OP_ORDER, "mode_order": MODE_ORDER,
-                       "cfg_counts": self.cfg_counts, **meta}, f, indent=1)
+                       "cfg_counts": self.cfg_counts, "batch_max": self.batch_max, **meta}, f, indent=1)
 
     @classmethod
     def load(cls, path: str, device="cuda"):
@@ -244,6 +265,7 @@ class Selector:
         with open(path + ".json") as f:
             s.meta = json.load(f)
         s.cfg_counts = s.meta.get("cfg_counts")
+        s.batch_max = s.meta.get("batch_max")
         return s
 
 
@@ -258,6 +280,20 @@ def trained_cfg_counts(X, M):
         if nz.size:
             key = f"{op}:{mode}"
             out[key] = max(out.get(key, 0), int(nz[-1]) + 1)
+    return out
+
+
+def trained_batch_max(X):
+    """{"op:bin:mode": the largest batch among the training rows of that size
+    bin and mode} from the one-hot, log2(n) and log2(batch) features."""
+    out = {}
+    for x in np.asarray(X, dtype=np.float64):
+        op = OP_ORDER[int(np.argmax(x[0:3]))]
+        mode = MODE_ORDER[int(np.argmax(x[5:5 + len(MODE_ORDER)]))]
+        k = ss.size_bin(int(round(2.0 ** (x[3] * 9.0))))
+        b = int(round(2.0 ** (x[4] * 14.0)))
+        key = f"{op}:{k}:{mode}"
+        out[key] = max(out.get(key, 0), b)
     return out
 
 

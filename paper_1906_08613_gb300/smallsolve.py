@@ -45,7 +45,7 @@ INFO_BAD_SIZE = -1
 INFO_ALIASED = -3
 INFO_NO_WORK = -2
 MAX_N = 4096
-MLP_IN, MLP_HIDDEN, MLP_OUT = 9, 64, 8
+MLP_IN, MLP_HIDDEN, MLP_OUT = 10, 64, 8
 MLP_PARAMS = MLP_HIDDEN * MLP_IN + MLP_HIDDEN + MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN + \
     MLP_OUT * MLP_HIDDEN + MLP_OUT
 NUM_BINS = 13

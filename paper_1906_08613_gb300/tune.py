@@ -5,7 +5,7 @@ This is the search loop of the paper's generator ("Generator structure"
 paragraph: autotuning selects the fastest code among alternative algorithms and
 implementation parameters), over this library's axes: algorithm variant x block
 size x threads per CTA x precision mode.  Only modes that meet the FP64
-accuracy gate are candidates (FP64 and the *_REFINED modes).
+accuracy gate are candidates (FP64, the *_REFINED modes and DF).
 
 A bucket's instances have order n uniform over the size bin
 (2^(k-1), 2^k] and are solved in one call; the time is the median of a few
@@ -16,6 +16,7 @@ CUDA-event-timed calls after a warm-up.  The database is JSON:
          "mode": "fp64", "cfg": 2, "ms": 1.23}, ...]}
 
 Usage (on a GPU):  python -m paper_1906_08613_gb300.tune --out DB.json
+            [--ops trsyl,trlyap --modes df --merge OLD.json]
 """
 from __future__ import annotations
 
@@ -31,7 +32,7 @@ import numpy as np
 from . import inputs
 from . import smallsolve as ss
 
-AUTO_MODES = ("fp64", "fp32_refined", "tf32_refined", "bf16_refined")
+AUTO_MODES = ("fp64", "fp32_refined", "tf32_refined", "bf16_refined", "df")
 OPS = ("potrf", "trsyl", "trlyap")
 
 
@@ -43,11 +44,14 @@ def bin_range(k: int):
 
 
 def default_buckets(max_bin: int = 9):
-    """(op, bin, batch) buckets: two batch sizes per bin, smaller for large n."""
+    """(op, bin, batch) buckets: two batch sizes per bin up to n = 128; for
+    larger n a small, a medium and a large batch (a mixed stream of n up to 512
+    puts several hundred instances in each of those bins, where the kernels
+    move from latency- to throughput-bound)."""
     out = []
     for op in OPS:
         for k in range(2, max_bin + 1):
-            batches = (256, 2048) if k <= 7 else (64, 256)
+            batches = (256, 2048) if k <= 7 else (64, 256, 1024)
             for b in batches:
                 out.append((op, k, b))
     return out
@@ -187,12 +191,28 @@ def main(argv=None):
     ap.add_argument("--max-bin", type=int, default=9)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--ops", default=",".join(OPS))
+    ap.add_argument("--modes", default=",".join(AUTO_MODES))
+    ap.add_argument("--min-bin", type=int, default=2)
+    ap.add_argument("--batches", default=None, help="only these batch sizes of the default buckets")
+    ap.add_argument("--merge", default=None,
+                    help="existing database: keep its entries, replacing those of the swept (op, bin, batch, mode)")
     args = ap.parse_args(argv)
     ops = args.ops.split(",")
-    buckets = [b for b in default_buckets(args.max_bin) if b[0] in ops]
+    modes = tuple(args.modes.split(","))
+    batches = None if args.batches is None else {int(b) for b in args.batches.split(",")}
+    buckets = [b for b in default_buckets(args.max_bin) if b[0] in ops and b[1] >= args.min_bin
+               and (batches is None or b[2] in batches)]
     t0 = time.time()
-    entries = sweep(buckets, reps=args.reps, log=lambda s: print(s, flush=True))
-    save(entries, args.out, {"sweep_seconds": time.time() - t0})
+    entries = sweep(buckets, modes=modes, reps=args.reps, log=lambda s: print(s, flush=True))
+    extra = {"sweep_seconds": time.time() - t0}
+    if args.merge:
+        old = load(args.merge)
+        swept = {(e["op"], e["bin"], e["batch"], e["mode"]) for e in entries}
+        kept = [e for e in old["entries"] if (e["op"], e["bin"], e["batch"], e["mode"]) not in swept]
+        entries = kept + entries
+        what = f"{','.join(modes)} x {','.join(ops)}, bins >= {args.min_bin}" + (f", batches {args.batches}" if batches else "")
+        extra["note"] = f"{old.get('note', '')}; swept {what} on {time.strftime('%Y-%m-%d')}".lstrip("; ")
+    save(entries, args.out, extra)
     print(f"{len(entries)} entries in {time.time() - t0:.0f} s -> {args.out}")
 
 

@@ -112,20 +112,22 @@ def test_df_mode_host_side(lib):
     text = open(HEADER).read()
     assert int(re.search(r"#define SS_MODE_DF\s+(\d+)", text).group(1)) == ss.MODE_DF
     assert ss.MODES["df"] == ss.MODE_DF
-    for op in (ss.OP_TRSYL, ss.OP_TRLYAP):
+    for op, want in ((ss.OP_POTRF, 2), (ss.OP_TRSYL, 3), (ss.OP_TRLYAP, 3)):
         cnt = ss.ss_config_count(op, ss.MODE_DF)
-        assert cnt == 3
+        assert cnt == want
         assert all(ss.ss_config_describe(op, ss.MODE_DF, c)[2] == 4 for c in range(cnt))
         # No scratch beyond FP64's.
         assert ss.ss_workspace_size(op, 1000, 128, ss.MODE_DF) == ss.ss_workspace_size(op, 1000, 128, ss.MODE_FP64)
-    assert ss.ss_config_count(ss.OP_POTRF, ss.MODE_DF) == 0
-    # Cholesky and the SPD solve have no DF form: rejected before any launch.
-    assert ss.potrf_upper(1, 4, 1, 1, 1, 1, 1, 1, mode=ss.MODE_DF, check=False) == -9
-    assert ss.posv_upper(1, 4, 4, *([1] * 11), mode=ss.MODE_DF, check=False) == -15
+    # Argument checks of the DF forms run before any launch.
+    assert ss.potrf_upper(1, 4, 1, 1, 1, 1, 1, 1, mode=ss.MODE_DF, cfg=2, check=False) == -10
+    assert ss.posv_upper(1, 4, 4, *([1] * 11), mode=ss.MODE_DF, cfg=2, check=False) == -16
+    assert ss.posv_upper(1, 4, 4, *([1] * 11), mode=ss.MODE_FP32_REFINED, check=False) == -15
     ss.ss_set_auto_table(ss.OP_TRSYL, [ss.MODE_DF, ss.MODE_FP64], [2, 0])
+    ss.ss_set_auto_table(ss.OP_POTRF, [ss.MODE_DF], [1])
     ss.ss_set_auto_table(ss.OP_TRSYL, [], [])
+    ss.ss_set_auto_table(ss.OP_POTRF, [], [])
     with pytest.raises(ss.SmallSolveError):
-        ss.ss_set_auto_table(ss.OP_POTRF, [ss.MODE_DF], [0])
+        ss.ss_set_auto_table(ss.OP_POTRF, [ss.MODE_DF], [2])
     with pytest.raises(ss.SmallSolveError):
         ss.ss_set_config_table(ss.OP_TRLYAP, ss.MODE_DF, [3])
 

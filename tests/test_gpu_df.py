@@ -1,6 +1,7 @@
-"""Parity of SS_MODE_DF (warp-specialised Sylvester / Lyapunov with
-double-float block updates on the FP32 pipe, FP64 diagonal blocks) with the
-CPU oracle, through the C ABI.
+"""Parity of SS_MODE_DF (the warp-specialised pipelines with double-float
+block updates on the FP32 pipe: Sylvester / Lyapunov with double-float
+diagonal blocks and FP64 divisions, Cholesky with an FP64 diagonal warp) with
+the CPU oracle, through the C ABI.
 
 Gate: ||X - X_oracle||_F / ||X_oracle||_F <= 1e-11 per instance, as for FP64;
 the mode's own bound, DF_TOL, is tighter (the split keeps about 48 bits of each
@@ -34,12 +35,11 @@ def run(op, pk, cfg=ss.CFG_DEFAULT, mode=DF, **kw):
 
 
 def test_df_configs_are_warp_specialised():
-    for op in (ss.OP_TRSYL, ss.OP_TRLYAP):
+    for op in (ss.OP_POTRF, ss.OP_TRSYL, ss.OP_TRLYAP):
         cnt = ss.ss_config_count(op, DF)
         assert cnt >= 1
         for c in range(cnt):
             assert ss.ss_config_describe(op, DF, c)[2] == 4
-    assert ss.ss_config_count(ss.OP_POTRF, DF) == 0
 
 
 @pytest.mark.parametrize("op", ["trsyl", "trlyap"])
@@ -170,3 +170,81 @@ def test_df_error_against_fp64_on_the_same_batch():
     assert e64.max() <= 1e-13
     assert edf.max() <= DF_TOL
     assert edf.max() <= TOL
+
+
+# ------------------------------------------------------------------ Cholesky
+
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_df_potrf_every_config_edge_sizes(cfg):
+    n = np.array(EDGE_SIZES, dtype=np.int32)
+    pk = inputs.make_batch("potrf", n, seed=120 + cfg)
+    x, info = run("potrf", pk, cfg=cfg)
+    ref, rinfo = oracle_batch("potrf", pk)
+    assert np.array_equal(info, rinfo)
+    errs = assert_parity("potrf", pk, x, ref, sentinel=SENT)
+    assert errs.max() <= DF_TOL, f"max rel err {errs.max():.3e}"
+
+
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_df_potrf_queue_in_place_and_failures(cfg):
+    n = inputs.sizes_uniform(1100, 1, 160, seed=121)
+    pk = inputs.make_batch("potrf", n, seed=122)
+    ref, rinfo = oracle_batch("potrf", pk)
+    x, info = run("potrf", pk, cfg=cfg)
+    assert np.array_equal(info, rinfo)
+    errs = assert_parity("potrf", pk, x, ref, sentinel=SENT)
+    assert errs.max() <= DF_TOL
+    from paper_1906_08613_gb300.device import DeviceBatch
+    sub = inputs.make_batch("potrf", n[:64], seed=123)
+    ref2, _ = oracle_batch("potrf", sub)
+    db = DeviceBatch(sub.n, sub.off, sub.ops, "potrf", alias_rhs=True)
+    db.solve(mode=DF, cfg=cfg)
+    torch.cuda.synchronize()
+    assert np.all(db.info_host() == 0)
+    assert_parity("potrf", sub, db.x_host(), ref2)
+    # Leading minors that are not positive: info = their order, the columns
+    # before the failing pivot as the oracle's.
+    m = np.array([12, 40, 70, 9], dtype=np.int32)
+    pk = inputs.make_batch("potrf", m, seed=124 + cfg)
+    fails = {0: 5, 1: 30, 2: 66}
+    for b, k in fails.items():
+        pk.view("A", b)[k, k] = -1.0
+    ref, rinfo = oracle_batch("potrf", pk)
+    x, info = run("potrf", pk, cfg=cfg)
+    assert np.array_equal(info, rinfo)
+    for b in range(pk.batch):
+        nb, o = int(m[b]), int(pk.off[b])
+        g = x[o:o + nb * nb].reshape(nb, nb, order="F")
+        r = ref[o:o + nb * nb].reshape(nb, nb, order="F")
+        good = fails.get(b, nb)
+        gu, ru = np.triu(g[:, :good]), np.triu(r[:, :good])
+        assert np.linalg.norm(gu - ru) <= DF_TOL * max(np.linalg.norm(ru), 1e-300)
+
+
+@pytest.mark.parametrize("name", ["potrf_1024x64", "potrf_8192xLU8-256"])
+def test_df_potrf_full_workloads(name):
+    pk = inputs.make_workload(name, seed=1234)
+    x, info = run("potrf", pk)
+    ref, rinfo = oracle_batch("potrf", pk, threads=16)
+    assert np.all(info == 0) and np.all(rinfo == 0)
+    errs = assert_parity("potrf", pk, x, ref, sentinel=SENT)
+    assert errs.max() <= DF_TOL, f"max rel err {errs.max():.3e}"
+
+
+def test_df_posv_factor_stage():
+    from paper_1906_08613_gb300.device import DevicePosvBatch
+    n = inputs.sizes_uniform(300, 1, 140, seed=125)
+    k = inputs.sizes_uniform(300, 1, 40, seed=126)
+    pk = inputs.posv_batch(n, k, seed=127)
+    xr, rr, rinfo = oracle.solve_posv_packed(pk)
+    for cfg in range(ss.ss_config_count(ss.OP_POTRF, DF)):
+        db = DevicePosvBatch(pk, x_fill=SENT)
+        db.solve(mode=DF, cfg=cfg)
+        torch.cuda.synchronize()
+        assert np.array_equal(db.info_host(), rinfo)
+        x = db.x_host()
+        for b in range(pk.batch):
+            o, c = int(pk.offB[b]), int(pk.n[b]) * int(pk.k[b])
+            r = xr[o:o + c]
+            err = np.linalg.norm(x[o:o + c] - r) / max(np.linalg.norm(r), 1e-300)
+            assert err <= DF_TOL, (cfg, b, err)

@@ -20,7 +20,8 @@ WEIGHTS = os.path.join(DATA, "selector_gb300")
 
 def test_features_and_bins():
     f = sel.features("trlyap", 128, 2048, "bf16_refined")
-    assert list(f[:3]) == [0, 0, 1] and list(f[5:]) == [0, 0, 0, 1]
+    assert list(f[:3]) == [0, 0, 1] and list(f[5:]) == [0, 0, 0, 1, 0]
+    assert list(sel.features("potrf", 8, 64, "df")[5:]) == [0, 0, 0, 0, 1]
     assert math.isclose(f[3], 7 / 9, rel_tol=1e-6) and math.isclose(f[4], 11 / 14, rel_tol=1e-6)
     assert tune.bin_range(7) == (65, 128) and tune.bin_range(0) == (1, 1)
     for n in (1, 2, 3, 64, 65, 128, 129, 4096):
