@@ -21,7 +21,8 @@ def test_two_threads_two_streams():
     from paper_1906_08613_gb300.device import DeviceBatch
     jobs = []
     for k, (op, mode) in enumerate((("trsyl", ss.MODE_FP64), ("trlyap", ss.MODE_AUTO),
-                                    ("potrf", ss.MODE_FP32_REFINED), ("trsyl", ss.MODE_AUTO))):
+                                    ("potrf", ss.MODE_FP32_REFINED), ("trsyl", ss.MODE_AUTO),
+                                    ("trlyap", ss.MODE_DF), ("potrf", ss.MODE_DF))):
         n = inputs.sizes_uniform(200, 1, 150, seed=90 + k)
         pk = inputs.make_batch(op, n, seed=90 + k)
         ref, rinfo = oracle_batch(op, pk)

@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("op,mode", [("trsyl", ss.MODE_FP64), ("potrf", ss.MODE_FP32_REFINED),
-                                     ("trlyap", ss.MODE_AUTO)])
+                                     ("trlyap", ss.MODE_AUTO), ("trsyl", ss.MODE_DF), ("potrf", ss.MODE_DF)])
 def test_graph_capture_and_replay(op, mode):
     from paper_1906_08613_gb300.device import DeviceBatch
     n = inputs.sizes_uniform(150, 1, 140, seed=51)

@@ -53,7 +53,7 @@ def work(op, batch, max_n, mode=ss.MODE_FP64):
 SIZES = [1, 7, 16, 17, 40, 70]
 
 
-@pytest.mark.parametrize("mode", [ss.MODE_FP64, ss.MODE_FP32_REFINED])
+@pytest.mark.parametrize("mode", [ss.MODE_FP64, ss.MODE_FP32_REFINED, ss.MODE_DF])
 def test_padded_ld_sylvester_lyapunov_cholesky(mode):
     dev = torch.device("cuda")
     rng = np.random.default_rng(11)
@@ -77,7 +77,7 @@ def test_padded_ld_sylvester_lyapunov_cholesky(mode):
     # Lyapunov (FP64: X in place of S; refined modes need X separate)
     ll, ss_, _ = zip(*[inputs.lyapunov_instance(int(k), 13, b) for b, k in enumerate(n)])
     Lb = padded(ll, pads(), dev); S = padded(ss_, pads(), dev)
-    Xl = S if mode == ss.MODE_FP64 else padded([np.zeros((k, k)) for k in n], pads(), dev)
+    Xl = S if mode in (ss.MODE_FP64, ss.MODE_DF) else padded([np.zeros((k, k)) for k in n], pads(), dev)
     w = work(ss.OP_TRLYAP, len(n), int(n.max()), mode)
     ss.trlyap_l(len(n), int(n.max()), dn.data_ptr(), Lb[1].data_ptr(), Lb[2].data_ptr(), S[1].data_ptr(),
                 S[2].data_ptr(), Xl[1].data_ptr(), Xl[2].data_ptr(), info.data_ptr(), mode=mode,
@@ -102,7 +102,8 @@ def test_padded_ld_sylvester_lyapunov_cholesky(mode):
         assert np.linalg.norm(np.triu(x) - ref) <= TOL * np.linalg.norm(ref) and np.all(pad == PAD_FILL)
 
 
-def test_padded_ld_rect_and_posv():
+@pytest.mark.parametrize("mode", [ss.MODE_FP64, ss.MODE_DF])
+def test_padded_ld_rect_and_posv(mode):
     dev = torch.device("cuda")
     rng = np.random.default_rng(12)
     m = np.array([1, 20, 33, 5, 64], dtype=np.int32)
@@ -116,7 +117,7 @@ def test_padded_ld_rect_and_posv():
     w = work(ss.OP_TRSYL, len(m), int(max(m.max(), n.max())))
     ss.trsyl_rect(len(m), int(m.max()), int(n.max()), dm.data_ptr(), dn.data_ptr(), L[1].data_ptr(), L[2].data_ptr(),
                   U[1].data_ptr(), U[2].data_ptr(), C[1].data_ptr(), C[2].data_ptr(), X[1].data_ptr(), X[2].data_ptr(),
-                  info.data_ptr(), d_work=w.data_ptr(), work_bytes=int(w.numel()))
+                  info.data_ptr(), mode=mode, d_work=w.data_ptr(), work_bytes=int(w.numel()))
     torch.cuda.synchronize()
     assert np.all(info.cpu().numpy() == 0)
     for (x, pad), l, u, c in zip(unpack(X[0], X[3], X[4], list(zip(m, n))), ls, us, cs):
@@ -131,7 +132,7 @@ def test_padded_ld_rect_and_posv():
     w = work(ss.OP_POTRF, len(nn), int(nn.max()))
     ss.posv_upper(len(nn), int(nn.max()), int(k.max()), dnn.data_ptr(), dk.data_ptr(), A[1].data_ptr(), A[2].data_ptr(),
                   R[1].data_ptr(), R[2].data_ptr(), B[1].data_ptr(), B[2].data_ptr(), Xp[1].data_ptr(), Xp[2].data_ptr(),
-                  info.data_ptr(), d_work=w.data_ptr(), work_bytes=int(w.numel()))
+                  info.data_ptr(), mode=mode, d_work=w.data_ptr(), work_bytes=int(w.numel()))
     torch.cuda.synchronize()
     assert np.all(info.cpu().numpy() == 0)
     for (x, pad), a, b in zip(unpack(Xp[0], Xp[3], Xp[4], list(zip(nn, k))), aa, bb):
@@ -145,7 +146,8 @@ def test_refined_modes_reject_in_place_raw_and_fp64_accept(op):
     n = np.array([5, 33, 70], dtype=np.int32)
     pk = inputs.make_batch(op, n, seed=17)
     rhs = {"potrf": "A", "trsyl": "C", "trlyap": "S"}[op]
-    for mode, want in ((ss.MODE_FP32_REFINED, ss.INFO_ALIASED), (ss.MODE_FP32_RAW, 0), (ss.MODE_FP64, 0)):
+    for mode, want in ((ss.MODE_FP32_REFINED, ss.INFO_ALIASED), (ss.MODE_FP32_RAW, 0), (ss.MODE_FP64, 0),
+                       (ss.MODE_DF, 0)):
         db = DeviceBatch(pk.n, pk.off, pk.ops, op, alias_rhs=True)
         db.ensure_work(mode)
         db.solve(mode=mode)
