@@ -52,7 +52,8 @@
  * diagonal-block recurrences in double-float; the divisors l_ii + u_jj and
  * their reciprocals are computed in FP64; X is rounded to FP64.  potrf_upper,
  * posv_upper (factor stage): T = A - sum X^T X in double-float; the diagonal
- * blocks (square roots, pivots, panel solves) stay FP64.  No refinement and no
+ * blocks (square roots, pivots, panel solves) stay FP64; posv_upper's
+ * triangular solves likewise.  No refinement and no
  * workspace beyond FP64's.  Accuracy is that of FP64 up to the split's 2^-47
  * relative representation error per operand.  Values must lie in FP32's
  * normal range (magnitude about 1.2e-38 to 3.4e38); outside it the split
@@ -194,9 +195,9 @@ int trsyl_rect(int batch, int max_m, int max_n, const int *d_m, const int *d_n,
  * <= SS_MAX_N and 0 <= k <= max_k.  info: 0 success; j > 0 the factor's
  * pivot j failed (X untouched); SS_INFO_BAD_SIZE for n or k out of range (X
  * untouched; for a bad k, R is computed).  mode must be SS_MODE_FP64 or
- * SS_MODE_DF (the factor stage's mode; the triangular solves are FP64; other
- * modes return -15); cfg selects the Cholesky configuration (as for
- * potrf_upper in that mode).  Workspace: the size ss_workspace_size(SS_OP_POTRF, batch,
+ * SS_MODE_DF (in DF the factor's and the triangular solves' block updates are
+ * double-float, their diagonal blocks FP64; other modes return -15); cfg
+ * selects the Cholesky configuration (as for potrf_upper in that mode).  Workspace: the size ss_workspace_size(SS_OP_POTRF, batch,
  * max_n, SS_MODE_FP64, ...) reports.  Two launches after the pre-pass: the
  * factor, then the solves, ordered on `stream`.
  */

@@ -458,7 +458,7 @@ int posv_upper(int batch, int max_n, int max_k, const int *d_n, const int *d_k, 
     Sched s;
     carve_workspace(d_work, batch, max_n, mode, &s);
     cudaError_t e = launch_posv_solve(d_n, d_k, max_k, d_R, d_ldr, d_B, d_ldb, d_X, d_ldx, d_info, s,
-                                      MAX_GROUPS - 1, batch, static_cast<cudaStream_t>(stream));
+                                      MAX_GROUPS - 1, batch, static_cast<cudaStream_t>(stream), mode == SS_MODE_DF);
     if (e != cudaSuccess) return SS_ERR_CUDA;
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return 0;

@@ -16,6 +16,7 @@
 // column, the column's B entries in registers: x_i = t_i / r_ii, then every
 // later entry of the column subtracts its r * x_i at once, so the dependent
 // chain is one multiply and one FMA per row.
+#include "df.cuh"
 #include "ss_internal.h"
 #include "ss_device.cuh"
 
@@ -53,9 +54,25 @@ __device__ __forceinline__ void stage(double *S, const double *G, long ld, int r
     }
 }
 
+// The same staging as double-float pairs (a float2 slot has the size of a
+// double, so the tile layout is unchanged).
+template <int R, int C, int LDS, int T>
+__device__ __forceinline__ void stage_df(float2 *S, const double *G, long ld, int rows, int cols)
+{
+#pragma unroll 4
+    for (int e = threadIdx.x; e < R * C; e += T) {
+        const int r = e % R, c = e / R;
+        float2 v = make_float2(0.f, 0.f);
+        if (r < rows && c < cols) split_df(G[r + (long)c * ld], v.x, v.y);
+        S[r + c * LDS] = v;
+    }
+}
+
 // CW: right-hand-side columns per chunk (16 or 32; the kernel picks 16 when
-// k <= 16 so that no update multiplies padding columns).
-template <int BS, int T, int CW>
+// k <= 16 so that no update multiplies padding columns).  DF (SS_MODE_DF):
+// the block updates in double-float arithmetic on the FP32 pipe, T rounded
+// to FP64 for the FP64 diagonal solve.
+template <int BS, int T, int CW, bool DF>
 __device__ void posv_instance(int n, int k, const double *R, long ldr, const double *Bm, long ldb, double *X,
                               long ldx, double *sm)
 {
@@ -76,34 +93,61 @@ __device__ void posv_instance(int n, int k, const double *R, long ldr, const dou
                 const int I = fwd ? q : nb - 1 - q;
                 const int i0 = I * BS, mI = min(BS, n - i0);
                 double acc[E];
+                float ah[E], al[E];
                 const double *src = fwd ? Bm : X;
                 const long lds = fwd ? ldb : ldx;
 #pragma unroll
                 for (int r = 0; r < E; ++r) {
                     const int e = threadIdx.x + T * r, row = e % BS, col = e / BS;
                     acc[r] = (row < mI && col < kc) ? src[(i0 + row) + (long)(c0 + col) * lds] : 0.0;
+                    if constexpr (DF) split_df(acc[r], ah[r], al[r]);
                 }
                 const int K0 = fwd ? 0 : I + 1, K1 = fwd ? I : nb;
                 for (int K = K0; K < K1; ++K) {
                     const int k0 = K * BS, mK = min(BS, n - k0);
                     __syncthreads();
-                    if (fwd) stage<BS, BS, LDR, T>(sR, R + k0 + (long)i0 * ldr, ldr, mK, mI);   // R_KI
-                    else     stage<BS, BS, LDR, T>(sR, R + i0 + (long)k0 * ldr, ldr, mI, mK);   // R_IK
-                    stage<BS, CW, LDK, T>(sY, X + k0 + (long)c0 * ldx, ldx, mK, kc);           // Y_K / X_K
+                    if constexpr (DF) {
+                        float2 *dR = reinterpret_cast<float2 *>(sR), *dY = reinterpret_cast<float2 *>(sY);
+                        if (fwd) stage_df<BS, BS, LDR, T>(dR, R + k0 + (long)i0 * ldr, ldr, mK, mI);
+                        else     stage_df<BS, BS, LDR, T>(dR, R + i0 + (long)k0 * ldr, ldr, mI, mK);
+                        stage_df<BS, CW, LDK, T>(dY, X + k0 + (long)c0 * ldx, ldx, mK, kc);
+                    } else {
+                        if (fwd) stage<BS, BS, LDR, T>(sR, R + k0 + (long)i0 * ldr, ldr, mK, mI);   // R_KI
+                        else     stage<BS, BS, LDR, T>(sR, R + i0 + (long)k0 * ldr, ldr, mI, mK);   // R_IK
+                        stage<BS, CW, LDK, T>(sY, X + k0 + (long)c0 * ldx, ldx, mK, kc);           // Y_K / X_K
+                    }
                     __syncthreads();
 #pragma unroll
                     for (int r = 0; r < E; ++r) {
                         const int e = threadIdx.x + T * r, row = e % BS, col = e / BS;
                         if (col >= kc) continue;    // whole half-warps of padding columns skip
-                        double s = acc[r];
+                        if constexpr (DF) {
+                            const float2 *dR = reinterpret_cast<const float2 *>(sR);
+                            const float2 *dY = reinterpret_cast<const float2 *>(sY);
+                            float h = ah[r], l = al[r];
 #pragma unroll 4
-                        for (int t = 0; t < mK; ++t) {
-                            // forward: (R_KI^T)(row, t) = R_KI(t, row); backward: R_IK(row, t)
-                            const double a = fwd ? sR[t + row * LDR] : sR[row + t * LDR];
-                            s = fma(-a, sY[t + col * LDK], s);
+                            for (int t = 0; t < mK; ++t) {
+                                const float2 a = fwd ? dR[t + row * LDR] : dR[row + t * LDR];
+                                const float2 y = dY[t + col * LDK];
+                                df_msub(h, l, a.x, a.y, y.x, y.y);
+                            }
+                            ah[r] = h;
+                            al[r] = l;
+                        } else {
+                            double s = acc[r];
+#pragma unroll 4
+                            for (int t = 0; t < mK; ++t) {
+                                // forward: (R_KI^T)(row, t) = R_KI(t, row); backward: R_IK(row, t)
+                                const double a = fwd ? sR[t + row * LDR] : sR[row + t * LDR];
+                                s = fma(-a, sY[t + col * LDK], s);
+                            }
+                            acc[r] = s;
                         }
-                        acc[r] = s;
                     }
+                }
+                if constexpr (DF) {
+#pragma unroll
+                    for (int r = 0; r < E; ++r) acc[r] = df_to_double(ah[r], al[r]);
                 }
                 __syncthreads();
                 stage<BS, BS, LDR, T>(sD, R + i0 + (long)i0 * ldr, ldr, mI, mI);
@@ -152,7 +196,7 @@ __device__ void posv_instance(int n, int k, const double *R, long ldr, const dou
     }
 }
 
-template <int CW>
+template <int CW, bool DF>
 __global__ void __launch_bounds__(128) posv_kernel(PosvOps o, Sched s, int group)
 {
     constexpr int BS = 16, T = 128;
@@ -171,7 +215,7 @@ __global__ void __launch_bounds__(128) posv_kernel(PosvOps o, Sched s, int group
             continue;
         }
         if (n == 0 || k == 0) continue;
-        posv_instance<BS, T, CW>(n, k, o.R[b], o.ldr[b], o.B[b], o.ldb[b], o.X[b], o.ldx[b], sm);
+        posv_instance<BS, T, CW, DF>(n, k, o.R[b], o.ldr[b], o.B[b], o.ldb[b], o.X[b], o.ldx[b], sm);
     }
 }
 
@@ -180,11 +224,12 @@ __global__ void __launch_bounds__(128) posv_kernel(PosvOps o, Sched s, int group
 // The solve stage on the queue head `group` over all valid instances.
 cudaError_t launch_posv_solve(const int *d_n, const int *d_k, int max_k, const double *const *d_R, const int *d_ldr,
                               const double *const *d_B, const int *d_ldb, double *const *d_X, const int *d_ldx,
-                              int *d_info, const Sched &s, int group, int batch, cudaStream_t st)
+                              int *d_info, const Sched &s, int group, int batch, cudaStream_t st, bool df)
 {
     constexpr int BS = 16, T = 128;
     const size_t smem = (size_t)(2 * BS * (BS + 1) + 2 * KC * (BS + 1) + BS) * sizeof(double);
-    auto kernel = max_k <= 16 ? posv_kernel<16> : posv_kernel<KC>;
+    auto kernel = max_k <= 16 ? (df ? posv_kernel<16, true> : posv_kernel<16, false>)
+                              : (df ? posv_kernel<KC, true> : posv_kernel<KC, false>);
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;

@@ -97,10 +97,11 @@ cudaError_t launch_potrf_ws(int block, int nu, bool df, const Operands &o, const
                             cudaStream_t st);
 
 // Solve stage of the SPD solve (R^T Y = B, R X = Y) over the valid instances
-// of a binning pass, on queue head `group`.
+// of a binning pass, on queue head `group`; df: double-float block updates
+// (SS_MODE_DF), the diagonal solves FP64.
 cudaError_t launch_posv_solve(const int *d_n, const int *d_k, int max_k, const double *const *d_R, const int *d_ldr,
                               const double *const *d_B, const int *d_ldb, double *const *d_X, const int *d_ldx,
-                              int *d_info, const Sched &s, int group, int batch, cudaStream_t st);
+                              int *d_info, const Sched &s, int group, int batch, cudaStream_t st, bool df);
 
 // Number of SMs of the current device (cached per device).
 int sm_count();

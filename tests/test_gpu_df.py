@@ -231,10 +231,12 @@ def test_df_potrf_full_workloads(name):
     assert errs.max() <= DF_TOL, f"max rel err {errs.max():.3e}"
 
 
-def test_df_posv_factor_stage():
+@pytest.mark.parametrize("kmax", [16, 40])
+def test_df_posv_factor_and_solves(kmax):
+    # k <= 16 and k up to 40 take the 16- and 32-column chunk kernels.
     from paper_1906_08613_gb300.device import DevicePosvBatch
-    n = inputs.sizes_uniform(300, 1, 140, seed=125)
-    k = inputs.sizes_uniform(300, 1, 40, seed=126)
+    n = inputs.sizes_uniform(300, 1, 140, seed=125 + kmax)
+    k = inputs.sizes_uniform(300, 1, kmax, seed=126)
     pk = inputs.posv_batch(n, k, seed=127)
     xr, rr, rinfo = oracle.solve_posv_packed(pk)
     for cfg in range(ss.ss_config_count(ss.OP_POTRF, DF)):
