@@ -97,10 +97,13 @@ __device__ void warp_diag_solve(const double *sL, const double *sU, double *sT, 
     for (int d = 0; d <= m + nn - 2; ++d) {
         const int ilo = SYM ? max((d + 1) / 2, d - nn + 1) : max(0, d - nn + 1), ihi = min(d, m - 1);
         const int cnt = ihi - ilo + 1;
-        int split = cnt >= 32 ? 1 : pow2_floor(32 / cnt);
+        // split = min(pow2_floor(32 / cnt), pow2_floor(d)), a power of two:
+        // shifts and masks instead of divisions on the dependent chain.
+        int split = cnt >= 32 ? 1 : (32 >> ceil_log2(cnt));
         const int byLen = pow2_floor(d > 1 ? d : 1);
         split = split < byLen ? split : byLen;
-        const int idx = lane / split, part = lane % split;
+        const int lg = 31 - __clz(split);
+        const int idx = lane >> lg, part = lane & (split - 1);
         const bool act = idx < cnt;
         const int i = ilo + (act ? idx : 0), j = d - i;
         double s0 = 0.0, s1 = 0.0;
@@ -142,10 +145,13 @@ __device__ void warp_diag_solve_df(const float2 *sLU, float2 *sT, const float2 *
     for (int d = 0; d <= m + nn - 2; ++d) {
         const int ilo = SYM ? max((d + 1) / 2, d - nn + 1) : max(0, d - nn + 1), ihi = min(d, m - 1);
         const int cnt = ihi - ilo + 1;
-        int split = cnt >= 32 ? 1 : pow2_floor(32 / cnt);
+        // split = min(pow2_floor(32 / cnt), pow2_floor(d)), a power of two:
+        // shifts and masks instead of divisions on the dependent chain.
+        int split = cnt >= 32 ? 1 : (32 >> ceil_log2(cnt));
         const int byLen = pow2_floor(d > 1 ? d : 1);
         split = split < byLen ? split : byLen;
-        const int idx = lane / split, part = lane % split;
+        const int lg = 31 - __clz(split);
+        const int idx = lane >> lg, part = lane & (split - 1);
         const bool act = idx < cnt;
         const int i = ilo + (act ? idx : 0), j = d - i;
         float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;

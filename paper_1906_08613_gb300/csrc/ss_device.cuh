@@ -130,6 +130,12 @@ __device__ __forceinline__ int pow2_floor(int x)
     return x <= 1 ? 1 : (1 << (31 - __clz(x)));
 }
 
+// Smallest k with 2^k >= x (x >= 1).
+__device__ __forceinline__ int ceil_log2(int x)
+{
+    return x <= 1 ? 0 : 32 - __clz(x - 1);
+}
+
 // Lanes per dot product when `cnt` dot products of length about `len` share T
 // threads: a power of two, at most 32, at most T/cnt, and small enough that
 // each lane still does about four terms.
