@@ -185,6 +185,13 @@ def load(path):
         return json.load(f)
 
 
+def merge_entries(old, new):
+    """The entries of `old` whose (op, bin, batch, mode) the sweep `new` did not
+    measure, followed by all of `new`."""
+    swept = {(e["op"], e["bin"], e["batch"], e["mode"]) for e in new}
+    return [e for e in old if (e["op"], e["bin"], e["batch"], e["mode"]) not in swept] + list(new)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", required=True)
@@ -207,9 +214,7 @@ def main(argv=None):
     extra = {"sweep_seconds": time.time() - t0}
     if args.merge:
         old = load(args.merge)
-        swept = {(e["op"], e["bin"], e["batch"], e["mode"]) for e in entries}
-        kept = [e for e in old["entries"] if (e["op"], e["bin"], e["batch"], e["mode"]) not in swept]
-        entries = kept + entries
+        entries = merge_entries(old["entries"], entries)
         what = f"{','.join(modes)} x {','.join(ops)}, bins >= {args.min_bin}" + (f", batches {args.batches}" if batches else "")
         extra["note"] = f"{old.get('note', '')}; swept {what} on {time.strftime('%Y-%m-%d')}".lstrip("; ")
     save(entries, args.out, extra)

@@ -112,3 +112,67 @@ def test_split_holds_out_every_third_cell_with_trained_neighbours():
     for op, k, b in held:
         assert any(t[0] == op and abs(t[1] - k) == 1 for t in train)
         assert any(t[0] == op and t[1] == k and t[2] != b for t in train)
+
+
+def test_tuner_merge_replaces_only_swept_buckets():
+    old = [dict(op="trsyl", bin=8, batch=256, mode="fp64", cfg=0, ms=1.0),
+           dict(op="trsyl", bin=8, batch=256, mode="df", cfg=0, ms=2.0),
+           dict(op="trsyl", bin=8, batch=1024, mode="df", cfg=0, ms=9.0),
+           dict(op="potrf", bin=8, batch=1024, mode="df", cfg=0, ms=3.0)]
+    new = [dict(op="trsyl", bin=8, batch=1024, mode="df", cfg=0, ms=4.0),
+           dict(op="trsyl", bin=8, batch=1024, mode="df", cfg=1, ms=5.0)]
+    got = tune.merge_entries(old, new)
+    keys = [(e["op"], e["bin"], e["batch"], e["mode"], e["cfg"], e["ms"]) for e in got]
+    assert ("trsyl", 8, 1024, "df", 0, 9.0) not in keys          # replaced
+    assert ("trsyl", 8, 1024, "df", 0, 4.0) in keys and ("trsyl", 8, 1024, "df", 1, 5.0) in keys
+    assert ("trsyl", 8, 256, "df", 0, 2.0) in keys and ("potrf", 8, 1024, "df", 0, 3.0) in keys
+    assert len(got) == 5
+
+
+def test_trained_batch_max_per_size_bin_and_mode():
+    ent = [dict(op="trsyl", bin=8, batch=b, mode=m, cfg=0, ms=1.0, info_nonzero=0)
+           for b, m in ((64, "fp64"), (256, "fp64"), (1024, "fp64"), (64, "df"), (256, "df"))]
+    X, _, _, _ = sel.dataset(ent)
+    bm = sel.trained_batch_max(X)
+    assert bm == {"trsyl:8:fp64": 1024, "trsyl:8:df": 256}
+
+
+class _FixedSelector(sel.Selector):
+    """Predictions from a table instead of the network (log2 ms per mode)."""
+
+    def __init__(self, table):
+        super().__init__()
+        self.table = table
+
+    def predict(self, X):
+        out = np.zeros((len(X), ss.MLP_OUT), dtype=np.float32)
+        for i, x in enumerate(np.asarray(X)):
+            mode = sel.MODE_ORDER[int(np.argmax(x[5:5 + len(sel.MODE_ORDER)]))]
+            batch = 2.0 ** (float(x[4]) * 14.0)
+            out[i, :] = self.table[mode](batch)
+        return out
+
+
+def test_selector_scales_predictions_beyond_the_trained_batch():
+    # In bin 8 the network saw DF only up to 256 instances and FP64 up to
+    # 1024.  Its DF prediction flattens out beyond 256 (a latency-bound time
+    # carried into the throughput-bound regime); with batch_max the DF
+    # prediction is taken at 256 and scaled by count / 256 instead.
+    table = {"fp64": lambda b: math.log2(2.0 + 0.008 * b),
+             "df": lambda b: math.log2(3.0 if b <= 256 else 3.0 + 0.0001 * b)}
+    s = _FixedSelector(table)
+    s.cfg_counts = {"trsyl:fp64": 1, "trsyl:df": 1}
+    counts = [0] * ss.NUM_BINS
+    counts[8] = 200
+    assert s.call_choice("trsyl", counts)[0] == "df"                # 3.0 ms vs 3.6 ms
+    counts[8] = 1024
+    assert s.call_choice("trsyl", counts)[0] == "df"                # unscaled: 3.1 ms vs 10.2 ms
+    s.batch_max = {"trsyl:8:fp64": 1024, "trsyl:8:df": 256}
+    mode, _, ms = s.call_choice("trsyl", counts)
+    assert mode == "fp64" and math.isclose(ms, 2.0 + 0.008 * 1024, rel_tol=1e-5)   # DF: 3 ms x 4 = 12 ms
+    # The per-bin choice applies the same rule.
+    modes, _ = s.auto_table("trsyl", counts)
+    assert modes[8] == ss.MODES["fp64"]
+    counts[8] = 200
+    modes, _ = s.auto_table("trsyl", counts)
+    assert modes[8] == ss.MODES["df"]
