@@ -1,5 +1,5 @@
-// FP64 triangular Sylvester (L X + X U = C) and Lyapunov (L X + X L^T = S)
-// with warp-specialised CTAs.
+// Triangular Sylvester (L X + X U = C), Lyapunov (L X + X L^T = S) and
+// Cholesky with warp-specialised CTAs, in FP64 or double-float arithmetic.
 //
 // The blocked lazy algorithm (the Bartels-Stewart back substitution of the
 // paper's triangular Sylvester and Lyapunov solves, done block by block)
@@ -26,6 +26,14 @@
 // warps wait once more after their last block), so the phases of a barrier
 // never overlap.  Barrier 1 synchronises the update warps' tile staging.
 // T and X of consecutive blocks alternate between two shared tiles.
+//
+// The same pipelines with double-float arithmetic (SS_MODE_DF, template flag
+// DF): the block updates run as TwoProduct / TwoSum updates on the FP32 pipe,
+// which on this GPU is 58 times wider than the FP64 pipe; for Sylvester /
+// Lyapunov the diagonal-block wavefront does too, on operands the update
+// warps prepare; divisions, square roots and pivots stay FP64.  The warp
+// roles, barriers and block order are the FP64 ones.  The warp-specialised
+// Cholesky (X^T X = A) follows the Sylvester kernel.
 #include <type_traits>
 
 #include "df.cuh"
@@ -786,6 +794,9 @@ __device__ void warp_trsm_ut(const double *sD, const double *sR, double *sT, int
     }
 }
 
+// DF: the update warps form T in double-float arithmetic (operands split on
+// staging, X_{I-1,J} split into the staging tile the last step leaves free)
+// and round it to FP64; the diagonal warp is the FP64 one.
 template <int B, int NU, bool DF>
 __device__ void chol_ws_instance(int n, const double *A, long lda, double *X, long ldx, int *info, double *sm)
 {

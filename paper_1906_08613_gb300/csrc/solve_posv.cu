@@ -1,5 +1,5 @@
 // Second stage of the SPD solve A X = B: with the upper Cholesky factor R
-// (R^T R = A, computed by the FP64 Cholesky kernels into R) solve
+// (R^T R = A, computed by the Cholesky kernels into R) solve
 //   R^T Y = B   (forward, row blocks I ascending),
 //   R X = Y     (backward, row blocks I descending),
 // for the k right-hand sides, Y held in X.  The paper names the Cholesky
@@ -15,7 +15,8 @@
 // block solve R_II^T Y_I = T (R_II X_I = T) is done by one warp, one lane per
 // column, the column's B entries in registers: x_i = t_i / r_ii, then every
 // later entry of the column subtracts its r * x_i at once, so the dependent
-// chain is one multiply and one FMA per row.
+// chain is one multiply and one FMA per row.  In SS_MODE_DF the block
+// products are double-float on the FP32 pipe; the diagonal solves stay FP64.
 #include "df.cuh"
 #include "ss_internal.h"
 #include "ss_device.cuh"
