@@ -7,7 +7,7 @@ model-based approach ("Limitations and future work" paragraph).  The network
 and its training run in the library's CUDA kernels (``ss_mlp_forward``,
 ``ss_mlp_grad``, ``ss_mlp_adam``); this module only encodes features, moves
 arrays and picks the argmin.  The exhaustive autotuner (``tune.py``) produces
-the training table, stays the fallback, and judges the selector's regret.
+the training table, stays the fallback, and is the yardstick of the selector's regret.
 
 Features (SS_MLP_IN = 10): op one-hot (potrf, trsyl, trlyap), log2(n)/9,
 log2(batch)/14, mode one-hot (fp64, fp32_refined, tf32_refined, bf16_refined,
