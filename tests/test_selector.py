@@ -176,3 +176,18 @@ def test_selector_scales_predictions_beyond_the_trained_batch():
     counts[8] = 200
     modes, _ = s.auto_table("trsyl", counts)
     assert modes[8] == ss.MODES["df"]
+
+
+def test_tuning_grid():
+    b = tune.default_buckets(9)
+    for op in tune.OPS:
+        for k in range(2, 10):
+            got = sorted(x[2] for x in b if x[0] == op and x[1] == k)
+            assert got == ([256, 2048] if k <= 7 else [64, 256, 1024])
+    # The committed database covers the grid for FP64 and DF.
+    entries = tune.load(DB)["entries"]
+    have = {(e["op"], e["bin"], e["batch"], e["mode"]) for e in entries}
+    for op, k, batch in b:
+        assert (op, k, batch, "fp64") in have
+        if op != "potrf" or ss.ss_config_count(ss.OP_POTRF, ss.MODE_DF) > 0:
+            assert (op, k, batch, "df") in have
