@@ -55,9 +55,29 @@
  * blocks (square roots, pivots, panel solves) stay FP64; posv_upper's
  * triangular solves likewise.  No refinement and no
  * workspace beyond FP64's.  Accuracy is that of FP64 up to the split's 2^-47
- * relative representation error per operand.  Values must lie in FP32's
- * normal range (magnitude about 1.2e-38 to 3.4e38); outside it the split
- * loses the double-float accuracy.
+ * relative representation error per operand.
+ *
+ * Magnitude.  The problems are plain double precision, so SS_MODE_DF and the
+ * refined modes, which compute in FP32 arithmetic, rescale an instance by
+ * powers of two where its data needs it (exact in binary floating point):
+ * L and U by 2^a and C by 2^c (X then carries 2^(c-a)), moving the largest
+ * entries of the operator and of the right-hand side to [1, 2) unless they
+ * already lie in [2^-12, 2^13); a Cholesky A by 4^s (X by 2^s) unless its
+ * largest entry lies in [2^-40, 2^41); for the SPD solve also B.  Data of any
+ * FP64 magnitude is thus solved to the same accuracy; entries more than
+ * 2^126 below the largest of their operand count as zero (a perturbation
+ * below 2^-126 of the operand's norm).  In SS_MODE_DF the largest entries of
+ * a Sylvester / Lyapunov instance come from a pre-pass over the batch (one
+ * launch more, reading the operands once); a Cholesky A is checked as the
+ * factorisation reads it, and an instance outside the band is factored again
+ * rescaled (as is, after a scan, every instance factored in place, X == A).
+ * A Sylvester / Lyapunov instance whose rescaled solution reaches 2^60 (a
+ * solution at least 2^60 times larger than its data) or holds Inf / NaN has
+ * left the double-float range: a last launch of the group solves it again in
+ * SS_MODE_FP64 from its right-hand side, or, when X overwrote that
+ * right-hand side (X == C or X == S), sets info = SS_INFO_RANGE.  In the
+ * refined modes such an instance ends as a refinement that did not converge
+ * (info n + 1).
  *
  * SS_MODE_AUTO solves each size bin in the (mode, cfg) pair given by
  * ss_set_auto_table (the autotuner's or the learned selector's choice among
@@ -85,7 +105,10 @@
  *                      SS_REFINE_MAXIT steps; X holds the last iterate;
  *   SS_INFO_BAD_SIZE   d_n[b] < 0 or d_n[b] > max_n; X untouched;
  *   SS_INFO_NO_WORK    the workspace was too small for this instance;
- *   SS_INFO_ALIASED    (refined modes) X aliases the right-hand side; X untouched.
+ *   SS_INFO_ALIASED    (refined modes) X aliases the right-hand side; X untouched;
+ *   SS_INFO_RANGE      (SS_MODE_DF, trsyl / trlyap / trsyl_rect, X == C or
+ *                      X == S) the solution left the double-float range (see
+ *                      Magnitude); X is undefined: solve again in SS_MODE_FP64.
  *
  * Streams.  `stream` is a cudaStream_t (NULL: the legacy default stream).
  * Every call is asynchronous with respect to the host.  When a call uses
@@ -133,6 +156,13 @@ extern "C" {
 #define SS_INFO_BAD_SIZE  (-1)
 #define SS_INFO_NO_WORK   (-2)
 #define SS_INFO_ALIASED   (-3)
+#define SS_INFO_RANGE     (-4)
+
+#define SS_ERR_IO          (-102)
+#define SS_ERR_NO_SELECTOR (-103)
+
+/* size bins of the configuration tables: bin(n) = ceil(log2(max(n, 1))) */
+#define SS_NUM_BINS 13
 
 #define SS_REFINE_MAXIT 10
 #define SS_REFINE_TOL   1e-13
@@ -172,7 +202,7 @@ int trsyl_lu(int batch, int max_n, const int *d_n,
  * magnitude of L and U, or is NaN.  Instances are scheduled longest-first by
  * max(m, n).  mode must be SS_MODE_FP64 or SS_MODE_DF (other modes return -15); cfg as for
  * trsyl_lu (the Sylvester configurations and tables).  Workspace: the size
- * ss_workspace_size(SS_OP_TRSYL, batch, max(max_m, max_n), SS_MODE_FP64, ...)
+ * ss_workspace_size(SS_OP_TRSYL, batch, max(max_m, max_n), mode, ...)
  * reports.
  */
 int trsyl_rect(int batch, int max_m, int max_n, const int *d_m, const int *d_n,
@@ -197,9 +227,10 @@ int trsyl_rect(int batch, int max_m, int max_n, const int *d_m, const int *d_n,
  * untouched; for a bad k, R is computed).  mode must be SS_MODE_FP64 or
  * SS_MODE_DF (in DF the factor's and the triangular solves' block updates are
  * double-float, their diagonal blocks FP64; other modes return -15); cfg
- * selects the Cholesky configuration (as for potrf_upper in that mode).  Workspace: the size ss_workspace_size(SS_OP_POTRF, batch,
- * max_n, SS_MODE_FP64, ...) reports.  Two launches after the pre-pass: the
- * factor, then the solves, ordered on `stream`.
+ * selects the Cholesky configuration (as for potrf_upper in that mode).
+ * Workspace: the size ss_workspace_size(SS_OP_POTRF, batch, max_n, mode, ...)
+ * reports.  After the pre-passes, two launches: the factor, then the solves,
+ * ordered on `stream`.
  */
 int posv_upper(int batch, int max_n, int max_k, const int *d_n, const int *d_k,
                const double *const *d_A, const int *d_lda,
@@ -251,7 +282,7 @@ int ss_set_config_table(int op, int mode, int nbins, const int *cfg_by_bin);
  * SS_MODE_FP64 with SS_CFG_DEFAULT, minus d_work/work_bytes: the scratch is a
  * fixed 1 MiB area in the library's own device memory, held on every device
  * that loads the library until the process exits.  That is enough for any
- * batch up to 262016 instances (any max_n); a larger batch returns
+ * batch up to 261952 instances (any max_n); a larger batch returns
  * SS_ERR_SCRATCH_LIMIT before anything is launched.  The first call on each
  * device looks the area's address up (cudaGetSymbolAddress) with that device
  * current, so make it before any stream capture.  All calls share the area:
@@ -302,6 +333,93 @@ int ss_mlp_grad(const float *d_params, int nrows, const float *d_x, const float 
                 void *d_work, size_t work_bytes, void *stream);
 int ss_mlp_adam(float *d_params, const float *d_grad, float *d_m, float *d_v, int step, float lr,
                 float beta1, float beta2, float eps, void *stream);
+
+/*
+ * The autotuner (the paper's search loop over algorithm variants and
+ * implementation parameters, "Generator structure" paragraph) on one batch:
+ * every configuration of `mode` (0 <= cfg < ss_config_count(op, mode)) is
+ * run once to warm up and then `reps` times, each call timed with CUDA
+ * events on `stream`; h_ms[cfg] gets the median milliseconds, h_bad[cfg]
+ * (may be NULL) the number of instances whose info was nonzero, and
+ * *best_cfg the fastest configuration whose solves all succeeded (-1: none).
+ * The operands are those of the entry point of `op`: potrf_upper takes d_A;
+ * trsyl_lu takes L = d_A, U = d_B, C = d_C; trlyap_l takes L = d_A,
+ * S = d_C (d_B unused); X, info and the workspace as there (sized for
+ * `mode`).  mode is any mode but SS_MODE_AUTO.  This is a tuning call, not
+ * part of the solve path: it synchronises `stream` and cannot be captured
+ * in a CUDA graph.  h_ms and h_bad hold ss_config_count(op, mode) entries.
+ * Returns 0, -k for an invalid argument k, or the error of the first
+ * failing solve call.
+ */
+int ss_autotune(int op, int mode, int batch, int max_n, const int *d_n,
+                const double *const *d_A, const int *d_lda,
+                const double *const *d_B, const int *d_ldb,
+                const double *const *d_C, const int *d_ldc,
+                double *const *d_X, const int *d_ldx, int *d_info,
+                void *d_work, size_t work_bytes, int reps,
+                float *h_ms, int *h_bad, int *best_cfg, void *stream);
+
+/*
+ * The learned selector (the paper's "Limitations and future work"
+ * paragraph: model-based selection instead of autotuning): the MLP above,
+ * evaluated for every (precision mode, configuration) of a call, predicts
+ * which one is fastest.  Library state, one model per process, guarded by a
+ * lock.
+ *
+ * Model: the SS_MLP_PARAMS parameters; cfg_count[op * 5 + m] (may be NULL:
+ * every configuration), the configurations of (op, selector mode m) that had
+ * training targets; batch_max[(op * SS_NUM_BINS + k) * 5 + m] (may be NULL:
+ * no limit), the largest batch trained for size bin k, beyond which a
+ * prediction is taken at that batch and scaled linearly with the count.
+ * Selector modes m = 0..4 are SS_MODE_FP64, SS_MODE_FP32_REFINED,
+ * SS_MODE_TF32_REFINED, SS_MODE_BF16_REFINED and SS_MODE_DF (the modes that
+ * meet the FP64 accuracy gate); the features of a (op, n, batch, m) query are
+ * op one-hot [3], log2(n) / 9, log2(batch) / 14, m one-hot [5], with n the
+ * geometric centre of the size bin.
+ *
+ * ss_selector_set / ss_selector_get: copy a model in or out (host arrays;
+ * get: -1 if none is set).  ss_selector_clear: forget it.
+ * ss_selector_save / ss_selector_load: the model as a little-endian binary
+ * file ("SSMLP1" header, dimensions, parameters, cfg_count, batch_max);
+ * SS_ERR_IO on a missing, short or mismatched file.
+ * ss_selector_train: Adam on the masked mean squared error of log2 ms
+ * targets (ss_mlp_grad / ss_mlp_adam, beta1 0.9, beta2 0.999, eps 1e-8,
+ * `steps` steps at rate lr) from h_init (NULL: the current model), rows of
+ * h_x [rows x SS_MLP_IN], h_t and h_m [rows x SS_MLP_OUT]; h_loss (may be
+ * NULL) gets the loss before each step.  The trained parameters, and
+ * cfg_count and batch_max read off the rows' features and mask, become the
+ * model.  Allocates and frees its device buffers; synchronises `stream`.
+ *
+ * A call with count_by_bin[k] instances in size bin k (k < nbins):
+ * ss_selector_queries writes the feature rows to evaluate (at most
+ * SS_SELECTOR_MAX_ROWS) and their number; ss_selector_decide turns the
+ * network's outputs for them, h_y [nrows x SS_MLP_OUT] log2 ms, into a
+ * (mode, cfg) per bin: SS_SELECTOR_PER_BIN the fastest per bin,
+ * SS_SELECTOR_CALL the single pair with the smallest predicted total over the
+ * call, written to every bin (one launch group); bins without a choice get
+ * -1; *pred_ms (may be NULL) the predicted total.  ss_selector_predict does
+ * both around the CUDA forward kernel on `stream` (synchronised; the model's
+ * device copy and row buffers are allocated on a device's first prediction
+ * and kept).  ss_selector_install predicts and passes the result to
+ * ss_set_auto_table.  All return 0, -k for an invalid argument k,
+ * SS_ERR_NO_SELECTOR without a model, or SS_ERR_CUDA.
+ */
+#define SS_SELECTOR_PER_BIN 0
+#define SS_SELECTOR_CALL 1
+#define SS_SELECTOR_MAX_ROWS (SS_NUM_BINS * 5)
+int ss_selector_set(const float *h_params, const int *cfg_count, const int *batch_max);
+int ss_selector_get(float *h_params, int *cfg_count, int *batch_max);
+int ss_selector_clear(void);
+int ss_selector_save(const char *path);
+int ss_selector_load(const char *path);
+int ss_selector_train(const float *h_x, const float *h_t, const float *h_m, int rows, const float *h_init,
+                      int steps, float lr, float *h_loss, void *stream);
+int ss_selector_queries(int op, int nbins, const int *count_by_bin, float *h_x, int *nrows);
+int ss_selector_decide(int op, int nbins, const int *count_by_bin, int policy, const float *h_y,
+                       int *mode_by_bin, int *cfg_by_bin, double *pred_ms);
+int ss_selector_predict(int op, int nbins, const int *count_by_bin, int policy,
+                        int *mode_by_bin, int *cfg_by_bin, double *pred_ms, void *stream);
+int ss_selector_install(int op, int nbins, const int *count_by_bin, int policy, void *stream);
 
 /* Library version. */
 int ss_version(void);

@@ -213,13 +213,16 @@ static long long scratch_per_n2(int op, int mode)
     return mode == SS_MODE_FP64 ? 0 : mixed_scratch_per_n2(op, mode);
 }
 
-// Workspace layout: [meta: META_INTS ints][perm: batch ints][scr: batch
-// int64][scratch: batch * max_n^2 * scratch_per_n2 floats], each part aligned
-// to 256 bytes.
+static bool has_df(int mode) { return mode == SS_MODE_DF || mode == SS_MODE_AUTO; }
+
+// Workspace layout: [meta: META_INTS ints][perm: batch ints][dfs: batch
+// DfInst, SS_MODE_DF and AUTO][scr: batch int64][scratch: batch * max_n^2 *
+// scratch_per_n2 floats], each part aligned to 256 bytes.
 size_t workspace_bytes(int op, int batch, int max_n, int mode)
 {
     size_t b = align_up(META_INTS * sizeof(int), 256);
     b += align_up((size_t)batch * sizeof(int), 256);
+    if (has_df(mode)) b += align_up((size_t)batch * sizeof(DfInst), 256);
     const long long per = scratch_per_n2(op, mode);
     if (per > 0) {
         b += align_up((size_t)batch * sizeof(long long), 256);
@@ -228,7 +231,7 @@ size_t workspace_bytes(int op, int batch, int max_n, int mode)
     return b;
 }
 
-void carve_workspace(void *d_work, int batch, int max_n, int mode, Sched *s)
+void carve_workspace(void *d_work, size_t work_bytes, int op, int batch, int max_n, int mode, Sched *s)
 {
     (void)max_n;
     char *p = static_cast<char *>(d_work);
@@ -236,10 +239,20 @@ void carve_workspace(void *d_work, int batch, int max_n, int mode, Sched *s)
     p += align_up(META_INTS * sizeof(int), 256);
     s->perm = reinterpret_cast<const int *>(p);
     p += align_up((size_t)batch * sizeof(int), 256);
+    s->dfs = nullptr;
+    if (has_df(mode)) {
+        s->dfs = reinterpret_cast<const DfInst *>(p);
+        p += align_up((size_t)batch * sizeof(DfInst), 256);
+    }
     s->scr = nullptr;
     s->scratch = nullptr;
     s->scratch_elems = 0;
-    (void)mode;
+    if (scratch_per_n2(op, mode) > 0) {
+        s->scr = reinterpret_cast<const long long *>(p);
+        p += align_up((size_t)batch * sizeof(long long), 256);
+        s->scratch = p;
+        s->scratch_elems = (long long)(((static_cast<char *>(d_work) + work_bytes) - p) / sizeof(float));
+    }
 }
 
 }  // namespace ss
@@ -302,19 +315,28 @@ int run(int op, int batch, int max_n, const Operands &o, int mode, int cfg, void
     }
 
     Sched s;
-    carve_workspace(d_work, batch, max_key, mode, &s);
+    carve_workspace(d_work, work_bytes, op, batch, max_key, mode, &s);
     const long long per = scratch_per_n2(op, mode);
-    if (per > 0) {
-        char *p = reinterpret_cast<char *>(const_cast<int *>(s.perm)) + align_up((size_t)batch * sizeof(int), 256);
-        s.scr = reinterpret_cast<const long long *>(p);
-        p += align_up((size_t)batch * sizeof(long long), 256);
-        s.scratch = p;
-        s.scratch_elems = (long long)((d_work == nullptr ? 0 : (static_cast<char *>(d_work) + work_bytes) - p) / sizeof(float));
-    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = launch_binning(batch, max_n, o.n, o.info, s, group_of_bin, ngroups, per, st, o.m, max_m);
     if (e != cudaSuccess) return SS_ERR_CUDA;
-    g_launches.fetch_add(1 + ngroups, std::memory_order_relaxed);
+    // A double-float group is the unscaled pipeline and the rescaled pass; for
+    // Sylvester / Lyapunov also the range fix-up pass, and the call gets the
+    // scale pre-pass.
+    int nlaunch = 1 + ngroups;
+    bool any_df = false;
+    for (int g = 0; g < ngroups; ++g)
+        if (group_mode[g] == SS_MODE_DF) {
+            if (s.dfs == nullptr) return SS_ERR_CUDA;
+            any_df = true;
+            nlaunch += op != SS_OP_POTRF ? 2 : 1;
+        }
+    if (any_df && op != SS_OP_POTRF) {
+        e = launch_df_scale(op, batch, o, s, st);
+        if (e != cudaSuccess) return SS_ERR_CUDA;
+        ++nlaunch;
+    }
+    g_launches.fetch_add(nlaunch, std::memory_order_relaxed);
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     const bool prof = profile_pair(&ev0, &ev1);
     if (prof) cudaEventRecord(ev0, st);
@@ -456,7 +478,7 @@ int posv_upper(int batch, int max_n, int max_k, const int *d_n, const int *d_k, 
     // Stage 2: the two triangular solves, on the last queue head (the factor
     // uses at most NUM_BINS < MAX_GROUPS launch groups).
     Sched s;
-    carve_workspace(d_work, batch, max_n, mode, &s);
+    carve_workspace(d_work, work_bytes, SS_OP_POTRF, batch, max_n, mode, &s);
     cudaError_t e = launch_posv_solve(d_n, d_k, max_k, d_R, d_ldr, d_B, d_ldb, d_X, d_ldx, d_info, s,
                                       MAX_GROUPS - 1, batch, static_cast<cudaStream_t>(stream), mode == SS_MODE_DF);
     if (e != cudaSuccess) return SS_ERR_CUDA;

@@ -14,6 +14,11 @@
 //      L D + D U = R in low precision, X += D, until the predicted error
 //      |D|^2 / |D_prev| (or |D| itself) is below SS_REFINE_TOL * |X|.
 // The Lyapunov form is the Sylvester one with U = L^T over the lower blocks.
+// Every instance is rescaled by powers of two (DfScale: L and U by 2^op, C by
+// 2^rhs, so X carries 2^x) before anything enters FP32: each FP64 value is
+// shifted as it is converted (the `sh` arguments below), X in global memory
+// stays in the caller's units.  Without it data outside FP32's exponent
+// range (or residuals that shrink below it) would be lost in conversion.
 //
 // Double-float arithmetic (split, TwoProduct / TwoSum updates) is in df.cuh.
 #pragma once
@@ -47,24 +52,32 @@ __device__ __forceinline__ float d2f_trunc(double x)
 }
 
 
-template <typename Src>
-__device__ __forceinline__ float to_f(Src v) { return (float)v; }
-template <>
-__device__ __forceinline__ float to_f<double>(double v) { return d2f_trunc(v); }
+// x * 2^sh -> FP32 by truncation (the high part of split_df_s, with its
+// flush below 2^-126 and +-Inf above the range).
+__device__ __forceinline__ float d2f_trunc_s(double x, int sh)
+{
+    float hi, lo;
+    split_df_s(x, sh, hi, lo);
+    return hi;
+}
 
-// Element conversion for staging: float (truncating FP64), float2 (double-float
-// split of an FP64 value).
+// Staging conversions of one element: FP64 sources are scaled by 2^sh and
+// truncated to FP32 (float) or split (float2); FP32 sources (scratch that is
+// already in scaled units) are copied.
+__device__ __forceinline__ float to_f(float v, int) { return v; }
+__device__ __forceinline__ float to_f(double v, int sh) { return d2f_trunc_s(v, sh); }
+
 template <typename Elem, typename Src>
-__device__ __forceinline__ Elem cvt_elem(Src v);
+__device__ __forceinline__ Elem cvt_elem(Src v, int sh);
 template <>
-__device__ __forceinline__ float cvt_elem<float, float>(float v) { return v; }
+__device__ __forceinline__ float cvt_elem<float, float>(float v, int) { return v; }
 template <>
-__device__ __forceinline__ float cvt_elem<float, double>(double v) { return d2f_trunc(v); }
+__device__ __forceinline__ float cvt_elem<float, double>(double v, int sh) { return d2f_trunc_s(v, sh); }
 template <>
-__device__ __forceinline__ float2 cvt_elem<float2, double>(double v)
+__device__ __forceinline__ float2 cvt_elem<float2, double>(double v, int sh)
 {
     float2 r;
-    split_df(v, r.x, r.y);
+    split_df_s(v, sh, r.x, r.y);
     return r;
 }
 
@@ -87,9 +100,10 @@ __device__ __forceinline__ bool fill_keep(int r, int c) {
     return F == F_FULL || F == F_SYM_LOWER || (F == F_LOWER ? r >= c : r <= c);
 }
 
-// Float tile from a double or float source (rows x cols valid, zero elsewhere).
+// Float tile from a double (scaled by 2^sh) or float source (rows x cols
+// valid, zero elsewhere).
 template <int B, int T, Fill F, typename Src>
-__device__ __forceinline__ void stage_f(float *S, const Src *G, long ldg, int rows, int cols)
+__device__ __forceinline__ void stage_f(float *S, const Src *G, long ldg, int rows, int cols, int sh)
 {
     constexpr int LD = FTile<B>::LD;
 #pragma unroll 4
@@ -98,15 +112,15 @@ __device__ __forceinline__ void stage_f(float *S, const Src *G, long ldg, int ro
         float v = 0.0f;
         if (r < rows && c < cols && fill_keep<F>(r, c)) {
             const long idx = (F == F_SYM_LOWER && r < c) ? (c + (long)r * ldg) : (r + (long)c * ldg);
-            v = to_f<Src>(G[idx]);
+            v = to_f(G[idx], sh);
         }
         S[r + c * LD] = v;
     }
 }
 
-// Double-float tile (float2 hi/lo) from a double source.
+// Double-float tile (float2 hi/lo) of a double source scaled by 2^sh.
 template <int B, int T, Fill F>
-__device__ __forceinline__ void stage_df(float2 *S, const double *G, long ldg, int rows, int cols)
+__device__ __forceinline__ void stage_df(float2 *S, const double *G, long ldg, int rows, int cols, int sh)
 {
     constexpr int LD = FTile<B>::LD;
 #pragma unroll 4
@@ -115,24 +129,26 @@ __device__ __forceinline__ void stage_df(float2 *S, const double *G, long ldg, i
         float2 v = make_float2(0.f, 0.f);
         if (r < rows && c < cols && fill_keep<F>(r, c)) {
             const long idx = (F == F_SYM_LOWER && r < c) ? (c + (long)r * ldg) : (r + (long)c * ldg);
-            split_df(G[idx], v.x, v.y);
+            split_df_s(G[idx], sh, v.x, v.y);
         }
         S[r + c * LD] = v;
     }
 }
 
-// Double tile (for the FP64-FMA residual).
+// Double tile (for the FP64-FMA residual) of a double source scaled by 2^sh
+// (exact products by powers of two).
 template <int B, int T, Fill F>
-__device__ __forceinline__ void stage_d(double *S, const double *G, long ldg, int rows, int cols)
+__device__ __forceinline__ void stage_d(double *S, const double *G, long ldg, int rows, int cols, int sh)
 {
     constexpr int LD = Tile<B>::LD;
+    const Pow2 f(sh);
 #pragma unroll 4
     for (int e = threadIdx.x; e < B * B; e += T) {
         const int r = e % B, c = e / B;
         double v = 0.0;
         if (r < rows && c < cols && fill_keep<F>(r, c)) {
             const long idx = (F == F_SYM_LOWER && r < c) ? (c + (long)r * ldg) : (r + (long)c * ldg);
-            v = G[idx];
+            v = f(G[idx]);
         }
         S[r + c * LD] = v;
     }
@@ -204,7 +220,7 @@ struct Micro {
 // Stage op(A) (rows x kk valid, zero elsewhere) k-major: sOA[r + k*LDA].
 // TRANS: op(A)(r, k) = G(k, r).
 template <int B, int T, bool TRANS, typename Src, typename Elem>
-__device__ __forceinline__ void stage_opA(Elem *S, const Src *G, long ldg, int rows, int kk)
+__device__ __forceinline__ void stage_opA(Elem *S, const Src *G, long ldg, int rows, int kk, int sh)
 {
     constexpr int LDA = Micro<B, T>::LDA;
 #pragma unroll 4
@@ -212,14 +228,14 @@ __device__ __forceinline__ void stage_opA(Elem *S, const Src *G, long ldg, int r
         const int x = e % B, y = e / B;      // fast index x walks memory
         const int r = TRANS ? y : x, k = TRANS ? x : y;
         Elem v{};
-        if (r < rows && k < kk) v = cvt_elem<Elem>(G[x + (long)y * ldg]);
+        if (r < rows && k < kk) v = cvt_elem<Elem>(G[x + (long)y * ldg], sh);
         S[r + k * LDA] = v;
     }
 }
 
 // Stage op(B) (kk x cols valid) k-major: sOB[c + k*LDB].  TRANS: op(B)(k, c) = G(c, k).
 template <int B, int T, bool TRANS, typename Src, typename Elem>
-__device__ __forceinline__ void stage_opB(Elem *S, const Src *G, long ldg, int kk, int cols)
+__device__ __forceinline__ void stage_opB(Elem *S, const Src *G, long ldg, int kk, int cols, int sh)
 {
     constexpr int LDB = Micro<B, T>::LDB;
 #pragma unroll 4
@@ -227,7 +243,7 @@ __device__ __forceinline__ void stage_opB(Elem *S, const Src *G, long ldg, int k
         const int x = e % B, y = e / B;
         const int k = TRANS ? y : x, c = TRANS ? x : y;
         Elem v{};
-        if (k < kk && c < cols) v = cvt_elem<Elem>(G[x + (long)y * ldg]);
+        if (k < kk && c < cols) v = cvt_elem<Elem>(G[x + (long)y * ldg], sh);
         S[c + k * LDB] = v;
     }
 }

@@ -15,6 +15,9 @@
 //      the step removes E to first order; the remaining error is the square of
 //      the previous one plus the FP32 rounding of the correction.  Stop as the
 //      Sylvester driver does (|D| or |D|^2/|D_prev| below SS_REFINE_TOL |X|).
+// The instance is rescaled by powers of two first (DfScale::cholesky: A by
+// 4^s, X by 2^s; F is unchanged), each FP64 value shifted as it is converted;
+// X in global memory stays in the caller's units.
 // Scratch: two n x n float buffers (W1, W2, ld n).
 #include "mixed.cuh"
 
@@ -87,20 +90,20 @@ __device__ void trsm_ut_f(const float *sD, const float *s_rinv, float *sT, int m
     }
 }
 
-// Stage the upper-triangular diagonal block X_II (FP64 source) as floats and
-// its reciprocal diagonal computed in FP64.
+// Stage the upper-triangular diagonal block X_II (FP64 source, scaled by
+// 2^shx) as floats and its reciprocal diagonal computed in FP64.
 template <int B, int T>
-__device__ void stage_pivots(float *sD, float *s_rinv, const double *X, long ldx, int i0, int m)
+__device__ void stage_pivots(float *sD, float *s_rinv, const double *X, long ldx, int i0, int m, int shx)
 {
-    stage_f<B, T, F_UPPER>(sD, X + i0 + (long)i0 * ldx, ldx, m, m);
-    for (int i = threadIdx.x; i < m; i += T) s_rinv[i] = d2f_trunc(1.0 / X[(i0 + i) + (long)(i0 + i) * ldx]);
+    stage_f<B, T, F_UPPER>(sD, X + i0 + (long)i0 * ldx, ldx, m, m, shx);
+    for (int i = threadIdx.x; i < m; i += T) s_rinv[i] = d2f_trunc_s(1.0 / X[(i0 + i) + (long)(i0 + i) * ldx], -shx);
     __syncthreads();
 }
 
 // Low-precision factor of A into W (upper triangle, ld n).  Returns 0 or the
 // failing leading minor.
 template <int B, int T, int P>
-__device__ int chol_low(int n, const double *A, long lda, float *W, float *sm)
+__device__ int chol_low(int n, const double *A, long lda, float *W, float *sm, int sha)
 {
     constexpr int LD = FTile<B>::LD, SZ = FTile<B>::SZ, E = B * B / T;
     float *sA = sm, *sB = sm + SZ, *sT = sm + 2 * SZ, *sD = sm + 3 * SZ;
@@ -115,8 +118,8 @@ __device__ int chol_low(int n, const double *A, long lda, float *W, float *sm)
             const bool diag = I == J;
             const int mI = diag ? nJ : B;
             __syncthreads();
-            if (diag) stage_f<B, T, F_UPPER>(sT, A + i0 + (long)j0 * lda, lda, mI, nJ);
-            else stage_f<B, T, F_FULL>(sT, A + i0 + (long)j0 * lda, lda, mI, nJ);
+            if (diag) stage_f<B, T, F_UPPER>(sT, A + i0 + (long)j0 * lda, lda, mI, nJ, sha);
+            else stage_f<B, T, F_FULL>(sT, A + i0 + (long)j0 * lda, lda, mI, nJ, sha);
             __syncthreads();
             float acc[E];
             float frag[FragN<B, T, P>::value][4];
@@ -130,8 +133,8 @@ __device__ int chol_low(int n, const double *A, long lda, float *W, float *sm)
             for (int K = 0; K < I; ++K) {
                 const int k0 = K * B;
                 __syncthreads();
-                stage_f<B, T, F_FULL>(sA, W + k0 + (long)i0 * ldw, ldw, B, mI);   // X_KI
-                stage_f<B, T, F_FULL>(sB, W + k0 + (long)j0 * ldw, ldw, B, nJ);   // X_KJ
+                stage_f<B, T, F_FULL>(sA, W + k0 + (long)i0 * ldw, ldw, B, mI, 0);   // X_KI
+                stage_f<B, T, F_FULL>(sB, W + k0 + (long)j0 * ldw, ldw, B, nJ, 0);   // X_KJ
                 __syncthreads();
                 if constexpr (P == P_FP32) slot_update_f<B, T, true, false>(acc, sl, sA, sB, B);
                 else mma_update<B, T, P, true, false>(frag, sA, sB, B);
@@ -146,7 +149,7 @@ __device__ int chol_low(int n, const double *A, long lda, float *W, float *sm)
             }
             __syncthreads();
             if (!diag) {
-                stage_f<B, T, F_UPPER>(sD, W + i0 + (long)i0 * ldw, ldw, B, B);
+                stage_f<B, T, F_UPPER>(sD, W + i0 + (long)i0 * ldw, ldw, B, B, 0);
                 // Pivot reciprocals in FP64 from the stored FP32 diagonal.
                 for (int i = threadIdx.x; i < B; i += T) s_rinv[i] = d2f_trunc(1.0 / f2d_exact(W[(i0 + i) + (long)(i0 + i) * ldw]));
                 __syncthreads();
@@ -169,7 +172,7 @@ __device__ int chol_low(int n, const double *A, long lda, float *W, float *sm)
 // full (both triangles, E is symmetric).
 template <int B, int T, int RS>
 __device__ void chol_residual(int n, const double *A, long lda, const double *X, long ldx, float *W,
-                              float *sm)
+                              float *sm, const DfScale &sc)
 {
     constexpr int E = B * B / T;
     using Elem = typename std::conditional<RS == R_DF, float2, double>::type;
@@ -192,8 +195,8 @@ __device__ void chol_residual(int n, const double *A, long lda, const double *X,
                     int rr = i0 + sl.row[r], cc = j0 + sl.col[r];
                     if (rr > cc) { const int t = rr; rr = cc; cc = t; }   // upper triangle of A
                     const double a = A[rr + (long)cc * lda];
-                    if constexpr (RS == R_DF) split_df(a, ah[r], al[r]);
-                    else ad[r] = a;
+                    if constexpr (RS == R_DF) split_df_s(a, sc.op, ah[r], al[r]);
+                    else ad[r] = Pow2(sc.op)(a);
                 }
             }
             for (int K = 0; K <= I; ++K) {
@@ -202,18 +205,18 @@ __device__ void chol_residual(int n, const double *A, long lda, const double *X,
                 // X_KI (upper when K == I) and X_KJ (upper when K == J).
                 if constexpr (RS == R_DF) {
                     float2 *a2 = reinterpret_cast<float2 *>(sA), *b2 = reinterpret_cast<float2 *>(sB);
-                    if (K == I) stage_df<B, T, F_UPPER>(a2, X + k0 + (long)i0 * ldx, ldx, kw, mI);
-                    else stage_df<B, T, F_FULL>(a2, X + k0 + (long)i0 * ldx, ldx, kw, mI);
-                    if (K == J) stage_df<B, T, F_UPPER>(b2, X + k0 + (long)j0 * ldx, ldx, kw, nJ);
-                    else stage_df<B, T, F_FULL>(b2, X + k0 + (long)j0 * ldx, ldx, kw, nJ);
+                    if (K == I) stage_df<B, T, F_UPPER>(a2, X + k0 + (long)i0 * ldx, ldx, kw, mI, sc.x);
+                    else stage_df<B, T, F_FULL>(a2, X + k0 + (long)i0 * ldx, ldx, kw, mI, sc.x);
+                    if (K == J) stage_df<B, T, F_UPPER>(b2, X + k0 + (long)j0 * ldx, ldx, kw, nJ, sc.x);
+                    else stage_df<B, T, F_FULL>(b2, X + k0 + (long)j0 * ldx, ldx, kw, nJ, sc.x);
                     __syncthreads();
                     slot_update_df<B, T, true, false>(ah, al, sl, a2, b2, kw);
                 } else {
                     double *a = reinterpret_cast<double *>(sA), *b = reinterpret_cast<double *>(sB);
-                    if (K == I) stage_d<B, T, F_UPPER>(a, X + k0 + (long)i0 * ldx, ldx, kw, mI);
-                    else stage_d<B, T, F_FULL>(a, X + k0 + (long)i0 * ldx, ldx, kw, mI);
-                    if (K == J) stage_d<B, T, F_UPPER>(b, X + k0 + (long)j0 * ldx, ldx, kw, nJ);
-                    else stage_d<B, T, F_FULL>(b, X + k0 + (long)j0 * ldx, ldx, kw, nJ);
+                    if (K == I) stage_d<B, T, F_UPPER>(a, X + k0 + (long)i0 * ldx, ldx, kw, mI, sc.x);
+                    else stage_d<B, T, F_FULL>(a, X + k0 + (long)i0 * ldx, ldx, kw, mI, sc.x);
+                    if (K == J) stage_d<B, T, F_UPPER>(b, X + k0 + (long)j0 * ldx, ldx, kw, nJ, sc.x);
+                    else stage_d<B, T, F_FULL>(b, X + k0 + (long)j0 * ldx, ldx, kw, nJ, sc.x);
                     __syncthreads();
                     slot_update<B, T, true, false>(ad, sl, a, b, kw);
                 }
@@ -236,7 +239,7 @@ __device__ void chol_residual(int n, const double *A, long lda, const double *X,
 // (staged as FP32; pivot reciprocals in FP64).  With TRANS the right-hand
 // side is read from Wsrc transposed (R = Wsrc^T) and the result goes to W.
 template <int B, int T, bool TRANS>
-__device__ void trsm_ut_blocked(int n, const double *X, long ldx, const float *Wsrc, float *W, float *sm)
+__device__ void trsm_ut_blocked(int n, const double *X, long ldx, const float *Wsrc, float *W, float *sm, int shx)
 {
     constexpr int LD = FTile<B>::LD, SZ = FTile<B>::SZ, E = B * B / T;
     float *sA = sm, *sB = sm + SZ, *sT = sm + 2 * SZ, *sD = sm + 3 * SZ;
@@ -247,7 +250,7 @@ __device__ void trsm_ut_blocked(int n, const double *X, long ldx, const float *W
     for (int I = 0; I < nb; ++I) {
         const int i0 = I * B, mI = min(B, n - i0);
         __syncthreads();
-        stage_pivots<B, T>(sD, s_rinv, X, ldx, i0, mI);
+        stage_pivots<B, T>(sD, s_rinv, X, ldx, i0, mI, shx);
         for (int J = 0; J < nb; ++J) {
             const int j0 = J * B, nJ = min(B, n - j0);
             sl.set(Shape::Full, mI, nJ);
@@ -263,8 +266,8 @@ __device__ void trsm_ut_blocked(int n, const double *X, long ldx, const float *W
             for (int K = 0; K < I; ++K) {
                 const int k0 = K * B;
                 __syncthreads();
-                stage_f<B, T, F_FULL>(sA, X + k0 + (long)i0 * ldx, ldx, B, mI);   // X_KI
-                stage_f<B, T, F_FULL>(sB, W + k0 + (long)j0 * ldw, ldw, B, nJ);   // Z_KJ
+                stage_f<B, T, F_FULL>(sA, X + k0 + (long)i0 * ldx, ldx, B, mI, shx);   // X_KI
+                stage_f<B, T, F_FULL>(sB, W + k0 + (long)j0 * ldw, ldw, B, nJ, 0);     // Z_KJ
                 __syncthreads();
                 slot_update_f<B, T, true, false>(acc, sl, sA, sB, B);
             }
@@ -287,7 +290,7 @@ __device__ void trsm_ut_blocked(int n, const double *X, long ldx, const float *W
 // Returns |D|_F^2.
 template <int B, int T>
 __device__ float chol_correct(int n, double *X, long ldx, const float *Wf, float *Wd, float *sm,
-                              float *s_red)
+                              float *s_red, int shx)
 {
     constexpr int LD = FTile<B>::LD, SZ = FTile<B>::SZ, E = B * B / T;
     float *sA = sm, *sB = sm + SZ;
@@ -316,8 +319,8 @@ __device__ float chol_correct(int n, double *X, long ldx, const float *Wf, float
                     }
                     sA[r + c * LD] = v;
                 }
-                if (K == J) stage_f<B, T, F_UPPER>(sB, X + k0 + (long)j0 * ldx, ldx, kw, nJ);
-                else stage_f<B, T, F_FULL>(sB, X + k0 + (long)j0 * ldx, ldx, kw, nJ);
+                if (K == J) stage_f<B, T, F_UPPER>(sB, X + k0 + (long)j0 * ldx, ldx, kw, nJ, shx);
+                else stage_f<B, T, F_FULL>(sB, X + k0 + (long)j0 * ldx, ldx, kw, nJ, shx);
                 __syncthreads();
                 // acc += M X : slot_update_f subtracts, so negate via the sign of M.
                 slot_update_f<B, T, false, false>(acc, sl, sA, sB, kw);
@@ -334,7 +337,7 @@ __device__ float chol_correct(int n, double *X, long ldx, const float *Wf, float
         if (r > c) continue;
         const float d = Wd[e];
         ss = fmaf(d, d, ss);
-        X[r + (long)c * ldx] += f2d_exact(d);
+        X[r + (long)c * ldx] += f2d_exact_s(d, -shx);
     }
     return block_sum_f(ss, s_red);
 }
@@ -344,7 +347,12 @@ __device__ void chol_mixed_instance(int n, const double *A, long lda, double *X,
                                     float *W1, float *W2, bool raw, float *sm)
 {
     float *s_red = sm + 5 * FTile<B>::SZ;
-    const int f = chol_low<B, T, P>(n, A, lda, W1, sm);
+    int ea, dummy;
+    scan_exp3(ScanOp{A, lda, n, n, 2}, ScanOp{nullptr, 0, 0, 0, 0}, ScanOp{nullptr, 0, 0, 0, 0}, threadIdx.x >> 5, T / 32,
+              threadIdx.x & 31, ea, dummy);
+    cta_max2(ea, dummy, reinterpret_cast<int *>(s_red));
+    const DfScale sc = DfScale::cholesky(ea);
+    const int f = chol_low<B, T, P>(n, A, lda, W1, sm, sc.op);
     if (f) {
         if (threadIdx.x == 0) *info = f;
         return;
@@ -355,16 +363,16 @@ __device__ void chol_mixed_instance(int n, const double *A, long lda, double *X,
         if (r > c) continue;
         const float v = W1[e];
         ss = fmaf(v, v, ss);
-        X[r + (long)c * ldx] = f2d_exact(v);
+        X[r + (long)c * ldx] = f2d_exact_s(v, -sc.x);
     }
     const float nx = sqrtf(block_sum_f(ss, s_red));
     int conv = raw || nx == 0.0f;
     float prev = nx;
     for (int it = 0; it < MAXIT && !conv; ++it) {
-        chol_residual<B, T, RS>(n, A, lda, X, ldx, W1, sm);            // E -> W1
-        trsm_ut_blocked<B, T, false>(n, X, ldx, W1, W1, sm);           // Y = X^-T E in W1
-        trsm_ut_blocked<B, T, true>(n, X, ldx, W1, W2, sm);            // F = X^-T Y^T in W2
-        const float nd = sqrtf(chol_correct<B, T>(n, X, ldx, W2, W1, sm, s_red));
+        chol_residual<B, T, RS>(n, A, lda, X, ldx, W1, sm, sc);        // E -> W1
+        trsm_ut_blocked<B, T, false>(n, X, ldx, W1, W1, sm, sc.x);     // Y = X^-T E in W1
+        trsm_ut_blocked<B, T, true>(n, X, ldx, W1, W2, sm, sc.x);      // F = X^-T Y^T in W2
+        const float nd = sqrtf(chol_correct<B, T>(n, X, ldx, W2, W1, sm, s_red, sc.x));
         const float pred = prev > 0.0f ? nd * (nd / prev) : nd;
         conv = (nd <= (float)SS_REFINE_TOL * nx) || (pred <= (float)SS_REFINE_TOL * nx);
         prev = nd;

@@ -17,10 +17,12 @@ constexpr size_t mixed_smem_bytes()
 }
 
 // Low-precision solve of L D + D U = RHS into W (FP32, ld n), in place when
-// the right-hand side is W itself (SRC_D = false) or from the FP64 C.
+// the right-hand side is W itself (SRC_D = false) or from the FP64 C.  All in
+// the instance's scaled units (sc): W and Rinv already are, L, U and C are
+// shifted as they are staged.
 template <int B, int T, bool LYAP, int P, bool SRC_D>
 __device__ void low_solve(int n, const double *L, long ldl, const double *U, long ldu,
-                          const double *Cd, long ldc, float *W, const float *Rinv, float *sm)
+                          const double *Cd, long ldc, float *W, const float *Rinv, float *sm, const DfScale &sc)
 {
     constexpr int LD = FTile<B>::LD, SZ = FTile<B>::SZ, E = B * B / T;
     float *sA = sm, *sB = sm + SZ, *sT = sm + 2 * SZ, *sL = sm + 3 * SZ, *sU = sm + 4 * SZ;
@@ -30,16 +32,16 @@ __device__ void low_solve(int n, const double *L, long ldl, const double *U, lon
     for (int I = 0; I < nb; ++I) {
         const int mI = min(B, n - I * B), i0 = I * B;
         __syncthreads();
-        stage_f<B, T, F_LOWER>(sL, L + i0 + (long)i0 * ldl, ldl, mI, mI);
+        stage_f<B, T, F_LOWER>(sL, L + i0 + (long)i0 * ldl, ldl, mI, mI, sc.op);
         const int jend = LYAP ? I + 1 : nb;
         for (int J = 0; J < jend; ++J) {
             const int nJ = min(B, n - J * B), j0 = J * B;
             __syncthreads();
             if (SRC_D) {
-                if (LYAP && I == J) stage_f<B, T, F_SYM_LOWER>(sT, Cd + i0 + (long)j0 * ldc, ldc, mI, nJ);
-                else stage_f<B, T, F_FULL>(sT, Cd + i0 + (long)j0 * ldc, ldc, mI, nJ);
+                if (LYAP && I == J) stage_f<B, T, F_SYM_LOWER>(sT, Cd + i0 + (long)j0 * ldc, ldc, mI, nJ, sc.rhs);
+                else stage_f<B, T, F_FULL>(sT, Cd + i0 + (long)j0 * ldc, ldc, mI, nJ, sc.rhs);
             } else {
-                stage_f<B, T, F_FULL>(sT, W + i0 + (long)j0 * ldw, ldw, mI, nJ);
+                stage_f<B, T, F_FULL>(sT, W + i0 + (long)j0 * ldw, ldw, mI, nJ, 0);
             }
             __syncthreads();
             using MT = Micro<B, T>;
@@ -71,15 +73,17 @@ __device__ void low_solve(int n, const double *L, long ldl, const double *U, lon
                     else mma_update<B, T, P, false, false>(frag, sA, sB, B);
                 }
             };
-            // Stage A (not transposed) and B (transposed when tb) for either layout.
-            auto stageAB = [&](const auto *GA, long lda_, int ra, const auto *GB, long ldb_, int rb, int cb, bool tb) {
+            // Stage A (not transposed) and B (transposed when tb) for either
+            // layout, FP64 sources shifted by sha / shb.
+            auto stageAB = [&](const auto *GA, long lda_, int ra, int sha, const auto *GB, long ldb_, int rb, int cb,
+                               int shb, bool tb) {
                 if (micro) {
-                    stage_opA<B, T, false>(sA, GA, lda_, ra, B);
-                    if (tb) stage_opB<B, T, true>(sB, GB, ldb_, B, rb);
-                    else stage_opB<B, T, false>(sB, GB, ldb_, B, cb);
+                    stage_opA<B, T, false>(sA, GA, lda_, ra, B, sha);
+                    if (tb) stage_opB<B, T, true>(sB, GB, ldb_, B, rb, shb);
+                    else stage_opB<B, T, false>(sB, GB, ldb_, B, cb, shb);
                 } else {
-                    stage_f<B, T, F_FULL>(sA, GA, lda_, ra, B);
-                    stage_f<B, T, F_FULL>(sB, GB, ldb_, rb, cb);
+                    stage_f<B, T, F_FULL>(sA, GA, lda_, ra, B, sha);
+                    stage_f<B, T, F_FULL>(sB, GB, ldb_, rb, cb, shb);
                 }
             };
             // sum_{K<I} L_IK D_KJ
@@ -87,8 +91,8 @@ __device__ void low_solve(int n, const double *L, long ldl, const double *U, lon
                 const int k0 = K * B;
                 __syncthreads();
                 const bool tr = LYAP && K < J;
-                if (!tr) stageAB(L + i0 + (long)k0 * ldl, ldl, mI, W + k0 + (long)j0 * ldw, ldw, B, nJ, false);
-                else stageAB(L + i0 + (long)k0 * ldl, ldl, mI, W + j0 + (long)k0 * ldw, ldw, nJ, B, true);
+                if (!tr) stageAB(L + i0 + (long)k0 * ldl, ldl, mI, sc.op, W + k0 + (long)j0 * ldw, ldw, B, nJ, 0, false);
+                else stageAB(L + i0 + (long)k0 * ldl, ldl, mI, sc.op, W + j0 + (long)k0 * ldw, ldw, nJ, B, 0, true);
                 __syncthreads();
                 update(tr);
             }
@@ -96,8 +100,8 @@ __device__ void low_solve(int n, const double *L, long ldl, const double *U, lon
             for (int K = 0; K < J; ++K) {
                 const int k0 = K * B;
                 __syncthreads();
-                if (!LYAP) stageAB(W + i0 + (long)k0 * ldw, ldw, mI, U + k0 + (long)j0 * ldu, ldu, B, nJ, false);
-                else stageAB(W + i0 + (long)k0 * ldw, ldw, mI, L + j0 + (long)k0 * ldl, ldl, nJ, B, true);
+                if (!LYAP) stageAB(W + i0 + (long)k0 * ldw, ldw, mI, 0, U + k0 + (long)j0 * ldu, ldu, B, nJ, sc.op, false);
+                else stageAB(W + i0 + (long)k0 * ldw, ldw, mI, 0, L + j0 + (long)k0 * ldl, ldl, nJ, B, sc.op, true);
                 __syncthreads();
                 update(LYAP);
             }
@@ -116,8 +120,8 @@ __device__ void low_solve(int n, const double *L, long ldl, const double *U, lon
             } else {
                 frag_store<B, T>(frag, sT);
             }
-            if (!LYAP) stage_f<B, T, F_UPPER>(sU, U + j0 + (long)j0 * ldu, ldu, nJ, nJ);
-            else stage_f<B, T, F_LOWER>(sU, L + j0 + (long)j0 * ldl, ldl, nJ, nJ);
+            if (!LYAP) stage_f<B, T, F_UPPER>(sU, U + j0 + (long)j0 * ldu, ldu, nJ, nJ, sc.op);
+            else stage_f<B, T, F_LOWER>(sU, L + j0 + (long)j0 * ldl, ldl, nJ, nJ, sc.op);
             __syncthreads();
             syl_diag_f<B, T, LYAP>(sL, sU, sT, mI, nJ, Rinv + i0 + (long)j0 * ldw, ldw, sA);
             for (int e = threadIdx.x; e < mI * nJ; e += T) {
@@ -131,11 +135,11 @@ __device__ void low_solve(int n, const double *L, long ldl, const double *U, lon
 
 // R = C - L X - X U (Lyapunov: U = L^T, lower blocks, X read through its
 // lower triangle) into W with FP64-class accuracy: double-float on the FP32
-// pipe (RS = R_DF) or FP64 FMA (RS = R_FP64).
+// pipe (RS = R_DF) or FP64 FMA (RS = R_FP64); in the scaled units of sc.
 template <int B, int T, bool LYAP, int RS>
 __device__ void residual(int n, const double *L, long ldl, const double *U, long ldu,
                          const double *C, long ldc, const double *X, long ldx, float *W, long ldw,
-                         float *sm)
+                         float *sm, const DfScale &sc)
 {
     constexpr int E = B * B / T;
     using Elem = typename std::conditional<RS == R_DF, float2, double>::type;
@@ -144,22 +148,22 @@ __device__ void residual(int n, const double *L, long ldl, const double *U, long
     const int nb = (n + B - 1) / B;
     Slots<B, T> sl;
 
-    auto stage = [&](Elem *S, const double *G, long ld, int rows, int cols, Fill f) {
+    auto stage = [&](Elem *S, const double *G, long ld, int rows, int cols, Fill f, int sh) {
         if constexpr (RS == R_DF) {
             float2 *S2 = reinterpret_cast<float2 *>(S);
             switch (f) {
-            case F_FULL: stage_df<B, T, F_FULL>(S2, G, ld, rows, cols); break;
-            case F_LOWER: stage_df<B, T, F_LOWER>(S2, G, ld, rows, cols); break;
-            case F_UPPER: stage_df<B, T, F_UPPER>(S2, G, ld, rows, cols); break;
-            default: stage_df<B, T, F_SYM_LOWER>(S2, G, ld, rows, cols); break;
+            case F_FULL: stage_df<B, T, F_FULL>(S2, G, ld, rows, cols, sh); break;
+            case F_LOWER: stage_df<B, T, F_LOWER>(S2, G, ld, rows, cols, sh); break;
+            case F_UPPER: stage_df<B, T, F_UPPER>(S2, G, ld, rows, cols, sh); break;
+            default: stage_df<B, T, F_SYM_LOWER>(S2, G, ld, rows, cols, sh); break;
             }
         } else {
             double *Sd = reinterpret_cast<double *>(S);
             switch (f) {
-            case F_FULL: stage_d<B, T, F_FULL>(Sd, G, ld, rows, cols); break;
-            case F_LOWER: stage_d<B, T, F_LOWER>(Sd, G, ld, rows, cols); break;
-            case F_UPPER: stage_d<B, T, F_UPPER>(Sd, G, ld, rows, cols); break;
-            default: stage_d<B, T, F_SYM_LOWER>(Sd, G, ld, rows, cols); break;
+            case F_FULL: stage_d<B, T, F_FULL>(Sd, G, ld, rows, cols, sh); break;
+            case F_LOWER: stage_d<B, T, F_LOWER>(Sd, G, ld, rows, cols, sh); break;
+            case F_UPPER: stage_d<B, T, F_UPPER>(Sd, G, ld, rows, cols, sh); break;
+            default: stage_d<B, T, F_SYM_LOWER>(Sd, G, ld, rows, cols, sh); break;
             }
         }
     };
@@ -181,7 +185,7 @@ __device__ void residual(int n, const double *L, long ldl, const double *U, long
                     for (int j = 0; j < MT::MC; ++j) {
                         int rr = MT::r0() + i, cc = MT::c0() + j;
                         if (LYAP && I == J && rr < cc) { const int t = rr; rr = cc; cc = t; }
-                        split_df(C[(i0 + rr) + (long)(j0 + cc) * ldc], mh[i][j], ml[i][j]);
+                        split_df_s(C[(i0 + rr) + (long)(j0 + cc) * ldc], sc.rhs, mh[i][j], ml[i][j]);
                     }
             } else {
                 sl.set(Shape::Full, mI, nJ);
@@ -192,8 +196,8 @@ __device__ void residual(int n, const double *L, long ldl, const double *U, long
                         int rr = sl.row[r], cc = sl.col[r];
                         if (LYAP && I == J && rr < cc) { const int t = rr; rr = cc; cc = t; }
                         const double c = C[(i0 + rr) + (long)(j0 + cc) * ldc];
-                        if (RS == R_DF) split_df(c, ah[r], al[r]);
-                        else ad[r] = c;
+                        if (RS == R_DF) split_df_s(c, sc.rhs, ah[r], al[r]);
+                        else ad[r] = Pow2(sc.rhs)(c);
                     }
                 }
             }
@@ -214,7 +218,7 @@ __device__ void residual(int n, const double *L, long ldl, const double *U, long
             // Micro-tile staging (double-float, k-major) of one A / B operand;
             // triangles (F_LOWER/F_UPPER) and the symmetric mirror are applied
             // by staging through the natural layout first when needed.
-            auto stageM = [&](bool isA, const double *G, long ld, int rows, int cols, Fill f, bool tb) {
+            auto stageM = [&](bool isA, const double *G, long ld, int rows, int cols, Fill f, bool tb, int sh) {
                 float2 *S = reinterpret_cast<float2 *>(isA ? sA : sB);
                 constexpr int LDA = MT::LDA, LDB = MT::LDB;
                 for (int e = threadIdx.x; e < B * B; e += T) {
@@ -227,21 +231,21 @@ __device__ void residual(int n, const double *L, long ldl, const double *U, long
                     }
                     if (keep) {
                         const long idx = (f == F_SYM_LOWER && x < y) ? (y + (long)x * ld) : (x + (long)y * ld);
-                        split_df(G[idx], v.x, v.y);
+                        split_df_s(G[idx], sh, v.x, v.y);
                     }
                     if (isA) S[x + y * LDA] = v;                 // op(A)(r=x, k=y)
                     else if (!tb) S[y + x * LDB] = v;            // op(B)(k=x, c=y)
                     else S[x + y * LDB] = v;                     // op(B)(k=y, c=x) = G(x, y)
                 }
             };
-            auto stage2 = [&](const double *GA, long lda_, int ra, int ca, Fill fa,
-                              const double *GB, long ldb_, int rb, int cb, Fill fb, bool tb) {
+            auto stage2 = [&](const double *GA, long lda_, int ra, int ca, Fill fa, int sha,
+                              const double *GB, long ldb_, int rb, int cb, Fill fb, int shb, bool tb) {
                 if (micro) {
-                    stageM(true, GA, lda_, ra, ca, fa, false);
-                    stageM(false, GB, ldb_, rb, cb, fb, tb);
+                    stageM(true, GA, lda_, ra, ca, fa, false, sha);
+                    stageM(false, GB, ldb_, rb, cb, fb, tb, shb);
                 } else {
-                    stage(sA, GA, lda_, ra, ca, fa);
-                    stage(sB, GB, ldb_, rb, cb, fb);
+                    stage(sA, GA, lda_, ra, ca, fa, sha);
+                    stage(sB, GB, ldb_, rb, cb, fb, shb);
                 }
             };
             // sum_{K<=I} L_IK X_KJ
@@ -250,9 +254,17 @@ __device__ void residual(int n, const double *L, long ldl, const double *U, long
                 __syncthreads();
                 const Fill fa = K == I ? F_LOWER : F_FULL;
                 bool tb = false;
-                if (!LYAP || K > J) stage2(L + i0 + (long)k0 * ldl, ldl, mI, kw, fa, X + k0 + (long)j0 * ldx, ldx, kw, nJ, F_FULL, false);
-                else if (K == J) stage2(L + i0 + (long)k0 * ldl, ldl, mI, kw, fa, X + j0 + (long)j0 * ldx, ldx, kw, nJ, F_SYM_LOWER, false);
-                else { stage2(L + i0 + (long)k0 * ldl, ldl, mI, kw, fa, X + j0 + (long)k0 * ldx, ldx, nJ, kw, F_FULL, true); tb = true; }
+                if (!LYAP || K > J)
+                    stage2(L + i0 + (long)k0 * ldl, ldl, mI, kw, fa, sc.op, X + k0 + (long)j0 * ldx, ldx, kw, nJ, F_FULL, sc.x,
+                           false);
+                else if (K == J)
+                    stage2(L + i0 + (long)k0 * ldl, ldl, mI, kw, fa, sc.op, X + j0 + (long)j0 * ldx, ldx, kw, nJ,
+                           F_SYM_LOWER, sc.x, false);
+                else {
+                    stage2(L + i0 + (long)k0 * ldl, ldl, mI, kw, fa, sc.op, X + j0 + (long)k0 * ldx, ldx, nJ, kw, F_FULL, sc.x,
+                           true);
+                    tb = true;
+                }
                 __syncthreads();
                 upd(tb, kw);
             }
@@ -262,8 +274,12 @@ __device__ void residual(int n, const double *L, long ldl, const double *U, long
                 __syncthreads();
                 const Fill fa = (LYAP && K == I) ? F_SYM_LOWER : F_FULL;
                 const long aoff = (LYAP && K == I) ? (i0 + (long)i0 * ldx) : (i0 + (long)k0 * ldx);
-                if (!LYAP) stage2(X + aoff, ldx, mI, kw, fa, U + k0 + (long)j0 * ldu, ldu, kw, nJ, K == J ? F_UPPER : F_FULL, false);
-                else stage2(X + aoff, ldx, mI, kw, fa, L + j0 + (long)k0 * ldl, ldl, nJ, kw, K == J ? F_LOWER : F_FULL, true);
+                if (!LYAP)
+                    stage2(X + aoff, ldx, mI, kw, fa, sc.x, U + k0 + (long)j0 * ldu, ldu, kw, nJ, K == J ? F_UPPER : F_FULL,
+                           sc.op, false);
+                else
+                    stage2(X + aoff, ldx, mI, kw, fa, sc.x, L + j0 + (long)k0 * ldl, ldl, nJ, kw, K == J ? F_LOWER : F_FULL,
+                           sc.op, true);
                 __syncthreads();
                 upd(LYAP, kw);
             }
@@ -287,10 +303,11 @@ __device__ void residual(int n, const double *L, long ldl, const double *U, long
     __syncthreads();
 }
 
-// X (FP64, the meaningful triangle) = X + D (first: X = D); returns |D|_F^2.
+// X (FP64, the meaningful triangle, caller's units) = X + D * 2^-shx (first:
+// X = D * 2^-shx), D in scaled units; returns |D|_F^2.
 template <int T, bool LYAP>
 __device__ float update_x(int n, double *X, long ldx, const float *W, long ldw, bool first,
-                          float *s_red)
+                          float *s_red, int shx)
 {
     float ss = 0.0f;
 #pragma unroll 4
@@ -300,16 +317,17 @@ __device__ float update_x(int n, double *X, long ldx, const float *W, long ldw, 
         const float d = W[r + (long)c * ldw];
         ss = fmaf(d, d, ss);
         double *p = X + r + (long)c * ldx;
-        *p = first ? f2d_exact(d) : *p + f2d_exact(d);
+        *p = first ? f2d_exact_s(d, -shx) : *p + f2d_exact_s(d, -shx);
     }
     return block_sum_f(ss, s_red);
 }
 
 // r_ij = 1 / (l_ii + u_jj) computed in FP64, stored (rounded) as FP32 into
-// Rinv (ld n); returns 1 if a divisor is tiny or NaN.
+// Rinv (ld n) in the units of L and U scaled by 2^sho; returns 1 if a divisor
+// is tiny or NaN.
 template <int T, bool LYAP>
 __device__ int reciprocal_divisors(int n, const double *L, long ldl, const double *U, long ldu,
-                                   float *Rinv, float *s_red)
+                                   float *Rinv, float *s_red, int sho)
 {
     double md = 0.0;
     for (int i = threadIdx.x; i < n; i += T) {
@@ -330,9 +348,23 @@ __device__ int reciprocal_divisors(int n, const double *L, long ldl, const doubl
         const int i = e % n, j = e / n;
         const double d = L[i + (long)i * ldl] + (LYAP ? L[j + (long)j * ldl] : U[j + (long)j * ldu]);
         if (!(fabs(d) > delta)) bad = 1;
-        Rinv[e] = d2f_trunc(1.0 / d);
+        Rinv[e] = d2f_trunc_s(1.0 / d, -sho);
     }
     return __syncthreads_or(bad);
+}
+
+// The instance's power-of-two scaling (DfScale) from the largest entries of
+// L, U and C (Lyapunov: the lower triangles of L and S); s_buf: 2 ints per
+// warp.
+template <int T, bool LYAP>
+__device__ DfScale instance_scale(int n, const double *L, long ldl, const double *U, long ldu, const double *C,
+                                  long ldc, float *s_buf)
+{
+    int eo, ec;
+    scan_exp3(ScanOp{L, ldl, n, n, 1}, ScanOp{LYAP ? nullptr : U, ldu, n, n, 2}, ScanOp{C, ldc, n, n, LYAP ? 1 : 0},
+              threadIdx.x >> 5, T / 32, threadIdx.x & 31, eo, ec);
+    cta_max2(eo, ec, reinterpret_cast<int *>(s_buf));
+    return DfScale::sylvester(eo, ec);
 }
 
 template <int B, int T, bool LYAP, int P, int RS>
@@ -341,18 +373,19 @@ __device__ void mixed_instance(int n, const double *L, long ldl, const double *U
                                float *W, float *Rinv, bool raw, float *sm)
 {
     float *s_red = sm + 5 * FTile<B>::SZ;
-    const int bad = reciprocal_divisors<T, LYAP>(n, L, ldl, U, ldu, Rinv, s_red);
-    low_solve<B, T, LYAP, P, true>(n, L, ldl, U, ldu, C, ldc, W, Rinv, sm);
-    const float nx2 = update_x<T, LYAP>(n, X, ldx, W, n, true, s_red);
+    const DfScale sc = instance_scale<T, LYAP>(n, L, ldl, U, ldu, C, ldc, s_red);
+    const int bad = reciprocal_divisors<T, LYAP>(n, L, ldl, U, ldu, Rinv, s_red, sc.op);
+    low_solve<B, T, LYAP, P, true>(n, L, ldl, U, ldu, C, ldc, W, Rinv, sm, sc);
+    const float nx2 = update_x<T, LYAP>(n, X, ldx, W, n, true, s_red, sc.x);
     int conv = nx2 == 0.0f;
     if (!raw) {
         const float tol = (float)SS_REFINE_TOL;
         const float nx = sqrtf(nx2);
         float prev = nx;
         for (int it = 0; it < MAXIT && !conv; ++it) {
-            residual<B, T, LYAP, RS>(n, L, ldl, U, ldu, C, ldc, X, ldx, W, n, sm);
-            low_solve<B, T, LYAP, P, false>(n, L, ldl, U, ldu, C, ldc, W, Rinv, sm);
-            const float nd = sqrtf(update_x<T, LYAP>(n, X, ldx, W, n, false, s_red));
+            residual<B, T, LYAP, RS>(n, L, ldl, U, ldu, C, ldc, X, ldx, W, n, sm, sc);
+            low_solve<B, T, LYAP, P, false>(n, L, ldl, U, ldu, C, ldc, W, Rinv, sm, sc);
+            const float nd = sqrtf(update_x<T, LYAP>(n, X, ldx, W, n, false, s_red, sc.x));
             const float pred = prev > 0.0f ? nd * (nd / prev) : nd;
             conv = (nd <= tol * nx) || (pred <= tol * nx);
             prev = nd;

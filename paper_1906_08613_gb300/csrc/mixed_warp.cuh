@@ -190,9 +190,10 @@ __device__ void wsolve(int n, const float *Lf, const float *Uf, const float *R, 
 }
 
 // Double-float operand tile staged k-major by one warp from an FP64 block
-// (rows x cols valid; triangle / symmetric-mirror fills as in the blocked path).
+// scaled by 2^sh (rows x cols valid; triangle / symmetric-mirror fills as in
+// the blocked path).
 __device__ __forceinline__ void wstage_df(float2 *S, const double *G, long ld, int rows, int cols, Fill f,
-                                          bool asA, bool trans)
+                                          bool asA, bool trans, int sh)
 {
     const int lane = threadIdx.x & 31;
 #pragma unroll 8
@@ -204,7 +205,7 @@ __device__ __forceinline__ void wstage_df(float2 *S, const double *G, long ld, i
         if (keep && f == F_UPPER) keep = x <= y;
         if (keep) {
             const long idx = (f == F_SYM_LOWER && x < y) ? (y + (long)x * ld) : (x + (long)y * ld);
-            split_df(G[idx], v.x, v.y);
+            split_df_s(G[idx], sh, v.x, v.y);
         }
         // source element (x, y): as op(A)(r = x, k = y); as op(B)(k = x, c = y),
         // or transposed op(B)(k = y, c = x).
@@ -232,10 +233,11 @@ __device__ __forceinline__ void wmicro_df(float (&h)[4][8], float (&l)[4][8], co
     }
 }
 
-// Residual block (I, J) by one warp into W (ld n).
+// Residual block (I, J) by one warp into W (ld n), in the scaled units of sc.
 template <bool LYAP>
 __device__ void warp_residual_block(int n, int I, int J, const double *L, long ldl, const double *U, long ldu,
-                                    const double *C, long ldc, const double *X, long ldx, float *W, float *sm)
+                                    const double *C, long ldc, const double *X, long ldx, float *W, float *sm,
+                                    const DfScale &sc)
 {
     float2 *sA = reinterpret_cast<float2 *>(sm), *sB = sA + TILE;
     const int i0 = I * BW, j0 = J * BW;
@@ -251,26 +253,26 @@ __device__ void warp_residual_block(int n, int I, int J, const double *L, long l
             l[i][j] = 0.f;
             if (r < mI && c < nJ) {
                 if (LYAP && I == J && r < c) { const int t = r; r = c; c = t; }
-                split_df(C[(i0 + r) + (long)(j0 + c) * ldc], h[i][j], l[i][j]);
+                split_df_s(C[(i0 + r) + (long)(j0 + c) * ldc], sc.rhs, h[i][j], l[i][j]);
             }
         }
     for (int K = 0; K <= I; ++K) {                          // L_IK X_KJ
         const int k0 = K * BW, kw = min(BW, n - k0);
         __syncwarp();
-        wstage_df(sA, L + i0 + (long)k0 * ldl, ldl, mI, kw, K == I ? F_LOWER : F_FULL, true, false);
-        if (!LYAP || K > J) wstage_df(sB, X + k0 + (long)j0 * ldx, ldx, kw, nJ, F_FULL, false, false);
-        else if (K == J) wstage_df(sB, X + j0 + (long)j0 * ldx, ldx, kw, nJ, F_SYM_LOWER, false, false);
-        else wstage_df(sB, X + j0 + (long)k0 * ldx, ldx, nJ, kw, F_FULL, false, true);
+        wstage_df(sA, L + i0 + (long)k0 * ldl, ldl, mI, kw, K == I ? F_LOWER : F_FULL, true, false, sc.op);
+        if (!LYAP || K > J) wstage_df(sB, X + k0 + (long)j0 * ldx, ldx, kw, nJ, F_FULL, false, false, sc.x);
+        else if (K == J) wstage_df(sB, X + j0 + (long)j0 * ldx, ldx, kw, nJ, F_SYM_LOWER, false, false, sc.x);
+        else wstage_df(sB, X + j0 + (long)k0 * ldx, ldx, nJ, kw, F_FULL, false, true, sc.x);
         __syncwarp();
         wmicro_df(h, l, sA, sB, kw);
     }
     for (int K = 0; K <= J; ++K) {                          // X_IK U_KJ
         const int k0 = K * BW, kw = min(BW, n - k0);
         __syncwarp();
-        if (LYAP && K == I) wstage_df(sA, X + i0 + (long)i0 * ldx, ldx, mI, kw, F_SYM_LOWER, true, false);
-        else wstage_df(sA, X + i0 + (long)k0 * ldx, ldx, mI, kw, F_FULL, true, false);
-        if (!LYAP) wstage_df(sB, U + k0 + (long)j0 * ldu, ldu, kw, nJ, K == J ? F_UPPER : F_FULL, false, false);
-        else wstage_df(sB, L + j0 + (long)k0 * ldl, ldl, nJ, kw, K == J ? F_LOWER : F_FULL, false, true);
+        if (LYAP && K == I) wstage_df(sA, X + i0 + (long)i0 * ldx, ldx, mI, kw, F_SYM_LOWER, true, false, sc.x);
+        else wstage_df(sA, X + i0 + (long)k0 * ldx, ldx, mI, kw, F_FULL, true, false, sc.x);
+        if (!LYAP) wstage_df(sB, U + k0 + (long)j0 * ldu, ldu, kw, nJ, K == J ? F_UPPER : F_FULL, false, false, sc.op);
+        else wstage_df(sB, L + j0 + (long)k0 * ldl, ldl, nJ, kw, K == J ? F_LOWER : F_FULL, false, true, sc.op);
         __syncwarp();
         wmicro_df(h, l, sA, sB, kw);
     }
@@ -288,7 +290,7 @@ __device__ void warp_residual_block(int n, int I, int J, const double *L, long l
 // warps; one barrier at the end.
 template <int WPC, bool LYAP>
 __device__ void wresidual(int n, const double *L, long ldl, const double *U, long ldu, const double *C,
-                          long ldc, const double *X, long ldx, float *W, float *smem)
+                          long ldc, const double *X, long ldx, float *W, float *smem, const DfScale &sc)
 {
     const int warp = threadIdx.x >> 5;
     float *sm = smem + warp * SLOTS * TILE;
@@ -298,7 +300,7 @@ __device__ void wresidual(int n, const double *L, long ldl, const double *U, lon
     for (int D = 2 * nb - 2; D >= 0; --D) {
         const int ilo = max(LYAP ? (D + 1) / 2 : 0, D - nb + 1), ihi = min(D, nb - 1);
         for (int I = ilo; I <= ihi; ++I, ++q)
-            if (q % WPC == warp) warp_residual_block<LYAP>(n, I, D - I, L, ldl, U, ldu, C, ldc, X, ldx, W, sm);
+            if (q % WPC == warp) warp_residual_block<LYAP>(n, I, D - I, L, ldl, U, ldu, C, ldc, X, ldx, W, sm, sc);
     }
     __syncthreads();
 }
@@ -311,23 +313,24 @@ __device__ void warp_instance(int n, const double *L, long ldl, const double *U,
     const long nn = (long)n * n;
     float *R = W + nn, *Lf = W + 2 * nn, *Uf = W + 3 * nn;
     float *s_red = smem + WPC * SLOTS * TILE;
-    const int bad = reciprocal_divisors<T, LYAP>(n, L, ldl, U, ldu, R, s_red);
+    const DfScale sc = instance_scale<T, LYAP>(n, L, ldl, U, ldu, C, ldc, s_red);
+    const int bad = reciprocal_divisors<T, LYAP>(n, L, ldl, U, ldu, R, s_red, sc.op);
 #pragma unroll 4
     for (long e = threadIdx.x; e < nn; e += T) {
         const int a = (int)(e % n), b = (int)(e / n);
-        Lf[e] = a > b ? d2f_trunc(L[a + (long)b * ldl]) : 0.0f;
+        Lf[e] = a > b ? d2f_trunc_s(L[a + (long)b * ldl], sc.op) : 0.0f;
         const double u = LYAP ? L[b + (long)a * ldl] : U[a + (long)b * ldu];
-        Uf[e] = a < b ? d2f_trunc(u) : 0.0f;
+        Uf[e] = a < b ? d2f_trunc_s(u, sc.op) : 0.0f;
         const double c = (LYAP && a < b) ? C[b + (long)a * ldc] : C[a + (long)b * ldc];
-        W[e] = d2f_trunc(c);
+        W[e] = d2f_trunc_s(c, sc.rhs);
     }
     __syncthreads();
     wsolve<WPC, LYAP>(n, Lf, Uf, R, W, smem);
-    const float nx = sqrtf(update_x<T, LYAP>(n, X, ldx, W, n, true, s_red));
+    const float nx = sqrtf(update_x<T, LYAP>(n, X, ldx, W, n, true, s_red, sc.x));
     int conv = nx == 0.0f || raw;
     float prev = nx;
     for (int it = 0; it < MAXIT && !conv; ++it) {
-        wresidual<WPC, LYAP>(n, L, ldl, U, ldu, C, ldc, X, ldx, W, smem);
+        wresidual<WPC, LYAP>(n, L, ldl, U, ldu, C, ldc, X, ldx, W, smem, sc);
         if (LYAP) {
             for (long e = threadIdx.x; e < nn; e += T) {
                 const int a = (int)(e % n), b = (int)(e / n);
@@ -336,7 +339,7 @@ __device__ void warp_instance(int n, const double *L, long ldl, const double *U,
             __syncthreads();
         }
         wsolve<WPC, LYAP>(n, Lf, Uf, R, W, smem);
-        const float nd = sqrtf(update_x<T, LYAP>(n, X, ldx, W, n, false, s_red));
+        const float nd = sqrtf(update_x<T, LYAP>(n, X, ldx, W, n, false, s_red, sc.x));
         const float pred = prev > 0.0f ? nd * (nd / prev) : nd;
         conv = (nd <= (float)SS_REFINE_TOL * nx) || (pred <= (float)SS_REFINE_TOL * nx);
         prev = nd;

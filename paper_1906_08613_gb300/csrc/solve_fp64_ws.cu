@@ -260,12 +260,14 @@ struct OutMap {
 
 // Where one operand tile of a block-update step comes from: rows x cols at
 // P (leading dimension ld); sym: the symmetric diagonal block whose lower
-// triangle is stored (rows = cols = m).
+// triangle is stored (rows = cols = m); sh: the operand's power-of-two shift
+// in the double-float pipelines (DfScale; 0 and unused in FP64).
 struct Src {
     const double *P;
     long ld;
     int rows, cols;
     bool sym;
+    int sh;
 };
 
 // The tile elements one update thread loads: e = ut + TU*q, (r, c) = (e % B, e / B).
@@ -300,9 +302,9 @@ struct Prefetch {
         }
     }
     // The same tiles as double-float pairs (DF update warps), leading
-    // dimension LDT.
+    // dimension LDT, each operand scaled by 2^sha / 2^shb.
     template <int LDT>
-    __device__ __forceinline__ void store_df(float2 *tA, float2 *tB, bool has_a, int ut) const
+    __device__ __forceinline__ void store_df(float2 *tA, float2 *tB, bool has_a, int ut, int sha, int shb) const
     {
         constexpr int LD = LDT;
 #pragma unroll
@@ -310,10 +312,10 @@ struct Prefetch {
             const int e = ut + TU * q, r = e % B, c = e / B;
             float2 v;
             if (has_a) {
-                split_df(a[q], v.x, v.y);
+                split_df_s(a[q], sha, v.x, v.y);
                 tA[r + c * LD] = v;
             }
-            split_df(b[q], v.x, v.y);
+            split_df_s(b[q], shb, v.x, v.y);
             tB[r + c * LD] = v;
         }
     }
@@ -419,7 +421,7 @@ __device__ __forceinline__ void tile_to_df(float2 *D, const double *S, int ut)
     for (int e = ut; e < B * B; e += TU) {
         const int r = e % B, c = e / B;
         float2 v;
-        split_df(S[r + c * LDT], v.x, v.y);
+        split_df_s(S[r + c * LDT], 0, v.x, v.y);
         D[r + c * LDT] = v;
     }
 }
@@ -440,30 +442,30 @@ __device__ __forceinline__ void upd_df_rt(bool tb, float (&ah)[B * B / TU], floa
 template <int B, bool LYAP>
 __device__ __forceinline__ void step_src(int s, int P1, int I, int J, int mI, int nJ, const double *L, long ldl,
                                          const double *U, long ldu, const double *X, long ldx, Src &a, Src &b,
-                                         bool &tb)
+                                         bool &tb, const DfScale &sc)
 {
     const int i0 = I * B, j0 = J * B;
     if (s < P1) {
         const int k0 = s * B;
-        a = Src{L + i0 + (long)k0 * ldl, ldl, mI, B, false};                 // L_IK
+        a = Src{L + i0 + (long)k0 * ldl, ldl, mI, B, false, sc.op};         // L_IK
         if (!LYAP || s > J) {
-            b = Src{X + k0 + (long)j0 * ldx, ldx, B, nJ, false};             // X_KJ
+            b = Src{X + k0 + (long)j0 * ldx, ldx, B, nJ, false, sc.x};       // X_KJ
             tb = false;
         } else if (s == J) {
-            b = Src{X + j0 + (long)j0 * ldx, ldx, nJ, nJ, true};             // X_JJ (symmetric)
+            b = Src{X + j0 + (long)j0 * ldx, ldx, nJ, nJ, true, sc.x};       // X_JJ (symmetric)
             tb = false;
         } else {
-            b = Src{X + j0 + (long)k0 * ldx, ldx, nJ, B, false};             // X_JK, used transposed
+            b = Src{X + j0 + (long)k0 * ldx, ldx, nJ, B, false, sc.x};       // X_JK, used transposed
             tb = true;
         }
     } else {
         const int k0 = (s - P1) * B;
-        a = Src{X + i0 + (long)k0 * ldx, ldx, mI, B, false};                 // X_IK
+        a = Src{X + i0 + (long)k0 * ldx, ldx, mI, B, false, sc.x};           // X_IK
         if (!LYAP) {
-            b = Src{U + k0 + (long)j0 * ldu, ldu, B, nJ, false};             // U_KJ
+            b = Src{U + k0 + (long)j0 * ldu, ldu, B, nJ, false, sc.op};      // U_KJ
             tb = false;
         } else {
-            b = Src{L + j0 + (long)k0 * ldl, ldl, nJ, B, false};             // L_JK, used transposed
+            b = Src{L + j0 + (long)k0 * ldl, ldl, nJ, B, false, sc.op};      // L_JK, used transposed
             tb = true;
         }
     }
@@ -474,16 +476,17 @@ __device__ __forceinline__ void step_src(int s, int P1, int I, int J, int mI, in
 // L_{I,I-1} (not transposed).
 template <int B, bool LYAP>
 __device__ __forceinline__ void last_src_t(int I, int J, int mI, int nJ, const double *L, long ldl,
-                                           const double *U, long ldu, Src &b, bool &tb)
+                                           const double *U, long ldu, Src &b, bool &tb, const DfScale &sc)
 {
     const int j0 = J * B;
     if (J == 0) {
-        b = Src{L + I * B + (long)(I - 1) * B * ldl, ldl, mI, B, false};
+        b = Src{L + I * B + (long)(I - 1) * B * ldl, ldl, mI, B, false, sc.op};
         tb = false;
         return;
     }
     const int k0 = (J - 1) * B;
-    b = LYAP ? Src{L + j0 + (long)k0 * ldl, ldl, nJ, B, false} : Src{U + k0 + (long)j0 * ldu, ldu, B, nJ, false};
+    b = LYAP ? Src{L + j0 + (long)k0 * ldl, ldl, nJ, B, false, sc.op}
+             : Src{U + k0 + (long)j0 * ldu, ldu, B, nJ, false, sc.op};
     tb = LYAP;
 }
 
@@ -513,9 +516,21 @@ constexpr size_t ws_smem_bytes() { return (size_t)WsTile<B, DF>::N * WsTile<B, D
 // without conversion.  Buffer t & 1 is free when block t starts: the diagonal
 // warp last read it for block t-2, before the "X ready" arrival the update
 // warps waited for in block t-1.
-template <int B, int NU, bool LYAP, bool DF>
-__device__ void syl_ws_instance(int m, int n, const double *L, long ldl, const double *U, long ldu,
-                                const double *C, long ldc, double *X, long ldx, int *info, double *sm)
+//
+// DF status (the return value, valid on thread 0 only): 1 if some
+// double-float intermediate left its range (df_out_of_range: a reciprocal
+// divisor or an entry of X more than 2^60 times the rescaled data, or Inf /
+// NaN), in which case X is not reliable and the caller solves the instance
+// again in FP64; else 0.  The FP64 form always returns 0.
+//
+// DF reads the divisor threshold and, with SC, the rescaling shifts from the
+// scale pre-pass (di).  Without SC the shifts are the constant zero of data
+// in DfScale's band, which keeps the pipeline's registers as without
+// rescaling.
+template <int B, int NU, bool LYAP, bool DF, bool SC = false>
+__device__ int syl_ws_instance(int m, int n, const double *L, long ldl, const double *U, long ldu,
+                               const double *C, long ldc, double *X, long ldx, int *info, double *sm,
+                               const DfInst *di)
 {
     constexpr int LD = WsTile<B, DF>::LD, SZ = WsTile<B, DF>::SZ;
     constexpr int TU = 32 * NU, TALL = TU + 32;
@@ -528,17 +543,30 @@ __device__ void syl_ws_instance(int m, int n, const double *L, long ldl, const d
     }
     double *s_red = sm + WsTile<B, DF>::N * SZ;
     int *s_bad = reinterpret_cast<int *>(s_red + 24);     // DF: a divisor check failed
+    int *s_rng = reinterpret_cast<int *>(s_red + 25);     // DF: range left (see above)
     const int mb = (m + B - 1) / B, nb = (n + B - 1) / B;
 
-    if (DF && threadIdx.x == 0) *s_bad = 0;
-    double md = max_abs_diag(L, ldl, m, s_red);
-    if (!LYAP) md = fmax(md, max_abs_diag(U, ldu, n, s_red));
-    const double delta = divisor_delta(max(m, n), md);
+    double delta;
+    DfScale sc{0, 0, 0};
+    if constexpr (DF) {
+        const DfInst d = *di;
+        if constexpr (SC) sc = DfScale::sylvester(d.eo, d.ec);
+        delta = divisor_delta(max(m, n), __longlong_as_double((long long)d.maxdiag));
+        if (threadIdx.x == 0) {
+            *s_bad = 0;
+            *s_rng = 0;
+        }
+        __syncthreads();
+    } else {
+        double md = max_abs_diag(L, ldl, m, s_red);
+        if (!LYAP) md = fmax(md, max_abs_diag(U, ldu, n, s_red));
+        delta = divisor_delta(max(m, n), md);
+    }
 
     if (threadIdx.x < 32) {
         // ------------------------------------------------ diagonal warp
         const int lane = threadIdx.x;
-        int bad = 0, t = 0;
+        int bad = 0, t = 0, rng = 0;
         for (int I = 0; I < mb; ++I) {
             const int mI = min(B, m - I * B), i0 = I * B;
             if constexpr (!DF) warp_stage_tri<B>(sL, L + i0 + (long)i0 * ldl, ldl, mI, true, lane);
@@ -565,7 +593,8 @@ __device__ void syl_ws_instance(int m, int n, const double *L, long ldl, const d
                         const int r = e % mI, c = e / mI;
                         if (!LYAP || I != J || r >= c) {
                             const float2 v = dT[r + c * LD];
-                            X[(i0 + r) + (long)(j0 + c) * ldx] = df_to_double(v.x, v.y);
+                            rng |= df_out_of_range(v.x);          // every entry of X passes here once
+                            X[(i0 + r) + (long)(j0 + c) * ldx] = df_to_double_s(v.x, v.y, -sc.x);
                         }
                     }
                 } else {
@@ -600,10 +629,13 @@ __device__ void syl_ws_instance(int m, int n, const double *L, long ldl, const d
                 named_arrive(kBarX, TALL);                 // X of block t is final
             }
         }
-        // DF: the update warps set s_bad before their last "T ready" arrival.
+        // DF: the update warps set s_bad and s_rng before their last "T ready"
+        // arrival, which this warp waited for.
         if (DF) bad = *s_bad;
         bad = __any_sync(0xffffffffu, bad);
         if (lane == 0) *info = bad ? 1 : 0;
+        if constexpr (DF) return (__any_sync(0xffffffffu, rng) || *s_rng) ? 1 : 0;
+        return 0;
     } else {
         // ------------------------------------------------- update warps
         constexpr int E = B * B / TU;
@@ -628,21 +660,23 @@ __device__ void syl_ws_instance(int m, int n, const double *L, long ldl, const d
                         const int r = e % B, c = e / B;
                         float2 v = make_float2(0.f, 0.f), w = make_float2(0.f, 0.f);
                         if (r > c && r < mI) {
-                            split_df(L[(i0 + r) + (long)(i0 + c) * ldl], v.x, v.y);
+                            split_df_s(L[(i0 + r) + (long)(i0 + c) * ldl], sc.op, v.x, v.y);
                         } else if (r < c && c < nJ) {
                             const double u = LYAP ? L[(j0 + c) + (long)(j0 + r) * ldl] : U[(j0 + r) + (long)(j0 + c) * ldu];
-                            split_df(u, v.x, v.y);
+                            split_df_s(u, sc.op, v.x, v.y);
                         }
                         if (r < mI && c < nJ && !(sym && r < c)) {
                             const double dd = L[(i0 + r) + (long)(i0 + r) * ldl] +
                                               (LYAP ? L[(j0 + c) + (long)(j0 + c) * ldl] : U[(j0 + c) + (long)(j0 + c) * ldu]);
                             if (!(fabs(dd) > delta)) bad = 1;
-                            split_df(1.0 / dd, w.x, w.y);
+                            split_df_s(1.0 / dd, -sc.op, w.x, w.y);   // 1 / (2^op dd)
+                            if (df_out_of_range(w.x)) bad |= 2;
                         }
                         pLU[r + c * LD] = v;
                         pR[r + c * LD] = w;
                     }
-                    if (bad) *s_bad = 1;
+                    if (bad & 1) *s_bad = 1;
+                    if (bad & 2) *s_rng = 1;
                 }
                 // FP64: even / odd terms; DF: hi / lo of one double-float sum.
                 Acc ae[E], ao[E];
@@ -654,7 +688,7 @@ __device__ void syl_ws_instance(int m, int n, const double *L, long ldl, const d
                         int rr = om.row[r], cc = om.col[r];
                         if (LYAP && I == J && rr < cc) { const int x = rr; rr = cc; cc = x; }
                         const double c = C[(i0 + rr) + (long)(j0 + cc) * ldc];
-                        if constexpr (DF) split_df(c, ae[r], ao[r]);
+                        if constexpr (DF) split_df_s(c, sc.rhs, ae[r], ao[r]);
                         else ae[r] = c;
                     }
                 }
@@ -669,13 +703,13 @@ __device__ void syl_ws_instance(int m, int n, const double *L, long ldl, const d
                 const bool has_last = J > 0 || lfirst;
                 const int nsteps = P1 + (J > 0 ? J - 1 : 0);
                 const int nload = nsteps + (has_last ? 1 : 0);
-                Src sa, sb;
+                Src sa{}, sb{};
                 bool tb = false, tb_next = false;
                 if (nload > 0) {
-                    if (nsteps > 0) step_src<B, LYAP>(0, P1, I, J, mI, nJ, L, ldl, U, ldu, X, ldx, sa, sb, tb_next);
-                    else last_src_t<B, LYAP>(I, J, mI, nJ, L, ldl, U, ldu, sb, tb_next);
+                    if (nsteps > 0) step_src<B, LYAP>(0, P1, I, J, mI, nJ, L, ldl, U, ldu, X, ldx, sa, sb, tb_next, sc);
+                    else last_src_t<B, LYAP>(I, J, mI, nJ, L, ldl, U, ldu, sb, tb_next, sc);
                     pf.load(sa, sb, nsteps > 0, ut);
-                    if constexpr (DF) pf.template store_df<LD>(df2(sA0), df2(sB0), nsteps > 0, ut);
+                    if constexpr (DF) pf.template store_df<LD>(df2(sA0), df2(sB0), nsteps > 0, ut, sa.sh, sb.sh);
                     else pf.store(sA0, sB0, nsteps > 0, ut);
                     named_sync(kBarUpd, TU);
                 }
@@ -685,14 +719,15 @@ __device__ void syl_ws_instance(int m, int n, const double *L, long ldl, const d
                     const bool more = s + 1 < nload;
                     const bool next_bulk = s + 1 < nsteps;
                     if (more) {
-                        if (next_bulk) step_src<B, LYAP>(s + 1, P1, I, J, mI, nJ, L, ldl, U, ldu, X, ldx, sa, sb, tb_next);
-                        else last_src_t<B, LYAP>(I, J, mI, nJ, L, ldl, U, ldu, sb, tb_next);
+                        if (next_bulk) step_src<B, LYAP>(s + 1, P1, I, J, mI, nJ, L, ldl, U, ldu, X, ldx, sa, sb, tb_next, sc);
+                        else last_src_t<B, LYAP>(I, J, mI, nJ, L, ldl, U, ldu, sb, tb_next, sc);
                         pf.load(sa, sb, next_bulk, ut);
                     }
                     if constexpr (DF) {
                         upd_df_rt<B, TU, LD>(tb, ae, ao, om, df2(sA0 + buf * SZ), df2(sB0 + buf * SZ));
                         if (more)
-                            pf.template store_df<LD>(df2(sA0 + (buf ^ 1) * SZ), df2(sB0 + (buf ^ 1) * SZ), next_bulk, ut);
+                            pf.template store_df<LD>(df2(sA0 + (buf ^ 1) * SZ), df2(sB0 + (buf ^ 1) * SZ), next_bulk, ut,
+                                                     sa.sh, sb.sh);
                     } else {
                         upd_fma_rt<B, TU>(tb, ae, ao, om, sA0 + buf * SZ, sB0 + buf * SZ);
                         if (more) pf.store(sA0 + (buf ^ 1) * SZ, sB0 + (buf ^ 1) * SZ, next_bulk, ut);
@@ -734,6 +769,7 @@ __device__ void syl_ws_instance(int m, int n, const double *L, long ldl, const d
         }
         named_sync(kBarX, TALL);                           // X of the last block is final
     }
+    return 0;
 }
 
 // ------------------------------------------------ Cholesky, warp-specialised
@@ -796,16 +832,32 @@ __device__ void warp_trsm_ut(const double *sD, const double *sR, double *sT, int
 
 // DF: the update warps form T in double-float arithmetic (operands split on
 // staging, X_{I-1,J} split into the staging tile the last step leaves free)
-// and round it to FP64; the diagonal warp is the FP64 one.
-template <int B, int NU, bool DF>
-__device__ void chol_ws_instance(int n, const double *A, long lda, double *X, long ldx, int *info, double *sm)
+// and round it to FP64; the diagonal warp is the FP64 one.  The instance is
+// rescaled by powers of two (DfScale::cholesky: A by 4^s, X by 2^s): shared
+// tiles hold scaled values, global X the caller's; the diagonal warp scales
+// the X blocks it stages and unscales what it writes (exact FP64 products).
+//
+// SC, the band check without SC and the status (valid on thread 0): as for
+// syl_ws_instance (the check covers every entry of A, each staged once).
+template <int B, int NU, bool DF, bool SC = false>
+__device__ int chol_ws_instance(int n, const double *A, long lda, double *X, long ldx, int *info, double *sm,
+                                const DfScale &scin)
 {
+    constexpr bool VAL = DF && !SC;
+    constexpr int W = DfScale::BAND_CHOL;
     constexpr int LD = Tile<B>::LD, SZ = Tile<B>::SZ;
     constexpr int TU = 32 * NU, TALL = TU + 32;
     static_assert((B * B) % TU == 0, "update threads must divide the block");
     double *sT0 = sm, *sD = sm + 2 * SZ, *sR = sm + 3 * SZ;
     double *sA0 = sm + 5 * SZ, *sB0 = sm + 7 * SZ;
     const int nb = (n + B - 1) / B;
+    DfScale sc{0, 0, 0};
+    if constexpr (SC) sc = scin;
+    int *s_chk = reinterpret_cast<int *>(sm + 9 * SZ + 26);    // band bits of A (VAL)
+    if constexpr (VAL) {
+        if (threadIdx.x == 0) *s_chk = 0;
+        __syncthreads();                       // before any update warp can set a bit
+    }
 
     if (threadIdx.x < 32) {
         // ------------------------------------------------ diagonal warp
@@ -817,6 +869,10 @@ __device__ void chol_ws_instance(int n, const double *A, long lda, double *X, lo
                 const int i0 = I * B;
                 if (I < J) {
                     warp_stage_tri<B>(sD, X + i0 + (long)i0 * ldx, ldx, B, false, lane);
+                    if constexpr (DF) {
+                        const double f = pow2d(sc.x);            // each lane scales the entries it staged
+                        for (int e = lane; e < B * B; e += 32) sD[e % B + (e / B) * LD] *= f;
+                    }
                     __syncwarp();
                     if (lane < B) sR[lane] = 1.0 / sD[lane * (LD + 1)];
                     __syncwarp();
@@ -832,13 +888,21 @@ __device__ void chol_ws_instance(int n, const double *A, long lda, double *X, lo
                     const int r = e % mI, c = e / mI;
                     // diagonal block: upper part; after a failing pivot only
                     // the rows above it are final.
-                    if (I < J || (r <= c && (!f || r < f - 1)))
-                        X[(i0 + r) + (long)(j0 + c) * ldx] = sT[r + c * LD];
+                    if (I < J || (r <= c && (!f || r < f - 1))) {
+                        if constexpr (DF) X[(i0 + r) + (long)(j0 + c) * ldx] = sT[r + c * LD] * pow2d(-sc.x);
+                        else X[(i0 + r) + (long)(j0 + c) * ldx] = sT[r + c * LD];
+                    }
                 }
                 named_arrive(kBarX, TALL);                 // X of block t is final
             }
         }
         if (lane == 0) *info = fail;
+        if constexpr (VAL) {
+            // The update warps set s_chk before their last "T ready" arrival.
+            const unsigned k = (unsigned)*s_chk;
+            return ((k & BAND_BIG) || !(k & BAND_OP)) ? 2 : 0;
+        }
+        return 0;
     } else {
         // ------------------------------------------------- update warps
         constexpr int E = B * B / TU;
@@ -846,6 +910,7 @@ __device__ void chol_ws_instance(int n, const double *A, long lda, double *X, lo
         OutMap<B, TU> om;
         Prefetch<B, TU> pf;
         using Acc = typename std::conditional<DF, float, double>::type;
+        unsigned chk = 0;                                  // band bits (VAL)
         int t = 0;
         for (int J = 0; J < nb; ++J) {
             const int nJ = min(B, n - J * B), j0 = J * B;
@@ -861,19 +926,19 @@ __device__ void chol_ws_instance(int n, const double *A, long lda, double *X, lo
                 const int nload = nsteps + (has_last && !diag ? 1 : 0);
                 auto bulk_src = [&](int K, Src &sa, Src &sb) {
                     const int k0 = K * B;
-                    sa = Src{X + k0 + (long)i0 * ldx, ldx, B, mI, false};   // X_KI (used transposed)
-                    sb = Src{X + k0 + (long)j0 * ldx, ldx, B, nJ, false};   // X_KJ
+                    sa = Src{X + k0 + (long)i0 * ldx, ldx, B, mI, false, sc.x};   // X_KI (used transposed)
+                    sb = Src{X + k0 + (long)j0 * ldx, ldx, B, nJ, false, sc.x};   // X_KJ
                 };
-                Src sa, sb;
+                Src sa{}, sb{};
                 if (nload > 0) {
                     if (nsteps > 0) {
                         bulk_src(0, sa, sb);
                         pf.load(sa, sb, true, ut);
                     } else {
-                        sb = Src{X + (long)(I - 1) * B + (long)i0 * ldx, ldx, B, mI, false};   // X_{I-1,I}
+                        sb = Src{X + (long)(I - 1) * B + (long)i0 * ldx, ldx, B, mI, false, sc.x};   // X_{I-1,I}
                         pf.load(sa, sb, false, ut);
                     }
-                    if constexpr (DF) pf.template store_df<LD>(df2(sA0), df2(sB0), nsteps > 0, ut);
+                    if constexpr (DF) pf.template store_df<LD>(df2(sA0), df2(sB0), nsteps > 0, ut, sa.sh, sb.sh);
                     else pf.store(sA0, sB0, nsteps > 0, ut);
                     named_sync(kBarUpd, TU);
                 }
@@ -885,8 +950,9 @@ __device__ void chol_ws_instance(int n, const double *A, long lda, double *X, lo
                     ae[r] = 0;
                     if (om.ok(r)) {
                         const double a = A[(i0 + om.row[r]) + (long)(j0 + om.col[r]) * lda];
-                        if constexpr (DF) split_df(a, ae[r], ao[r]);
+                        if constexpr (DF) split_df_s(a, sc.op, ae[r], ao[r]);
                         else ae[r] = a;
+                        if constexpr (VAL) chk |= band_bits<W>(a, BAND_OP);
                     }
                 }
                 for (int s = 0; s < nsteps; ++s) {
@@ -894,13 +960,14 @@ __device__ void chol_ws_instance(int n, const double *A, long lda, double *X, lo
                     const bool more = s + 1 < nload, next_bulk = s + 1 < nsteps;
                     if (more) {
                         if (next_bulk) bulk_src(s + 1, sa, sb);
-                        else sb = Src{X + (long)(I - 1) * B + (long)i0 * ldx, ldx, B, mI, false};
+                        else sb = Src{X + (long)(I - 1) * B + (long)i0 * ldx, ldx, B, mI, false, sc.x};
                         pf.load(sa, sb, next_bulk, ut);
                     }
                     if constexpr (DF) {
                         upd_df_ta<B, TU, LD>(ae, ao, om, df2(sA0 + buf * SZ), df2(sB0 + buf * SZ));
                         if (more)
-                            pf.template store_df<LD>(df2(sA0 + (buf ^ 1) * SZ), df2(sB0 + (buf ^ 1) * SZ), next_bulk, ut);
+                            pf.template store_df<LD>(df2(sA0 + (buf ^ 1) * SZ), df2(sB0 + (buf ^ 1) * SZ), next_bulk, ut,
+                                                     sa.sh, sb.sh);
                     } else {
                         upd_fma_ta<B, TU>(ae, ao, om, sA0 + buf * SZ, sB0 + buf * SZ);
                         if (more) pf.store(sA0 + (buf ^ 1) * SZ, sB0 + (buf ^ 1) * SZ, next_bulk, ut);
@@ -933,17 +1000,24 @@ __device__ void chol_ws_instance(int n, const double *A, long lda, double *X, lo
                     }
                 }
                 named_sync(kBarUpd, TU);                   // staging tiles free again
+                if (VAL && J == nb - 1 && I == J) {
+                    // Before the last arrival: the band bits of the whole instance.
+                    chk = __reduce_or_sync(0xffffffffu, chk);
+                    if ((threadIdx.x & 31) == 0) atomicOr(s_chk, (int)chk);
+                }
                 named_arrive(kBarT, TALL);                 // T of block t is in sT
             }
         }
         named_sync(kBarX, TALL);                           // X of the last block is final
     }
+    return 0;
 }
 
-__device__ __forceinline__ bool next_instance(const Sched &s, int group, int *s_slot, int &b)
+__device__ __forceinline__ bool next_instance(const Sched &s, int group, int *s_slot, int &b,
+                                              int head = META_HEAD)
 {
     const int lo = s.meta[META_RANGE + 2 * group], hi = s.meta[META_RANGE + 2 * group + 1];
-    const int w = lo + claim_slot(s.meta + META_HEAD + group, s_slot);
+    const int w = lo + claim_slot(s.meta + head + group, s_slot);
     if (w >= hi) return false;
     b = s.perm[w];
     return true;
@@ -951,18 +1025,71 @@ __device__ __forceinline__ bool next_instance(const Sched &s, int group, int *s_
 
 // MINB: CTAs per SM the register allocation must allow (the two roles share
 // one register budget, set by the larger of them).
-template <int B, int NU, bool LYAP, int MINB, bool DF>
+// DF without SC: the persistent queue over the group, solving with zero
+// shifts the instances whose data the scale pre-pass found in DfScale's
+// band; the others are left to the SC pass (DfInst::pend and the group's
+// META_SCL flag).  DF with SC: only those instances, solved with their
+// shifts, from a second queue over the group's positions (longest first, as
+// the first); it returns at once when the group's flag is clear.
+template <int B, int NU, bool LYAP, int MINB, bool DF, bool SC>
 __global__ void __launch_bounds__(32 * NU + 32, MINB) syl_ws_kernel(Operands o, Sched s, int group)
 {
     extern __shared__ double sm[];
     __shared__ int s_slot;
+    auto one = [&](int b) {
+        const int n = o.n[b], m = o.m != nullptr ? o.m[b] : n;
+        if (n == 0 || m == 0) { if (threadIdx.x == 0) o.info[b] = 0; return; }
+        if constexpr (DF && !SC) {
+            const DfInst d = s.dfs[b];                        // the same on every thread
+            if (!DfScale::sylvester(d.eo, d.ec).zero()) {
+                if (threadIdx.x == 0) {
+                    const_cast<DfInst *>(s.dfs)[b].pend = 1;
+                    s.meta[META_SCL + group] = 1;
+                }
+                return;
+            }
+        }
+        const double *U = LYAP ? nullptr : o.U[b];
+        const int ldu = LYAP ? 0 : o.ldu[b];
+        const int st = syl_ws_instance<B, NU, LYAP, DF, SC>(m, n, o.A[b], o.lda[b], U, ldu, o.C[b], o.ldc[b], o.X[b],
+                                                            o.ldx[b], o.info + b, sm, DF ? s.dfs + b : nullptr);
+        // Out of the double-float range: syl_ws_fixup_kernel, launched last,
+        // solves the instance again in FP64 (unless X overwrote C).
+        if (DF && st != 0 && threadIdx.x == 0) {
+            o.info[b] = SS_INFO_RANGE;
+            s.meta[META_RNG + group] = 1;
+        }
+    };
     int b;
     claim_init(&s_slot);
-    while (next_instance(s, group, &s_slot, b)) {
+    if constexpr (SC) {
+        if (s.meta[META_SCL + group] == 0) return;            // the same on every thread
+        while (next_instance(s, group, &s_slot, b, META_SCL_HEAD))
+            if (s.dfs[b].pend != 0) one(b);                   // the same on every thread
+    } else {
+        while (next_instance(s, group, &s_slot, b)) one(b);
+    }
+}
+
+// After a double-float launch group: every instance of the group whose info
+// is SS_INFO_RANGE is solved again in FP64 from its right-hand side, unless X
+// overwrote it (X == C), where the code stays.  Usually the group's range
+// flag is clear and every CTA returns after one load; otherwise one CTA per
+// SM strides over the group's positions.  (A separate launch keeps the FP64
+// code out of the double-float kernel's register allocation.)
+template <int B, int NU, bool LYAP, int MINB>
+__global__ void __launch_bounds__(32 * NU + 32, MINB) syl_ws_fixup_kernel(Operands o, Sched s, int group)
+{
+    extern __shared__ double sm[];
+    if (s.meta[META_RNG + group] == 0) return;            // the same on every thread
+    const int lo = s.meta[META_RANGE + 2 * group], hi = s.meta[META_RANGE + 2 * group + 1];
+    for (int w = lo + (int)blockIdx.x; w < hi; w += (int)gridDim.x) {
+        const int b = s.perm[w];
+        if (o.info[b] != SS_INFO_RANGE || o.X[b] == o.C[b]) continue;   // the same on every thread
         const int n = o.n[b], m = o.m != nullptr ? o.m[b] : n;
-        if (n == 0 || m == 0) { if (threadIdx.x == 0) o.info[b] = 0; continue; }
-        syl_ws_instance<B, NU, LYAP, DF>(m, n, o.A[b], o.lda[b], LYAP ? nullptr : o.U[b], LYAP ? 0 : o.ldu[b],
-                                     o.C[b], o.ldc[b], o.X[b], o.ldx[b], o.info + b, sm);
+        __syncthreads();                                      // the previous instance's shared data is dead
+        syl_ws_instance<B, NU, LYAP, false>(m, n, o.A[b], o.lda[b], LYAP ? nullptr : o.U[b], LYAP ? 0 : o.ldu[b],
+                                           o.C[b], o.ldc[b], o.X[b], o.ldx[b], o.info + b, sm, nullptr);
     }
 }
 
@@ -983,49 +1110,118 @@ cudaError_t launch_ws(K kernel, int threads, size_t smem, int batch, cudaStream_
     return cudaGetLastError();
 }
 
+// The range fix-up pass after a double-float group: one CTA per SM (or per
+// instance, if fewer).
+template <typename K>
+cudaError_t launch_fixup(K kernel, int threads, size_t smem, int batch, cudaStream_t st, const Operands &o,
+                         const Sched &s, int group)
+{
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int grid = sm_count();
+    if (grid > batch) grid = batch;
+    if (grid < 1) grid = 1;
+    kernel<<<grid, threads, smem, st>>>(o, s, group);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
-template <int B, int NU, int MINB, bool DF>
+// DF without SC / with SC: as for syl_ws_kernel (an instance out of the band,
+// or solved in place, X == A, is left to the rescaled pass).
+template <int B, int NU, int MINB, bool DF, bool SC>
 __global__ void __launch_bounds__(32 * NU + 32, MINB) chol_ws_kernel(Operands o, Sched s, int group)
 {
     extern __shared__ double sm[];
     __shared__ int s_slot;
+    int *s_scan = reinterpret_cast<int *>(sm + 9 * Tile<B>::SZ);
+    auto pend = [&](int b) {
+        if (threadIdx.x == 0) {
+            const_cast<DfInst *>(s.dfs)[b].pend = 1;
+            s.meta[META_SCL + group] = 1;
+        }
+    };
+    auto one = [&](int b) {
+        const int n = o.n[b];
+        if (n == 0) { if (threadIdx.x == 0) o.info[b] = 0; return; }
+        DfScale sc{0, 0, 0};
+        if constexpr (DF && !SC) {
+            if (o.X[b] == o.A[b]) { pend(b); return; }           // in place: scanned first by the SC pass
+        }
+        if constexpr (SC) {
+            int ea, unused;
+            scan_exp3(ScanOp{o.A[b], o.lda[b], n, n, 2}, ScanOp{nullptr, 0, 0, 0, 0}, ScanOp{nullptr, 0, 0, 0, 0},
+                      threadIdx.x >> 5, (int)(blockDim.x >> 5), threadIdx.x & 31, ea, unused);
+            cta_max2(ea, unused, s_scan);
+            sc = DfScale::cholesky(ea);
+        }
+        const int st = chol_ws_instance<B, NU, DF, SC>(n, o.A[b], o.lda[b], o.X[b], o.ldx[b], o.info + b, sm, sc);
+        if (DF && (st & 2)) pend(b);                            // out of the band: solve again rescaled
+    };
     int b;
     claim_init(&s_slot);
-    while (next_instance(s, group, &s_slot, b)) {
-        const int n = o.n[b];
-        if (n == 0) { if (threadIdx.x == 0) o.info[b] = 0; continue; }
-        chol_ws_instance<B, NU, DF>(n, o.A[b], o.lda[b], o.X[b], o.ldx[b], o.info + b, sm);
+    if constexpr (SC) {
+        if (s.meta[META_SCL + group] == 0) return;              // the same on every thread
+        while (next_instance(s, group, &s_slot, b, META_SCL_HEAD))
+            if (s.dfs[b].pend != 0) one(b);                     // the same on every thread
+    } else {
+        while (next_instance(s, group, &s_slot, b)) one(b);
     }
 }
 
 // Warp-specialised Cholesky configurations: block B, NU update warps; df:
-// double-float update warps (the diagonal warp stays FP64).
+// double-float update warps (the diagonal warp stays FP64), then the scaled
+// pass.
+template <int BB, int NN, int MB>
+cudaError_t launch_chol_df(const Operands &o, const Sched &s, const Launch &l, cudaStream_t st)
+{
+    cudaError_t e = launch_ws(chol_ws_kernel<BB, NN, MB, true, false>, 32 * NN + 32, ws_smem_bytes<BB>(), l.batch, st,
+                              o, s, l.group);
+    if (e != cudaSuccess) return e;
+    return launch_ws(chol_ws_kernel<BB, NN, MB, true, true>, 32 * NN + 32, ws_smem_bytes<BB>(), l.batch, st, o, s,
+                     l.group);
+}
+
 cudaError_t launch_potrf_ws(int block, int nu, bool df, const Operands &o, const Sched &s, const Launch &l,
                             cudaStream_t st)
 {
 #define CWS_CASE(BB, NN, MB)                                                                              \
     if (block == BB && nu == NN)                                                                          \
-        return df ? launch_ws(chol_ws_kernel<BB, NN, MB, true>, 32 * NN + 32, ws_smem_bytes<BB>(), l.batch, st, o, \
-                              s, l.group)                                                                 \
-                  : launch_ws(chol_ws_kernel<BB, NN, MB, false>, 32 * NN + 32, ws_smem_bytes<BB>(), l.batch, st, \
-                              o, s, l.group);
+        return df ? launch_chol_df<BB, NN, MB>(o, s, l, st)                                               \
+                  : launch_ws(chol_ws_kernel<BB, NN, MB, false, false>, 32 * NN + 32, ws_smem_bytes<BB>(), l.batch, \
+                              st, o, s, l.group);
     CWS_CASE(16, 2, 8)
     CWS_CASE(16, 4, 6)
 #undef CWS_CASE
     return cudaErrorInvalidValue;
 }
 
+// A double-float Sylvester / Lyapunov group (three launches): the unscaled
+// pipeline over the queue, the scaled pipeline for the instances it left,
+// then the range fix-up pass.
+template <int BB, int NN, int MB, bool LY>
+cudaError_t launch_syl_df(const Operands &o, const Sched &s, const Launch &l, cudaStream_t st)
+{
+    cudaError_t e = launch_ws(syl_ws_kernel<BB, NN, LY, MB, true, false>, 32 * NN + 32, ws_smem_bytes<BB, true>(),
+                              l.batch, st, o, s, l.group);
+    if (e != cudaSuccess) return e;
+    e = launch_ws(syl_ws_kernel<BB, NN, LY, MB, true, true>, 32 * NN + 32, ws_smem_bytes<BB, true>(), l.batch, st, o,
+                  s, l.group);
+    if (e != cudaSuccess) return e;
+    return launch_fixup(syl_ws_fixup_kernel<BB, NN, LY, MB>, 32 * NN + 32, ws_smem_bytes<BB, false>(), l.batch, st, o,
+                        s, l.group);
+}
+
 // Warp-specialised configurations: block B, NU update warps (+1 diagonal warp);
-// df: double-float update warps.
+// df: double-float update warps (plus the scaled pass and the range fix-up pass).
 cudaError_t launch_syl_ws(int block, int nu, bool lyap, bool df, const Operands &o, const Sched &s, const Launch &l,
                           cudaStream_t st)
 {
 #define WS_ONE(BB, NN, MB, LY, D)                                                                          \
-    launch_ws(syl_ws_kernel<BB, NN, LY, MB, D>, 32 * NN + 32, ws_smem_bytes<BB, D>(), l.batch, st, o, s, l.group)
+    launch_ws(syl_ws_kernel<BB, NN, LY, MB, D, false>, 32 * NN + 32, ws_smem_bytes<BB, D>(), l.batch, st, o, s, l.group)
 #define WS_CASE(BB, NN, MB)                                                                                \
     if (block == BB && nu == NN)                                                                           \
-        return df ? (lyap ? WS_ONE(BB, NN, MB, true, true) : WS_ONE(BB, NN, MB, false, true))              \
+        return df ? (lyap ? launch_syl_df<BB, NN, MB, true>(o, s, l, st) : launch_syl_df<BB, NN, MB, false>(o, s, l, st)) \
                   : (lyap ? WS_ONE(BB, NN, MB, true, false) : WS_ONE(BB, NN, MB, false, false));
     WS_CASE(16, 4, 6)
     WS_CASE(16, 2, 8)

@@ -55,16 +55,16 @@ __device__ __forceinline__ void stage(double *S, const double *G, long ld, int r
     }
 }
 
-// The same staging as double-float pairs (a float2 slot has the size of a
-// double, so the tile layout is unchanged).
+// The same staging as double-float pairs of G * 2^sh (a float2 slot has the
+// size of a double, so the tile layout is unchanged).
 template <int R, int C, int LDS, int T>
-__device__ __forceinline__ void stage_df(float2 *S, const double *G, long ld, int rows, int cols)
+__device__ __forceinline__ void stage_df(float2 *S, const double *G, long ld, int rows, int cols, int sh)
 {
 #pragma unroll 4
     for (int e = threadIdx.x; e < R * C; e += T) {
         const int r = e % R, c = e / R;
         float2 v = make_float2(0.f, 0.f);
-        if (r < rows && c < cols) split_df(G[r + (long)c * ld], v.x, v.y);
+        if (r < rows && c < cols) split_df_s(G[r + (long)c * ld], sh, v.x, v.y);
         S[r + c * LDS] = v;
     }
 }
@@ -72,7 +72,12 @@ __device__ __forceinline__ void stage_df(float2 *S, const double *G, long ld, in
 // CW: right-hand-side columns per chunk (16 or 32; the kernel picks 16 when
 // k <= 16 so that no update multiplies padding columns).  DF (SS_MODE_DF):
 // the block updates in double-float arithmetic on the FP32 pipe, T rounded
-// to FP64 for the FP64 diagonal solve.
+// to FP64 for the FP64 diagonal solve.  DF rescales the system by powers of
+// two so that the largest entries of R and of B lie in [1, 2): R by 2^r and B
+// by 2^q make Y = R^-T B carry 2^(q-r) and X = R^-1 Y carry 2^(q-2r), exactly.
+// The double-float operands take their shift in the split, the FP64 diagonal
+// solves work on the scaled values, and X (holding Y between the passes) is
+// stored in the caller's units.
 template <int BS, int T, int CW, bool DF>
 __device__ void posv_instance(int n, int k, const double *R, long ldr, const double *Bm, long ldb, double *X,
                               long ldx, double *sm)
@@ -86,6 +91,17 @@ __device__ void posv_instance(int n, int k, const double *R, long ldr, const dou
     double *sT = sD + BS * LDR;               // BS x KC: T handed to the diagonal warp
     double *sInv = sT + KC * LDK;             // BS reciprocals 1 / r_ii
     const int nb = (n + BS - 1) / BS;
+    int shR = 0, shY = 0, shX = 0;            // DF: shifts of R, Y and X
+    if constexpr (DF) {
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        int er, eb;
+        scan_exp3(ScanOp{R, ldr, n, n, 2}, ScanOp{nullptr, 0, 0, 0, 0}, ScanOp{Bm, ldb, n, k, 0}, w, T / 32, lane, er, eb);
+        cta_max2(er, eb, reinterpret_cast<int *>(sInv + BS));
+        shR = er ? 1023 - er : 0;
+        const int shB = eb ? 1023 - eb : shR;
+        shY = shB - shR;
+        shX = shB - 2 * shR;
+    }
     for (int c0 = 0; c0 < k; c0 += CW) {
         const int kc = min(CW, k - c0);
         for (int pass = 0; pass < 2; ++pass) {
@@ -97,11 +113,12 @@ __device__ void posv_instance(int n, int k, const double *R, long ldr, const dou
                 float ah[E], al[E];
                 const double *src = fwd ? Bm : X;
                 const long lds = fwd ? ldb : ldx;
+                const int shs = fwd ? shY + shR : shY;            // B: 2^q, Y: 2^(q-r)
 #pragma unroll
                 for (int r = 0; r < E; ++r) {
                     const int e = threadIdx.x + T * r, row = e % BS, col = e / BS;
                     acc[r] = (row < mI && col < kc) ? src[(i0 + row) + (long)(c0 + col) * lds] : 0.0;
-                    if constexpr (DF) split_df(acc[r], ah[r], al[r]);
+                    if constexpr (DF) split_df_s(acc[r], shs, ah[r], al[r]);
                 }
                 const int K0 = fwd ? 0 : I + 1, K1 = fwd ? I : nb;
                 for (int K = K0; K < K1; ++K) {
@@ -109,9 +126,9 @@ __device__ void posv_instance(int n, int k, const double *R, long ldr, const dou
                     __syncthreads();
                     if constexpr (DF) {
                         float2 *dR = reinterpret_cast<float2 *>(sR), *dY = reinterpret_cast<float2 *>(sY);
-                        if (fwd) stage_df<BS, BS, LDR, T>(dR, R + k0 + (long)i0 * ldr, ldr, mK, mI);
-                        else     stage_df<BS, BS, LDR, T>(dR, R + i0 + (long)k0 * ldr, ldr, mI, mK);
-                        stage_df<BS, CW, LDK, T>(dY, X + k0 + (long)c0 * ldx, ldx, mK, kc);
+                        if (fwd) stage_df<BS, BS, LDR, T>(dR, R + k0 + (long)i0 * ldr, ldr, mK, mI, shR);
+                        else     stage_df<BS, BS, LDR, T>(dR, R + i0 + (long)k0 * ldr, ldr, mI, mK, shR);
+                        stage_df<BS, CW, LDK, T>(dY, X + k0 + (long)c0 * ldx, ldx, mK, kc, fwd ? shY : shX);
                     } else {
                         if (fwd) stage<BS, BS, LDR, T>(sR, R + k0 + (long)i0 * ldr, ldr, mK, mI);   // R_KI
                         else     stage<BS, BS, LDR, T>(sR, R + i0 + (long)k0 * ldr, ldr, mI, mK);   // R_IK
@@ -152,6 +169,11 @@ __device__ void posv_instance(int n, int k, const double *R, long ldr, const dou
                 }
                 __syncthreads();
                 stage<BS, BS, LDR, T>(sD, R + i0 + (long)i0 * ldr, ldr, mI, mI);
+                if constexpr (DF) {
+                    // Same thread-to-element map as stage(): each thread scales its own entries.
+                    const Pow2 fr(shR);
+                    for (int e = threadIdx.x; e < BS * BS; e += T) sD[e % BS + (e / BS) * LDR] = fr(sD[e % BS + (e / BS) * LDR]);
+                }
 #pragma unroll
                 for (int r = 0; r < E; ++r) {
                     const int e = threadIdx.x + T * r, row = e % BS, col = e / BS;
@@ -162,6 +184,7 @@ __device__ void posv_instance(int n, int k, const double *R, long ldr, const dou
                 __syncthreads();
                 if (threadIdx.x < 32) {
                     const int j = threadIdx.x;          // column of the chunk
+                    const Pow2 fo(DF ? (fwd ? -shY : -shX) : 0);   // back to the caller's units
                     double t[BS];
 #pragma unroll
                     for (int i = 0; i < BS; ++i) t[i] = sT[i + j * LDK];
@@ -189,7 +212,10 @@ __device__ void posv_instance(int n, int k, const double *R, long ldr, const dou
                     if (j < kc)
 #pragma unroll
                         for (int i = 0; i < BS; ++i)
-                            if (i < mI) X[(i0 + i) + (long)(c0 + j) * ldx] = t[i];
+                            if (i < mI) {
+                                if constexpr (DF) X[(i0 + i) + (long)(c0 + j) * ldx] = fo(t[i]);
+                                else X[(i0 + i) + (long)(c0 + j) * ldx] = t[i];
+                            }
                 }
                 __syncthreads();
             }
@@ -197,8 +223,10 @@ __device__ void posv_instance(int n, int k, const double *R, long ldr, const dou
     }
 }
 
+// One persistent CTA per system, over the same size-sorted order as the
+// factor launch.
 template <int CW, bool DF>
-__global__ void __launch_bounds__(128) posv_kernel(PosvOps o, Sched s, int group)
+__device__ __forceinline__ void posv_loop(const PosvOps &o, const Sched &s, int group)
 {
     constexpr int BS = 16, T = 128;
     extern __shared__ double sm[];
@@ -220,6 +248,20 @@ __global__ void __launch_bounds__(128) posv_kernel(PosvOps o, Sched s, int group
     }
 }
 
+// FP64 and double-float forms; the double-float one is held to five CTAs per
+// SM (seven for 16-column chunks), as without its scaling shifts.
+template <int CW>
+__global__ void __launch_bounds__(128) posv_kernel(PosvOps o, Sched s, int group)
+{
+    posv_loop<CW, false>(o, s, group);
+}
+
+template <int CW>
+__global__ void __launch_bounds__(128, CW == 16 ? 7 : 5) posv_df_kernel(PosvOps o, Sched s, int group)
+{
+    posv_loop<CW, true>(o, s, group);
+}
+
 }  // namespace
 
 // The solve stage on the queue head `group` over all valid instances.
@@ -228,9 +270,9 @@ cudaError_t launch_posv_solve(const int *d_n, const int *d_k, int max_k, const d
                               int *d_info, const Sched &s, int group, int batch, cudaStream_t st, bool df)
 {
     constexpr int BS = 16, T = 128;
-    const size_t smem = (size_t)(2 * BS * (BS + 1) + 2 * KC * (BS + 1) + BS) * sizeof(double);
-    auto kernel = max_k <= 16 ? (df ? posv_kernel<16, true> : posv_kernel<16, false>)
-                              : (df ? posv_kernel<KC, true> : posv_kernel<KC, false>);
+    const size_t smem = (size_t)(2 * BS * (BS + 1) + 2 * KC * (BS + 1) + BS + 4) * sizeof(double);
+    auto kernel = max_k <= 16 ? (df ? posv_df_kernel<16> : posv_kernel<16>)
+                              : (df ? posv_df_kernel<KC> : posv_kernel<KC>);
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;

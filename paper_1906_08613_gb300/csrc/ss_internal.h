@@ -29,6 +29,11 @@ struct Operands {
 //   meta[META_BIN_LO + k]     first position (in perm) of size bin k
 //   meta[META_BIN_HI + k]     one past the last position of size bin k
 //   meta[META_HEAD + g]       work-queue head of launch group g
+//   meta[META_RNG + g]        nonzero if a double-float solve of group g left
+//                             its range (an instance has info SS_INFO_RANGE)
+//   meta[META_SCL + g]        nonzero if an instance of double-float group g
+//                             needs rescaling (DfInst::pend)
+//   meta[META_SCL_HEAD + g]   work-queue head of that scaled pass
 //   perm[w]                   instance index at position w (sizes descending)
 //   scr[w]                    element offset of position w's scratch area
 constexpr int META_COUNT = 0;
@@ -37,12 +42,30 @@ constexpr int META_BIN_HI = 32;
 constexpr int META_HEAD = 48;
 constexpr int META_RANGE = 64;     // pairs (lo, hi) per launch group, 2 * MAX_GROUPS
 constexpr int MAX_GROUPS = 16;
-constexpr int META_INTS = 128;
-constexpr int NUM_BINS = 13;       // bin(n) = ceil(log2(max(n,1))), n <= 4096
+constexpr int META_RNG = 96;       // MAX_GROUPS flags
+constexpr int META_SCL = 112;      // MAX_GROUPS flags
+constexpr int META_SCL_HEAD = 128; // MAX_GROUPS queue heads
+constexpr int META_INTS = 144;
+constexpr int NUM_BINS = SS_NUM_BINS;   // bin(n) = ceil(log2(max(n,1))), n <= 4096
+
+// Per-instance state of the double-float pipelines.  Sylvester / Lyapunov:
+// the scale pre-pass writes the largest biased FP64 exponents of the
+// operator (L and U) and of the right-hand side, and the largest diagonal
+// magnitude of L and U (the singular-divisor threshold).  pend: set by the
+// unscaled pipeline when the instance needs the rescaled one (Cholesky:
+// found out of DfScale's band while the solve read A).  The binning pre-pass
+// zeroes every entry.
+struct DfInst {
+    int eo, ec;
+    int pend;
+    int pad;
+    unsigned long long maxdiag;   // bits of a nonnegative double
+};
 
 struct Sched {
     int *meta;
     const int *perm;
+    const DfInst *dfs;         // per instance, indexed by instance (SS_MODE_DF / AUTO calls), may be null
     const long long *scr;      // scratch offsets (elements), may be null
     void *scratch;             // scratch base, may be null
     long long scratch_elems;   // capacity in elements of the scratch element type
@@ -58,17 +81,24 @@ struct Launch {
 };
 
 size_t workspace_bytes(int op, int batch, int max_n, int mode);
-void carve_workspace(void *d_work, int batch, int max_n, int mode, Sched *s);
+// The parts of a workspace of work_bytes laid out as workspace_bytes counts them.
+void carve_workspace(void *d_work, size_t work_bytes, int op, int batch, int max_n, int mode, Sched *s);
 
 // Binning pre-pass: sorts valid instances by size (descending), fills bins,
 // scratch offsets and the launch-group ranges, resets the queue heads.
 // group_of_bin[k] is the launch group of size bin k (-1: none, only for bins
 // that cannot hold instances); ngroups groups are used.
 // With d_m (rectangular Sylvester) the sort key of an instance is max(m, n),
-// and m outside [0, max_m] is a bad size too.
+// and m outside [0, max_m] is a bad size too.  It also zeroes s.dfs when
+// present.
 cudaError_t launch_binning(int batch, int max_n, const int *d_n, int *d_info, const Sched &s,
                            const int *group_of_bin, int ngroups, long long scratch_per_n2,
                            cudaStream_t st, const int *d_m = nullptr, int max_m = 0);
+
+// Scale pre-pass of the double-float Sylvester / Lyapunov pipelines: s.dfs[b]
+// for every instance in the binning pass's order (one CTA per instance at a
+// time, all in parallel).  Runs after the binning pre-pass.
+cudaError_t launch_df_scale(int op, int batch, const Operands &o, const Sched &s, cudaStream_t st);
 
 // Configuration tables.
 struct Config {

@@ -69,6 +69,20 @@ class DeviceBatch:
                            p["S"].data_ptr(), ld, p["X"].data_ptr(), ld, self.info.data_ptr(),
                            **common)
 
+    def autotune(self, mode: int, reps: int = 3, stream: int = 0):
+        """ss_autotune on this batch: (ms per configuration, bad instances per
+        configuration, best configuration) of `mode`."""
+        self.ensure_work(mode)
+        p = self.ptrs
+        ld = self.d_ld.data_ptr()
+        names = {"potrf": ("A", None, None), "trsyl": ("L", "U", "C"), "trlyap": ("L", None, "S")}[self.op]
+        a, b, c = (p[k] if k is not None else None for k in names)
+        ptr = lambda t: t.data_ptr() if t is not None else 0
+        return ss.ss_autotune(ss.OPS[self.op], mode, self.batch, self.max_n, self.d_n.data_ptr(), ptr(a), ld,
+                              ptr(b), ld if b is not None else 0, ptr(c), ld if c is not None else 0,
+                              p["X"].data_ptr(), ld, self.info.data_ptr(), self.work.data_ptr(), self.work_bytes,
+                              reps=reps, stream=stream)
+
     def x_host(self) -> np.ndarray:
         return self.X.cpu().numpy()
 
@@ -98,7 +112,8 @@ class DeviceRectBatch:
         self.ptrs = {k: (v.data_ptr() + to(off[k] * 8)).contiguous() for k, v in self.bufs.items()}
         self.ptrs["X"] = (self.X.data_ptr() + to(pk.offC * 8)).contiguous()
         self.info = torch.full((max(self.batch, 1),), 12345, dtype=torch.int32, device=self.device)
-        need = ss.ss_workspace_size(ss.OP_TRSYL, self.batch, max(self.max_m, self.max_n), ss.MODE_FP64)
+        # sized for SS_MODE_DF, which needs more than FP64 (its scale array)
+        need = ss.ss_workspace_size(ss.OP_TRSYL, self.batch, max(self.max_m, self.max_n), ss.MODE_DF)
         self.work = torch.empty(max(need, 256), dtype=torch.uint8, device=self.device)
 
     def solve(self, cfg: int = ss.CFG_DEFAULT, mode: int = ss.MODE_FP64, stream: int = 0,
@@ -139,7 +154,8 @@ class DevicePosvBatch:
         self.ptrs = {"A": (self.bufs["A"].data_ptr() + oA).contiguous(), "R": (self.R.data_ptr() + oA).contiguous(),
                      "B": (self.bufs["B"].data_ptr() + oB).contiguous(), "X": (self.X.data_ptr() + oB).contiguous()}
         self.info = torch.full((max(self.batch, 1),), 12345, dtype=torch.int32, device=self.device)
-        need = ss.ss_workspace_size(ss.OP_POTRF, self.batch, self.max_n, ss.MODE_FP64)
+        # sized for SS_MODE_DF, which needs more than FP64 (its scale array)
+        need = ss.ss_workspace_size(ss.OP_POTRF, self.batch, self.max_n, ss.MODE_DF)
         self.work = torch.empty(max(need, 256), dtype=torch.uint8, device=self.device)
 
     def solve(self, cfg: int = ss.CFG_DEFAULT, mode: int = ss.MODE_FP64, stream: int = 0,

@@ -311,3 +311,76 @@ def make_batch(op: str, n, seed: int) -> Packed:
     if op == "trlyap":
         return lyapunov_batch(n, seed)
     raise ValueError(f"unknown op {op!r}")
+
+
+# ---- magnitude: instances rescaled by powers of two ----
+#
+# The problems are plain double precision (the paper's "Preliminary
+# performance results" paragraph), so a solver must give the same accuracy on
+# data of any magnitude.  Multiplying an instance's operands by powers of two
+# is exact in FP64, which makes these scaled copies test inputs whose
+# solutions are known exactly in terms of the unscaled ones.
+
+RANGE_SHIFTS = (0, 70, -70, 100, -100, 130, -130)
+
+
+def scale_instances(pk, op: str, shifts) -> None:
+    """In place: instance b's operator by 2^s_op and its right-hand side by
+    2^s_rhs, with shifts[b] = (s_op, s_rhs).  Sylvester / Lyapunov (Packed):
+    L and U (or L) by 2^s_op, C (or S) by 2^s_rhs, so X becomes
+    2^(s_rhs - s_op) X.  Cholesky (Packed): A by 2^s_op (s_op even, X by
+    2^(s_op / 2)); s_rhs is unused.  Rectangular Sylvester (RectPacked): as
+    Sylvester.  SPD solve (PosvPacked): A by 2^s_op, B by 2^s_rhs.  The stored
+    X0 is scaled to match (Cholesky, SPD solve: left as it is)."""
+    for b, (so, sr) in enumerate(shifts):
+        if isinstance(pk, RectPacked):
+            mb, nb = int(pk.m[b]), int(pk.n[b])
+            for name, o, cnt, s in (("L", pk.offL, mb * mb, so), ("U", pk.offU, nb * nb, so),
+                                    ("C", pk.offC, mb * nb, sr), ("X0", pk.offC, mb * nb, sr - so)):
+                seg = slice(int(o[b]), int(o[b]) + cnt)
+                pk.ops[name][seg] = np.ldexp(pk.ops[name][seg], s)
+            continue
+        if isinstance(pk, PosvPacked):
+            nb, kb = int(pk.n[b]), int(pk.k[b])
+            for name, o, cnt, s in (("A", pk.offA, nb * nb, so), ("B", pk.offB, nb * kb, sr)):
+                seg = slice(int(o[b]), int(o[b]) + cnt)
+                pk.ops[name][seg] = np.ldexp(pk.ops[name][seg], s)
+            continue
+        nb, o = int(pk.n[b]), int(pk.off[b])
+        seg = slice(o, o + nb * nb)
+        if op == "potrf":
+            if so % 2:
+                raise ValueError("a Cholesky operator shift must be even")
+            pk.ops["A"][seg] = np.ldexp(pk.ops["A"][seg], so)
+            pk.ops["X0"][seg] = np.ldexp(pk.ops["X0"][seg], so // 2)
+            continue
+        names = ("L", "U") if op == "trsyl" else ("L",)
+        for name in names:
+            pk.ops[name][seg] = np.ldexp(pk.ops[name][seg], so)
+        rhs = "C" if op == "trsyl" else "S"
+        pk.ops[rhs][seg] = np.ldexp(pk.ops[rhs][seg], sr)
+        pk.ops["X0"][seg] = np.ldexp(pk.ops["X0"][seg], sr - so)
+
+
+def range_shifts(batch: int, op: str, seed: int = 0):
+    """Per-instance (s_op, s_rhs) pairs that mix well-scaled instances with
+    instances scaled by 2^+-70, 2^+-100 and 2^+-130, cycling through those
+    shifts s: instance b gets, by b mod 4, no scaling, (s, s) (the whole
+    instance; X unchanged), (0, s) (the right-hand side; X by 2^s) or
+    (s, -s) (X by 2^-2s).  Cholesky: (2s, 0), so that X moves by 2^s.  The
+    start of the cycle depends on the seed."""
+    nz = [s for s in RANGE_SHIFTS if s != 0]
+    out = []
+    for b in range(batch):
+        s = nz[(b // 4 + seed) % len(nz)]
+        if b % 4 == 0:
+            out.append((0, 0))
+        elif op == "potrf":
+            out.append((2 * s, 0))
+        elif b % 4 == 1:
+            out.append((s, s))
+        elif b % 4 == 2:
+            out.append((0, s))
+        else:
+            out.append((s, -s))
+    return out

@@ -3,10 +3,11 @@ batch, precision mode) bucket, the run time of every kernel configuration, so
 that the fastest (mode, configuration) can be chosen without timing them.
 
 The paper names this as future work: replacing the autotuning loops with a
-model-based approach ("Limitations and future work" paragraph).  The network
-and its training run in the library's CUDA kernels (``ss_mlp_forward``,
-``ss_mlp_grad``, ``ss_mlp_adam``); this module only encodes features, moves
-arrays and picks the argmin.  The exhaustive autotuner (``tune.py``) produces
+model-based approach ("Limitations and future work" paragraph).  The network,
+its training and the choice it makes run in the library (``ss_selector_train``,
+``ss_selector_predict``, the CUDA kernels behind ``ss_mlp_*``); this module
+builds the training rows from the tuning database, moves arrays and keeps the
+model's files.  The exhaustive autotuner (``tune.py``) produces
 the training table, stays the fallback, and is the yardstick of the selector's regret.
 
 Features (SS_MLP_IN = 10): op one-hot (potrf, trsyl, trlyap), log2(n)/9,
@@ -124,34 +125,51 @@ class Selector:
             cnt = min(cnt, int(self.cfg_counts.get(f"{op}:{mode}", 0)))
         return cnt
 
+    # ------------------------------------------------- the library's model
+    def tables(self):
+        """(cfg_count, batch_max) in the layout of ss_selector_set (None where
+        this selector has no such record)."""
+        cc = None
+        if self.cfg_counts is not None:
+            cc = [int(self.cfg_counts.get(f"{op}:{m}", 0)) for op in OP_ORDER for m in MODE_ORDER]
+        bm = None
+        if self.batch_max is not None:
+            bm = [0] * (len(OP_ORDER) * ss.NUM_BINS * len(MODE_ORDER))
+            for key, v in self.batch_max.items():
+                op, k, m = key.split(":")
+                bm[(OP_ORDER.index(op) * ss.NUM_BINS + int(k)) * len(MODE_ORDER) + MODE_ORDER.index(m)] = int(v)
+        return cc, bm
+
+    def push(self):
+        """Make this the library's model (ss_selector_set); the choices below
+        are the library's (ss_selector_predict)."""
+        ss.ss_selector_set(self.params, *self.tables())
+
+    def pull(self):
+        """Take the library's model (after ss_selector_train)."""
+        p, cc, bm = ss.ss_selector_get()
+        self.params = p
+        self.cfg_counts = {f"{op}:{m}": cc[i * len(MODE_ORDER) + j]
+                           for i, op in enumerate(OP_ORDER) for j, m in enumerate(MODE_ORDER)}
+        self.batch_max = {}
+        for i, op in enumerate(OP_ORDER):
+            for k in range(ss.NUM_BINS):
+                for j, m in enumerate(MODE_ORDER):
+                    v = bm[(i * ss.NUM_BINS + k) * len(MODE_ORDER) + j]
+                    if v > 0:
+                        self.batch_max[f"{op}:{k}:{m}"] = v
+
     # ----------------------------------------------------------- training
     def train(self, X, T, M, steps=3000, lr=3e-3, log_every=0, log=print):
-        """Adam on the masked MSE, on the GPU; returns the loss history."""
-        import torch
-        dev = torch.device(self.device)
-        t = lambda a: torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device=dev)
-        P, dX, dT, dM = t(self.params), t(X), t(T), t(M)
-        G = torch.zeros_like(P)
-        m1 = torch.zeros_like(P)
-        m2 = torch.zeros_like(P)
-        L = torch.zeros(1, dtype=torch.float32, device=dev)
-        rows = int(X.shape[0])
-        wb = ss.ss_mlp_workspace_size(rows)
-        W = torch.empty(max(wb, 4), dtype=torch.uint8, device=dev)
-        total = float(M.sum())
-        self.cfg_counts = trained_cfg_counts(X, M)
-        self.batch_max = trained_batch_max(X)
-        hist = []
-        for step in range(1, steps + 1):
-            ss.ss_mlp_grad(P.data_ptr(), rows, dX.data_ptr(), dT.data_ptr(), dM.data_ptr(), total,
-                           G.data_ptr(), L.data_ptr(), W.data_ptr(), wb)
-            ss.ss_mlp_adam(P.data_ptr(), G.data_ptr(), m1.data_ptr(), m2.data_ptr(), step, lr)
-            if step == 1 or step % 50 == 0 or step == steps:
-                hist.append((step, float(L.item())))
-                if log_every and step % log_every == 0:
-                    log(f"step {step} loss {hist[-1][1]:.5f}")
-        torch.cuda.synchronize(dev)
-        self.params = P.cpu().numpy()
+        """Adam on the masked MSE by the library's kernels on the GPU
+        (ss_selector_train, from this selector's parameters); returns the loss
+        history as (step, loss) pairs."""
+        loss = ss.ss_selector_train(X, T, M, steps, lr, init=self.params)
+        self.pull()
+        hist = [(s, float(loss[s - 1])) for s in range(1, steps + 1) if s == 1 or s % 50 == 0 or s == steps]
+        if log_every:
+            for s in range(log_every, steps + 1, log_every):
+                log(f"step {s} loss {float(loss[s - 1]):.5f}")
         return hist
 
     # ---------------------------------------------------------- inference
@@ -168,82 +186,51 @@ class Selector:
         torch.cuda.synchronize(dev)
         return Y.cpu().numpy()
 
-    def query_batch(self, op: str, n: float, batch: float, mode: str):
-        """(batch fed to the network, factor on its prediction) for `batch`
-        instances of order n in `mode` (see batch_max)."""
-        if self.batch_max:
-            bmax = self.batch_max.get(f"{op}:{ss.size_bin(int(round(n)))}:{mode}")
-            if bmax and batch > bmax:
-                return float(bmax), batch / float(bmax)
-        return batch, 1.0
+    def _predict_table(self, op: str, counts, policy):
+        self.push()
+        return ss.ss_selector_predict(ss.OPS[op], list(counts), policy)
+
+    def decide_with(self, predict_fn, op: str, counts, policy=ss.SELECTOR_PER_BIN):
+        """The library's decision (ss_selector_queries / ss_selector_decide)
+        on predictions from predict_fn(feature rows) instead of the network."""
+        self.push()
+        X = ss.ss_selector_queries(ss.OPS[op], list(counts))
+        Y = np.asarray(predict_fn(X), dtype=np.float32).reshape(len(X), ss.MLP_OUT)
+        return ss.ss_selector_decide(ss.OPS[op], list(counts), policy, Y)
 
     def choose_many(self, queries):
-        """queries: list of (op, n, batch) -> list of (mode, cfg, predicted ms)."""
-        rows, idx = [], []
-        for qi, (op, n, batch) in enumerate(queries):
-            for mode in MODE_ORDER:
-                cnt = self.n_cfgs(op, mode)
-                if cnt <= 0:
-                    continue
-                fb, scale = self.query_batch(op, n, batch, mode)
-                rows.append(features(op, n, fb, mode))
-                idx.append((qi, mode, cnt, scale))
-        Y = self.predict(np.array(rows)) if rows else np.zeros((0, ss.MLP_OUT))
-        best = [None] * len(queries)
-        for (qi, mode, cnt, scale), y in zip(idx, Y):
-            c = int(np.argmin(y[:cnt]))
-            v = float(y[c]) + math.log2(scale)
-            if best[qi] is None or v < best[qi][2]:
-                best[qi] = (mode, c, v)
-        return [(m, c, 2.0 ** v) for (m, c, v) in best]
+        """queries: list of (op, n, batch) -> list of (mode, cfg, predicted ms),
+        each the library's per-bin choice for `batch` instances in bin(n)."""
+        inv = {v: k for k, v in ss.MODES.items()}
+        out = []
+        for op, n, batch in queries:
+            k = ss.size_bin(int(round(n)))
+            counts = [0] * ss.NUM_BINS
+            counts[k] = int(round(batch))
+            modes, cfgs, ms = self._predict_table(op, counts, ss.SELECTOR_PER_BIN)
+            out.append((inv[modes[k]], cfgs[k], ms))
+        return out
 
     def auto_table(self, op: str, batch, nbins: int = ss.NUM_BINS):
         """Per-bin (mode ids, cfg ids) for ss_set_auto_table.  `batch` is the
         number of instances per size bin (a list, or one number for all);
         bins with no instances keep the library default (-1)."""
         counts = list(batch) if hasattr(batch, "__len__") else [batch] * nbins
-        want = [k for k in range(nbins) if counts[k] > 0]
-        ch = self.choose_many([(op, bin_center(k), counts[k]) for k in want])
-        modes, cfgs = [-1] * nbins, [-1] * nbins
-        for k, (m, c, _) in zip(want, ch):
-            modes[k], cfgs[k] = ss.MODES[m], c
+        modes, cfgs, _ = self._predict_table(op, counts[:nbins], ss.SELECTOR_PER_BIN)
         return modes, cfgs
 
     def call_choice(self, op: str, batch, nbins: int = ss.NUM_BINS):
-        """One (mode, cfg) for a whole call: the candidate whose predicted
-        total over the call's size bins (bin k with batch[k] instances) is
-        smallest.  One launch keeps every size in one persistent queue, whose
-        longest-first order balances the SMs; a different choice per bin would
-        split the call into serialized launches, each with its own tail."""
+        """One (mode, cfg, predicted ms) for a whole call (SS_SELECTOR_CALL)."""
         counts = list(batch) if hasattr(batch, "__len__") else [batch] * nbins
-        want = [k for k in range(nbins) if counts[k] > 0]
-        rows, cand, scales = [], [], []
-        for mode in MODE_ORDER:
-            cnt = self.n_cfgs(op, mode)
-            if cnt <= 0:
-                continue
-            cand.append((mode, cnt))
-            for k in want:
-                fb, scale = self.query_batch(op, bin_center(k), counts[k], mode)
-                rows.append(features(op, bin_center(k), fb, mode))
-                scales.append(scale)
-        Y = self.predict(np.array(rows)) if rows else np.zeros((0, ss.MLP_OUT))
-        best, i = None, 0
-        for mode, cnt in cand:
-            tot = np.zeros(cnt)
-            for _ in want:
-                tot += scales[i] * 2.0 ** Y[i, :cnt]
-                i += 1
-            c = int(np.argmin(tot))
-            if best is None or tot[c] < best[2]:
-                best = (mode, c, float(tot[c]))
-        return best
+        modes, cfgs, ms = self._predict_table(op, counts[:nbins], ss.SELECTOR_CALL)
+        inv = {v: k for k, v in ss.MODES.items()}
+        return inv[modes[0]], cfgs[0], ms
 
     def call_table(self, op: str, batch, nbins: int = ss.NUM_BINS):
-        """AUTO table with the single call_choice in every bin that has instances."""
+        """AUTO table with the single call choice in every bin."""
         counts = list(batch) if hasattr(batch, "__len__") else [batch] * nbins
-        mode, cfg, _ = self.call_choice(op, counts, nbins)
-        return [ss.MODES[mode]] * nbins, [cfg] * nbins
+        modes, cfgs, _ = self._predict_table(op, counts[:nbins], ss.SELECTOR_CALL)
+        return modes, cfgs
 
     def install(self, op: str, batch, per_bin: bool = False):
         modes, cfgs = (self.auto_table if per_bin else self.call_table)(op, batch)

@@ -41,8 +41,15 @@ CFG_TABLE = -2
 
 ERR_CUDA = -100
 ERR_SCRATCH_LIMIT = -101
+ERR_IO = -102
+ERR_NO_SELECTOR = -103
+SELECTOR_PER_BIN = 0
+SELECTOR_CALL = 1
+SELECTOR_MODES = (MODE_FP64, MODE_FP32_REFINED, MODE_TF32_REFINED, MODE_BF16_REFINED, MODE_DF)
+SELECTOR_MAX_ROWS = 13 * 5
 INFO_BAD_SIZE = -1
 INFO_ALIASED = -3
+INFO_RANGE = -4
 INFO_NO_WORK = -2
 MAX_N = 4096
 MLP_IN, MLP_HIDDEN, MLP_OUT = 10, 64, 8
@@ -108,6 +115,23 @@ def lib():
             L.ss_profile_enable.restype = i
             L.ss_profile_read.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i)]
             L.ss_profile_read.restype = i
+            fp = ctypes.POINTER(fl)
+            dp = ctypes.POINTER(ctypes.c_double)
+            L.ss_autotune.argtypes = [i, i, i, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, i, fp, ip, ip, vp]
+            L.ss_selector_set.argtypes = [fp, ip, ip]
+            L.ss_selector_get.argtypes = [fp, ip, ip]
+            L.ss_selector_clear.argtypes = []
+            L.ss_selector_save.argtypes = [ctypes.c_char_p]
+            L.ss_selector_load.argtypes = [ctypes.c_char_p]
+            L.ss_selector_train.argtypes = [fp, fp, fp, i, fp, i, fl, fp, vp]
+            L.ss_selector_queries.argtypes = [i, i, ip, fp, ip]
+            L.ss_selector_decide.argtypes = [i, i, ip, i, fp, ip, ip, dp]
+            L.ss_selector_predict.argtypes = [i, i, ip, i, ip, ip, dp, vp]
+            L.ss_selector_install.argtypes = [i, i, ip, i, vp]
+            for f in (L.ss_autotune, L.ss_selector_set, L.ss_selector_get, L.ss_selector_clear, L.ss_selector_save,
+                      L.ss_selector_load, L.ss_selector_train, L.ss_selector_queries, L.ss_selector_decide,
+                      L.ss_selector_predict, L.ss_selector_install):
+                f.restype = i
             _lib = L
     return _lib
 
@@ -243,3 +267,116 @@ def size_bin(n: int) -> int:
     while (1 << k) < n:
         k += 1
     return k
+
+
+# ---------------------------------------------------------------- autotuner
+
+def ss_autotune(op, mode, batch, max_n, d_n, d_A, d_lda, d_B, d_ldb, d_C, d_ldc, d_X, d_ldx, d_info,
+                d_work, work_bytes, reps=3, stream=0):
+    """Times every configuration of `mode` on the given batch (see the header);
+    returns (ms per configuration, bad instances per configuration, best cfg)."""
+    cnt = ss_config_count(op, mode)
+    ms = (ctypes.c_float * max(cnt, 1))()
+    bad = (ctypes.c_int * max(cnt, 1))()
+    best = ctypes.c_int(-1)
+    _check(lib().ss_autotune(op, mode, batch, max_n, d_n, d_A, d_lda, d_B or None, d_ldb or None, d_C or None,
+                             d_ldc or None, d_X, d_ldx, d_info, d_work, work_bytes, reps, ms, bad,
+                             ctypes.byref(best), stream or None), "ss_autotune")
+    return [float(v) for v in ms[:cnt]], [int(v) for v in bad[:cnt]], int(best.value)
+
+
+# ------------------------------------------------------------------ selector
+
+def _int_array(vals):
+    return (ctypes.c_int * max(1, len(vals)))(*[int(v) for v in vals])
+
+
+def _float_ptr(a):
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def ss_selector_set(params, cfg_count=None, batch_max=None) -> None:
+    """params: SS_MLP_PARAMS floats; cfg_count: 15 ints (op * 5 + selector
+    mode) or None; batch_max: 3 * 13 * 5 ints or None."""
+    keep, pp = _float_ptr(params)
+    assert keep.size == MLP_PARAMS
+    cc = _int_array(cfg_count) if cfg_count is not None else None
+    bm = _int_array(batch_max) if batch_max is not None else None
+    _check(lib().ss_selector_set(pp, cc, bm), "ss_selector_set")
+
+
+def ss_selector_get():
+    """(params, cfg_count, batch_max) of the library's model."""
+    import numpy as np
+    p = np.zeros(MLP_PARAMS, dtype=np.float32)
+    cc = (ctypes.c_int * 15)()
+    bm = (ctypes.c_int * (3 * NUM_BINS * 5))()
+    _check(lib().ss_selector_get(p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), cc, bm), "ss_selector_get")
+    return p, list(cc), list(bm)
+
+
+def ss_selector_clear() -> None:
+    _check(lib().ss_selector_clear(), "ss_selector_clear")
+
+
+def ss_selector_save(path: str) -> None:
+    _check(lib().ss_selector_save(os.fsencode(path)), "ss_selector_save")
+
+
+def ss_selector_load(path: str) -> None:
+    _check(lib().ss_selector_load(os.fsencode(path)), "ss_selector_load")
+
+
+def ss_selector_train(X, T, M, steps, lr, init=None, stream=0):
+    """Trains the library's model on the GPU; returns the loss before each step."""
+    import numpy as np
+    kx, px = _float_ptr(X)
+    kt, pt = _float_ptr(T)
+    km, pm = _float_ptr(M)
+    ki, pi = _float_ptr(init) if init is not None else (None, None)
+    loss = np.zeros(max(int(steps), 1), dtype=np.float32)
+    _check(lib().ss_selector_train(px, pt, pm, int(kx.shape[0]), pi, int(steps), float(lr),
+                                   loss.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), stream or None),
+           "ss_selector_train")
+    return loss[:steps]
+
+
+def ss_selector_queries(op, count_by_bin):
+    """Feature rows [nrows x SS_MLP_IN] the selector evaluates for a call."""
+    import numpy as np
+    x = np.zeros((SELECTOR_MAX_ROWS, MLP_IN), dtype=np.float32)
+    nr = ctypes.c_int(0)
+    _check(lib().ss_selector_queries(op, len(count_by_bin), _int_array(count_by_bin),
+                                     x.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(nr)),
+           "ss_selector_queries")
+    return x[:nr.value].copy()
+
+
+def ss_selector_decide(op, count_by_bin, policy, y):
+    """(modes, cfgs, predicted ms) from network outputs y for those rows."""
+    nb = len(count_by_bin)
+    ky, py = _float_ptr(y)
+    m = (ctypes.c_int * max(nb, 1))()
+    c = (ctypes.c_int * max(nb, 1))()
+    ms = ctypes.c_double(0.0)
+    _check(lib().ss_selector_decide(op, nb, _int_array(count_by_bin), policy, py, m, c, ctypes.byref(ms)),
+           "ss_selector_decide")
+    return list(m[:nb]), list(c[:nb]), float(ms.value)
+
+
+def ss_selector_predict(op, count_by_bin, policy, stream=0):
+    """(modes, cfgs, predicted ms) by the CUDA forward of the library's model."""
+    nb = len(count_by_bin)
+    m = (ctypes.c_int * max(nb, 1))()
+    c = (ctypes.c_int * max(nb, 1))()
+    ms = ctypes.c_double(0.0)
+    _check(lib().ss_selector_predict(op, nb, _int_array(count_by_bin), policy, m, c, ctypes.byref(ms),
+                                     stream or None), "ss_selector_predict")
+    return list(m[:nb]), list(c[:nb]), float(ms.value)
+
+
+def ss_selector_install(op, count_by_bin, policy, stream=0) -> None:
+    _check(lib().ss_selector_install(op, len(count_by_bin), _int_array(count_by_bin), policy, stream or None),
+           "ss_selector_install")

@@ -9,7 +9,7 @@ accuracy gate are candidates (FP64, the *_REFINED modes and DF).
 
 A bucket's instances have order n uniform over the size bin
 (2^(k-1), 2^k] and are solved in one call; the time is the median of a few
-CUDA-event-timed calls after a warm-up.  The database is JSON:
+CUDA-event-timed calls after a warm-up (the library's ss_autotune).  The database is JSON:
 
     {"gpu": ..., "created": ..., "entries": [
         {"op": "trsyl", "bin": 7, "n_lo": 65, "n_hi": 128, "batch": 2048,
@@ -63,27 +63,9 @@ def bucket_sizes(k: int, batch: int, seed: int) -> np.ndarray:
     return rng.integers(lo, hi + 1, size=batch).astype(np.int32)
 
 
-def time_call(db, mode: int, cfg: int, reps: int = 3, budget_ms: float = 400.0) -> float:
-    """Median milliseconds of one batched call (after one warm-up call)."""
-    import torch
-    db.solve(mode=mode, cfg=cfg)
-    torch.cuda.synchronize()
-    ts = []
-    for _ in range(reps):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        db.solve(mode=mode, cfg=cfg)
-        e1.record()
-        torch.cuda.synchronize()
-        ts.append(e0.elapsed_time(e1))
-        if sum(ts) > budget_ms:
-            break
-    return float(np.median(ts))
-
-
 def sweep(buckets, modes=AUTO_MODES, seed: int = 99, reps: int = 3, log=print):
-    """Time every (mode, cfg) on every bucket; returns the list of entries."""
+    """Time every (mode, cfg) on every bucket (the library's ss_autotune, one
+    call per bucket and mode); returns the list of entries."""
     import torch
     from .device import DeviceBatch
     entries = []
@@ -94,9 +76,8 @@ def sweep(buckets, modes=AUTO_MODES, seed: int = 99, reps: int = 3, log=print):
         lo, hi = bin_range(k)
         for mname in modes:
             m = ss.MODES[mname]
-            for cfg in range(ss.ss_config_count(ss.OPS[op], m)):
-                ms = time_call(db, m, cfg, reps=reps)
-                bad = int((db.info_host() != 0).sum())
+            times, bads, _ = db.autotune(m, reps=reps)
+            for cfg, (ms, bad) in enumerate(zip(times, bads)):
                 entries.append(dict(op=op, bin=k, n_lo=lo, n_hi=hi, batch=batch, mode=mname,
                                     cfg=cfg, ms=ms, info_nonzero=bad))
                 log(f"{op:6s} bin={k} n=({lo},{hi}] batch={batch:5d} {mname:13s} cfg={cfg} "

@@ -116,8 +116,11 @@ def test_df_mode_host_side(lib):
         cnt = ss.ss_config_count(op, ss.MODE_DF)
         assert cnt == want
         assert all(ss.ss_config_describe(op, ss.MODE_DF, c)[2] == 4 for c in range(cnt))
-        # No scratch beyond FP64's.
-        assert ss.ss_workspace_size(op, 1000, 128, ss.MODE_DF) == ss.ss_workspace_size(op, 1000, 128, ss.MODE_FP64)
+        # FP64's workspace plus 24 bytes per instance (the scale pre-pass's
+        # exponents and diagonal maximum, the flag that hands an instance to
+        # the rescaled pass), 256-byte aligned; no scratch.
+        extra = ss.ss_workspace_size(op, 1000, 128, ss.MODE_DF) - ss.ss_workspace_size(op, 1000, 128, ss.MODE_FP64)
+        assert extra == (1000 * 24 + 255) // 256 * 256
     # Argument checks of the DF forms run before any launch.
     assert ss.potrf_upper(1, 4, 1, 1, 1, 1, 1, 1, mode=ss.MODE_DF, cfg=2, check=False) == -10
     assert ss.posv_upper(1, 4, 4, *([1] * 11), mode=ss.MODE_DF, cfg=2, check=False) == -16

@@ -114,7 +114,7 @@ def test_padded_ld_rect_and_posv(mode):
     X = padded([np.zeros((int(a), int(b))) for a, b in zip(m, n)], pads(), dev)
     dm, dn = torch.from_numpy(m).to(dev), torch.from_numpy(n).to(dev)
     info = torch.zeros(len(m), dtype=torch.int32, device=dev)
-    w = work(ss.OP_TRSYL, len(m), int(max(m.max(), n.max())))
+    w = work(ss.OP_TRSYL, len(m), int(max(m.max(), n.max())), mode)
     ss.trsyl_rect(len(m), int(m.max()), int(n.max()), dm.data_ptr(), dn.data_ptr(), L[1].data_ptr(), L[2].data_ptr(),
                   U[1].data_ptr(), U[2].data_ptr(), C[1].data_ptr(), C[2].data_ptr(), X[1].data_ptr(), X[2].data_ptr(),
                   info.data_ptr(), mode=mode, d_work=w.data_ptr(), work_bytes=int(w.numel()))
@@ -129,7 +129,7 @@ def test_padded_ld_rect_and_posv(mode):
     A = padded(aa, pads(), dev); R = padded([np.zeros((int(a), int(a))) for a in nn], pads(), dev)
     B = padded(bb, pads(), dev); Xp = padded([np.zeros((int(a), int(b))) for a, b in zip(nn, k)], pads(), dev)
     dnn, dk = torch.from_numpy(nn).to(dev), torch.from_numpy(k).to(dev)
-    w = work(ss.OP_POTRF, len(nn), int(nn.max()))
+    w = work(ss.OP_POTRF, len(nn), int(nn.max()), mode)
     ss.posv_upper(len(nn), int(nn.max()), int(k.max()), dnn.data_ptr(), dk.data_ptr(), A[1].data_ptr(), A[2].data_ptr(),
                   R[1].data_ptr(), R[2].data_ptr(), B[1].data_ptr(), B[2].data_ptr(), Xp[1].data_ptr(), Xp[2].data_ptr(),
                   info.data_ptr(), mode=mode, d_work=w.data_ptr(), work_bytes=int(w.numel()))
