@@ -44,7 +44,7 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07   # SMs x DFMA/clk/SM x flop/FMA x GHz = 1
 # double-float multiply-add (TwoProduct with cross terms, TwoSum, low-part
 # update), counted as the 2 flops of the FP64 operation it replaces.
 DF_OPS_PER_TERM = 13
-DF_PEAK_GFLOPS = 152 * 128 * 2.07 / DF_OPS_PER_TERM * 2   # = 6189.6
+DF_PEAK_GFLOPS = 152 * 128 * 2.07 / DF_OPS_PER_TERM * 2   # = 6196.0
 GATE = 1e-11
 
 
@@ -487,6 +487,104 @@ def run_extra(args):
     return 0
 
 
+SIDE_WORKLOADS = ("potrf_1024x64", "trlyap_2048x128", "potrf_8192xLU8-256")
+
+
+def measure_side_workloads(args, dev, stream):
+    """The other measured configurations, each as the headline: mixed +
+    learned (SS_MODE_AUTO with the selector's one choice for the call) against
+    plain FP64 with the default configuration, on inputs resident in HBM;
+    the learned path's accuracy against the oracle on a sample of 32
+    instances and the roofline fraction of its dominant kernel."""
+    import torch
+    import oracle
+    from paper_1906_08613_gb300 import inputs, selector as sel, smallsolve as ss
+    from paper_1906_08613_gb300.device import DeviceBatch
+    sh = stream.cuda_stream
+    model = sel.Selector.load(os.path.join(ROOT, "paper_1906_08613_gb300", "data", "selector_gb300"), device=str(dev))
+    inv = {v: k for k, v in ss.MODES.items()}
+    out = {}
+    for name in SIDE_WORKLOADS:
+        op = inputs.WORKLOADS[name]["op"]
+        o = ss.OPS[op]
+        pk = inputs.make_workload(name, seed=args.seed)
+        db = DeviceBatch(pk.n, pk.off, pk.ops, op, device=dev)
+        table = model.install(op, sel.counts_by_bin(pk.n))
+        torch.cuda.synchronize(dev)
+        res = {}
+        x_learned = None
+        for label, mode in (("mixed_learned", ss.MODE_AUTO), ("fp64_default", ss.MODE_FP64)):
+            db.ensure_work(mode)
+            reps = max(3, min(args.steps, 20))
+            with torch.cuda.stream(stream):
+                for _ in range(3):
+                    db.solve(mode=mode, stream=sh)
+                ss.ss_profile_enable(True)
+                ss.ss_profile_read()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    db.solve(mode=mode, stream=sh)
+                e1.record(stream)
+            stream.synchronize()
+            kms, kc = ss.ss_profile_read()
+            ss.ss_profile_enable(False)
+            ms = e0.elapsed_time(e1) / reps
+            res[label] = {"ms_per_step": ms, "value": pk.batch / (ms * 1e-3), "kernel_ms": kms / max(kc, 1)}
+            if label == "mixed_learned":
+                x_learned = db.x_host()
+                res[label]["info_nonzero"] = int((db.info_host() != 0).sum())
+        ss.ss_set_auto_table(o, [], [])
+        idx = sample_indices(pk, 32, seed=11)
+        ops = {k: v for k, v in pk.ops.items() if k != "X0"}
+        ref, _ = oracle.solve_packed_parallel(op, pk.n, pk.off, ops, threads=os.cpu_count() or 1, indices=idx)
+        errs = []
+        for b in idx:
+            nb, ob = int(pk.n[b]), int(pk.off[b])
+            g = x_learned[ob:ob + nb * nb].reshape(nb, nb, order="F")
+            r = ref[ob:ob + nb * nb].reshape(nb, nb, order="F")
+            g, r = (np.triu(g), np.triu(r)) if op == "potrf" else ((np.tril(g), np.tril(r)) if op == "trlyap" else (g, r))
+            errs.append(float(np.linalg.norm(g - r) / np.linalg.norm(r)))
+        kbin = ss.size_bin(int(pk.n.max()))
+        dm = inv.get(table[0][kbin], "fp64")
+        peak = DF_PEAK_GFLOPS if dm == "df" else FP64_PEAK_GFLOPS
+        achieved = flops_algorithmic(op, pk.n) / (res["mixed_learned"]["kernel_ms"] * 1e-3) / 1e9
+        out[name] = {
+            "op": op, "batch": pk.batch,
+            "selector_choice": [dm, int(table[1][kbin])],
+            "mixed_learned": res["mixed_learned"], "fp64_default": res["fp64_default"],
+            "speedup_vs_fp64_default": res["mixed_learned"]["value"] / res["fp64_default"]["value"],
+            "accuracy": {"max_rel_fro_err_vs_oracle": max(errs), "gate": GATE, "instances_checked": len(idx),
+                         "pass": bool(max(errs) <= GATE)},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
+                         "frac": achieved / peak, "fp64_equivalent_frac": achieved / FP64_PEAK_GFLOPS,
+                         "peak_source": "derived (see the headline's roofline)"}}
+        del db
+        torch.cuda.empty_cache()
+    return out
+
+
+def measure_selector_stream():
+    """The held-out stream of 16384 mixed instances (operation uniform over the
+    three, n log-uniform in [4, 512]): each operation's share solved in one
+    call under the selector, the exhaustive autotune tables, the best single
+    (mode, cfg) chosen on the training buckets, and the FP64 default."""
+    from paper_1906_08613_gb300 import selector as sel, train_selector as tsel, tune
+    model = sel.Selector.load(os.path.join(ROOT, "paper_1906_08613_gb300", "data", "selector_gb300"))
+    entries = tune.load(os.path.join(ROOT, "paper_1906_08613_gb300", "data", "tune_gb300.json"))["entries"]
+    res = tsel.evaluate_stream(model, entries, total=16384, seed=2026, log=lambda _: None)
+    keep = ("instances", "fp64_default_ms", "exhaustive_ms", "exhaustive_call_ms", "fixed_policy_ms", "fixed_policy",
+            "selector_ms", "selector_table", "selector_bad", "regret", "gain_over_fp64_default",
+            "gain_over_fixed_policy")
+    out = {op: {k: v for k, v in r.items() if k in keep} for op, r in res.items() if op != "total"}
+    out["total"] = res["total"]
+    for r in out.values():
+        if "selector_table" in r:
+            r["selector_table"] = [list(map(int, r["selector_table"][0]))]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -507,6 +605,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-sample", type=int, default=256)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-side", action="store_true",
+                    help="skip the other configurations and the selector stream")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -725,6 +825,9 @@ def main():
                                           f"repeated for {el:.1f} s ({done} solves)"}
         line["accuracy"] = {"max_rel_fro_err_vs_oracle": float(max(errs)), "gate": GATE,
                             "instances_checked": len(idx), "pass": bool(max(errs) <= GATE)}
+    if not args.no_side:
+        line["workloads"] = measure_side_workloads(args, dev, stream)
+        line["selector_stream"] = measure_selector_stream()
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

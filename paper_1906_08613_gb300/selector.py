@@ -284,6 +284,24 @@ def trained_batch_max(X):
     return out
 
 
+def best_fixed_policy(entries, op: str, buckets):
+    """The single (mode, cfg) with the smallest geometric-mean measured time
+    over the given (op, bin, batch) buckets of `op`, among the pairs measured
+    in all of them: the method without a model, tuned on the same data."""
+    T = {(e["op"], e["bin"], e["batch"], e["mode"], e["cfg"]): e["ms"]
+         for e in entries if not e.get("info_nonzero", 0)}
+    bks = [b for b in buckets if b[0] == op]
+    best = None
+    for mc in sorted({k[3:] for k in T if k[0] == op}):
+        ts = [T.get(tuple(b) + mc) for b in bks]
+        if not ts or any(t is None for t in ts):
+            continue
+        g = float(np.exp(np.mean(np.log(ts))))
+        if best is None or g < best[1]:
+            best = (mc, g)
+    return best[0] if best else None
+
+
 def counts_by_bin(n, nbins: int = ss.NUM_BINS):
     """Number of instances of each order in each size bin."""
     c = [0] * nbins
