@@ -45,6 +45,9 @@ FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07   # SMs x DFMA/clk/SM x flop/FMA x GHz = 1
 # update), counted as the 2 flops of the FP64 operation it replaces.
 DF_OPS_PER_TERM = 13
 DF_PEAK_GFLOPS = 152 * 128 * 2.07 / DF_OPS_PER_TERM * 2   # = 6196.0
+# The same ceiling from the measured FP32 rate (an FFMA probe: 72 TFLOP/s =
+# 36e12 FFMA/s) instead of the nominal lane rate.
+DF_PEAK_MEASURED_FFMA_GFLOPS = 72000.0 / 2 / DF_OPS_PER_TERM * 2   # = 5538.5
 GATE = 1e-11
 
 
@@ -208,7 +211,7 @@ def read_traffic(key):
         return None
     from paper_1906_08613_gb300 import build as b
     ent = d.get(key)
-    if not ent or ent.get("sources_sha") != b.sources_sha():
+    if not ent or ent.get("sources_sha") != b.sources_sha(ent.get("sources")):
         return None
     return ent.get("dram_bytes_per_launch")
 
@@ -774,6 +777,7 @@ def main():
             "dominant": dominant_key,
             "peak_source": peak_source,
             "fp64_equivalent_frac": achieved / FP64_PEAK_GFLOPS,
+            "frac_of_measured_ffma": (achieved / DF_PEAK_MEASURED_FFMA_GFLOPS) if df_dominant else None,
             "kernel_ms": kern_avg_ms, "algorithmic_bytes": Balg,
             "hbm_frac": Balg / (kern_avg_ms * 1e-3) / 6801.3e9}
     used = sorted({inv_mode(m) for m in table[0] if m >= 0}) if table else [args.mode]

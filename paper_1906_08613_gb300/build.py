@@ -45,11 +45,19 @@ def _stale(target: str, sources: list[str]) -> bool:
     return any(os.path.getmtime(s) > t for s in sources)
 
 
-def sources_sha() -> str:
-    """Hash of every kernel source and header (ties profiles to a build)."""
+def sources_sha(files=None) -> str:
+    """Hash of kernel sources and headers (ties profiles to a build): every
+    one, or only the named files (basenames under csrc/ or include/), so that
+    a profile of one kernel stays valid while other translation units change."""
     import hashlib
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(CSRC, "*.cu")) + _deps()):
+    paths = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + _deps())
+    if files is not None:
+        want = set(files)
+        paths = [p for p in paths if os.path.basename(p) in want]
+        if len(paths) != len(want):
+            return "missing-source"
+    for p in paths:
         h.update(os.path.basename(p).encode())
         h.update(open(p, "rb").read())
     return h.hexdigest()[:16]
