@@ -421,6 +421,22 @@ int ss_selector_predict(int op, int nbins, const int *count_by_bin, int policy,
                         int *mode_by_bin, int *cfg_by_bin, double *pred_ms, void *stream);
 int ss_selector_install(int op, int nbins, const int *count_by_bin, int policy, void *stream);
 
+/*
+ * Tensor-core self-test (no counterpart in the paper): one 128 x n tile on
+ * the fifth-generation tensor cores through the operand layout, descriptors,
+ * tensor-memory accumulator and completion path that the refined modes'
+ * trailing updates use, so that the encodings can be checked against a host
+ * product.  D = op(A) B^T, or D = C + op(A) B^T with flags bit 0; op(A) = -A
+ * with flags bit 1 (the instruction's negate-A bit).  Device arrays, FP32,
+ * row-major: A 128 x k, B n x k, C and D 128 x n.  kind 0: the operands are
+ * rounded to TF32 (k a multiple of 8), kind 1: to BF16 (k a multiple of 16);
+ * 16 <= n <= 256 with n % 16 == 0, k <= 64.  One CTA on `stream`; *d_status
+ * = 0 when the tile completed, 1 if the bounded wait for it ran out (D is
+ * then unwritten).  Returns 0, -k for an invalid argument k, or SS_ERR_CUDA.
+ */
+int ss_umma_selftest(int kind, int n, int k, const float *d_a, const float *d_b, const float *d_c, float *d_d,
+                     int flags, int *d_status, void *stream);
+
 /* Library version. */
 int ss_version(void);
 

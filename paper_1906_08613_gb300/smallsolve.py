@@ -109,6 +109,8 @@ def lib():
             L.ss_mlp_adam.restype = i
             L.ss_version.argtypes = []
             L.ss_version.restype = i
+            L.ss_umma_selftest.argtypes = [i, i, i, vp, vp, vp, vp, i, vp, vp]
+            L.ss_umma_selftest.restype = i
             L.ss_launch_count.argtypes = []
             L.ss_launch_count.restype = ctypes.c_longlong
             L.ss_profile_enable.argtypes = [i]
@@ -233,6 +235,14 @@ def ss_mlp_grad(d_params, nrows, d_x, d_t, d_mask, mask_total, d_grad, d_loss, d
                 stream=0):
     return _check(lib().ss_mlp_grad(d_params, nrows, d_x, d_t, d_mask, float(mask_total), d_grad,
                                     d_loss, d_work, work_bytes, stream or None), "ss_mlp_grad")
+
+
+UMMA_TF32, UMMA_BF16 = 0, 1
+
+
+def ss_umma_selftest(kind, n, k, d_a, d_b, d_c, d_d, flags, d_status, stream=0, check=True):
+    rc = lib().ss_umma_selftest(kind, n, k, d_a, d_b, d_c or None, d_d, flags, d_status, stream or None)
+    return _check(rc, "ss_umma_selftest") if check else rc
 
 
 def ss_mlp_adam(d_params, d_grad, d_m, d_v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, stream=0):
