@@ -109,6 +109,11 @@
  *   SS_INFO_RANGE      (SS_MODE_DF, trsyl / trlyap / trsyl_rect, X == C or
  *                      X == S) the solution left the double-float range (see
  *                      Magnitude); X is undefined: solve again in SS_MODE_FP64.
+ *   SS_INFO_TIMEOUT    (refined modes, tensor-memory configurations) the
+ *                      bounded wait for the tensor cores ran out; X is
+ *                      undefined, and that CTA took no further instances
+ *                      (the others finish the batch).  Not expected in
+ *                      normal operation.
  *
  * Streams.  `stream` is a cudaStream_t (NULL: the legacy default stream).
  * Every call is asynchronous with respect to the host.  When a call uses
@@ -157,6 +162,7 @@ extern "C" {
 #define SS_INFO_NO_WORK   (-2)
 #define SS_INFO_ALIASED   (-3)
 #define SS_INFO_RANGE     (-4)
+#define SS_INFO_TIMEOUT   (-5)
 
 #define SS_ERR_IO          (-102)
 #define SS_ERR_NO_SELECTOR (-103)
@@ -261,7 +267,12 @@ int ss_workspace_size(int op, int batch, int max_n, int mode, size_t *bytes);
  * Kernel configurations.  ss_config_count returns how many explicit
  * configurations `op` has in `mode` (or a negative error);
  * ss_config_describe writes the block size, threads per CTA and algorithm
- * variant of configuration `cfg` (any pointer may be NULL).
+ * variant of configuration `cfg` (any pointer may be NULL).  In the TF32 and
+ * BF16 refined modes, variant bit 2 marks the tensor-memory configurations:
+ * the low-precision solve keeps its trailing matrix (Cholesky, n <= 256) or
+ * right-hand side (Sylvester / Lyapunov, n <= 128) in tensor memory and
+ * applies the trailing updates with tcgen05 MMAs; larger instances of the
+ * same call take the blocked / warp-block path.
  */
 int ss_config_count(int op, int mode);
 int ss_config_describe(int op, int mode, int cfg, int *block, int *threads, int *variant);

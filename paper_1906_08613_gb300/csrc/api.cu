@@ -21,6 +21,7 @@ cudaError_t launch_mixed(int op, const Operands &o, const Sched &s, const Launch
 int mixed_config_count(int op, int mode);
 const Config *mixed_config_get(int op, int mode, int cfg);
 long long mixed_scratch_per_n2(int op, int mode);
+int mixed_launches(int op, int mode, int cfg);
 
 namespace {
 
@@ -325,12 +326,15 @@ int run(int op, int batch, int max_n, const Operands &o, int mode, int cfg, void
     // scale pre-pass.
     int nlaunch = 1 + ngroups;
     bool any_df = false;
-    for (int g = 0; g < ngroups; ++g)
+    for (int g = 0; g < ngroups; ++g) {
         if (group_mode[g] == SS_MODE_DF) {
             if (s.dfs == nullptr) return SS_ERR_CUDA;
             any_df = true;
             nlaunch += op != SS_OP_POTRF ? 2 : 1;
+        } else if (group_mode[g] != SS_MODE_FP64) {
+            nlaunch += mixed_launches(op, group_mode[g], group_cfg[g]) - 1;
         }
+    }
     if (any_df && op != SS_OP_POTRF) {
         e = launch_df_scale(op, batch, o, s, st);
         if (e != cudaSuccess) return SS_ERR_CUDA;

@@ -17,10 +17,14 @@ namespace {
 // wavefront, 32 x 32 blocks, one warp per block of a block anti-diagonal).
 const Config kFp32Cfg[] = {{16, 64, 0},  {16, 128, 0}, {32, 128, 0}, {16, 128, 1},
                            {32, 128, 1}, {32, 128, 2}, {32, 64, 2},  {32, 256, 2}};
-const Config kTcCfg[] = {{16, 64, 0}, {32, 128, 0}, {16, 64, 1}, {32, 128, 1}};
+// variant bit 2: the right-hand side resident in tensor memory, trailing
+// updates by tcgen05 MMA (n > 128 falls back to the warp-block wavefront).
+const Config kTcCfg[] = {{16, 64, 0}, {32, 128, 0}, {16, 64, 1}, {32, 128, 1}, {32, 128, 4}};
 // Cholesky (blocked lazy factorization, then factor refinement).
 const Config kCholFp32Cfg[] = {{16, 64, 0}, {16, 128, 0}, {32, 128, 0}, {32, 128, 1}};
-const Config kCholTcCfg[] = {{16, 64, 0}, {32, 128, 0}, {32, 128, 1}};
+// variant bit 2: the trailing matrix resident in tensor memory, SYRK updates
+// by tcgen05 MMA (TF32 / BF16 only; n > 256 falls back to the blocked path).
+const Config kCholTcCfg[] = {{16, 64, 0}, {32, 128, 0}, {32, 128, 1}, {32, 128, 4}};
 
 // Low-precision arithmetic of a mode: 0 FP32, 1 TF32, 2 BF16; -1 not mixed.
 int mode_prec(int mode)
@@ -56,12 +60,20 @@ const Config *mixed_config_get(int op, int mode, int cfg)
 }
 
 // Scratch per instance in floats per n^2: the right-hand side / correction
-// and the reciprocal divisors; the warp-block variant also keeps FP32 copies
-// of L and U.
+// and the reciprocal divisors; the warp-block and tensor-memory variants
+// (Sylvester / Lyapunov) also keep FP32 copies of L and U.
 long long mixed_scratch_per_n2(int op, int mode)
 {
     if (mixed_config_count(op, mode) <= 0) return 0;
-    return (op != SS_OP_POTRF && mode_prec(mode) == 0) ? 4 : 2;
+    return op != SS_OP_POTRF ? 4 : 2;
+}
+
+// Kernels one launch group of (op, mode, cfg) launches: the tensor-memory
+// Cholesky factors in one pass and refines in a second.
+int mixed_launches(int op, int mode, int cfg)
+{
+    const Config *c = mixed_config_get(op, mode, cfg);
+    return (c && op == SS_OP_POTRF && (c->variant & 4)) ? 2 : 1;
 }
 
 cudaError_t launch_mixed(int op, const Operands &o, const Sched &s, const Launch &l, cudaStream_t st)

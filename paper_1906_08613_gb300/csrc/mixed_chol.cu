@@ -19,7 +19,16 @@
 // 4^s, X by 2^s; F is unchanged), each FP64 value shifted as it is converted;
 // X in global memory stays in the caller's units.
 // Scratch: two n x n float buffers (W1, W2, ld n).
+//
+// The tensor-memory variant (TF32 / BF16, n <= 256) replaces step 1 by a
+// right-looking factorization whose whole trailing matrix stays on chip as
+// the FP32 accumulator of the fifth-generation tensor cores: per block row
+// of 32, the warp that owns those TMEM lanes reads the panel out, the CTA
+// factors its diagonal block and solves the panel (FP32, FP64 pivots), and
+// one thread issues the SYRK update A' -= P^T P of the trailing matrix as
+// 128-row MMA tiles (umma.cuh).  Refinement is the same.
 #include "mixed.cuh"
+#include "umma.cuh"
 
 namespace ss {
 namespace mx {
@@ -166,6 +175,177 @@ __device__ int chol_low(int n, const double *A, long lda, float *W, float *sm, i
     }
     __syncthreads();
     return 0;
+}
+
+// ---- Tensor-memory (tcgen05) variant of step 1 ----------------------------
+constexpr int TCB = 32, TCT = 128, TCLD = TCB + 1, TCMAXN = 256;
+
+template <int KIND>
+constexpr size_t tc_q_bytes() { return (size_t)TCMAXN * TCB * tc::KindTraits<KIND>::ES; }
+// Float region: the panel (TCLD x TCMAXN; the refinement's tiles reuse it),
+// 64 pivot scalars, 32 pivot reciprocals.
+constexpr int TC_FLOATS = TCLD * TCMAXN + 64 + TCB;
+static_assert(chol_smem_bytes<32>() <= (size_t)TCLD * TCMAXN * sizeof(float), "refinement tiles fit the panel");
+template <int KIND>
+constexpr size_t tc_chol_smem_bytes() { return 1024 + tc_q_bytes<KIND>() + (size_t)TC_FLOATS * sizeof(float) + 16; }
+
+struct TcChol {
+    unsigned char *q;    // SYRK operand, K-major, TCMAXN rows x 32
+    float *sm;           // panel P (column-major, ld TCLD) / refinement tiles
+    float *s_scal, *s_rinv;
+    uint64_t *mbar;      // MMA completion
+    uint32_t *slot;      // TMEM base address
+};
+
+template <int KIND>
+__device__ TcChol tc_chol_carve(unsigned char *raw)
+{
+    TcChol c;
+    const uint32_t mis = tc::smem_u32(raw) & 1023u;
+    c.q = raw + ((1024u - mis) & 1023u);
+    c.sm = reinterpret_cast<float *>(c.q + tc_q_bytes<KIND>());
+    c.s_scal = c.sm + TCLD * TCMAXN;
+    c.s_rinv = c.s_scal + 64;
+    c.mbar = reinterpret_cast<uint64_t *>(c.sm + TC_FLOATS);
+    c.slot = reinterpret_cast<uint32_t *>(c.mbar + 1);
+    return c;
+}
+
+// Low-precision factor of A (n <= TCMAXN) into W (upper, ld n) with the
+// trailing matrix in TMEM as -A' (tile 0: rows 0..127 x columns 0..255;
+// tile 1: rows 128..255 x columns 128..255 at TMEM columns 256..383).
+// Returns 0, the failing leading minor, or -1 if a bounded wait for the
+// tensor cores ran out (the CTA must then stop).  `phase` is the mbarrier
+// parity, carried across calls.
+template <int KIND>
+__device__ int chol_low_tc(int n, const double *A, long lda, float *W, const TcChol &c, uint32_t &phase, int sha)
+{
+    constexpr int KS = TCB / tc::KindTraits<KIND>::KSTEP;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nr = (n + 15) & ~15;
+    const bool two = n > 128;
+    const uint32_t ncols = two ? 512u : 128u;
+    float *P = c.sm;
+    if (warp == 0) tc::tmem_alloc(c.slot, ncols);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t base = *c.slot;
+    {
+        const int i = 32 * warp + lane;
+        for (int cc = 0; cc < nr; cc += 16) {
+            float v[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int j = cc + q;
+                v[q] = (i <= j && j < n) ? -d2f_trunc_s(A[i + (long)j * lda], sha) : 0.0f;
+            }
+            tc::st16(tc::taddr(base, warp, cc), v);
+        }
+        if (two) {
+            const int i1 = 128 + i;
+            for (int cc = 128; cc < nr; cc += 16) {
+                float v[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int j = cc + q;
+                    v[q] = (i1 <= j && j < n) ? -d2f_trunc_s(A[i1 + (long)j * lda], sha) : 0.0f;
+                }
+                tc::st16(tc::taddr(base, warp, 256 + cc - 128), v);
+            }
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const int nb = (n + TCB - 1) / TCB;
+    const int rq = two ? 256 : 128;
+    int fail = 0;
+    for (int K = 0; K < nb; ++K) {
+        const int k0 = K * TCB, kb = min(TCB, n - k0), w = n - k0;
+        // Panel rows k0 .. k0 + 31 (columns k0 .. n-1) out of TMEM.
+        if (warp == ((k0 & 127) >> 5)) {
+            for (int cc = k0; cc < nr; cc += 16) {
+                float v[16];
+                tc::ld16(tc::taddr(base, warp, k0 >= 128 ? 256 + cc - 128 : cc), v);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int j = cc + q - k0;
+                    if (j < w) P[lane + j * TCLD] = -v[q];
+                }
+            }
+        }
+        tc::fence_before();
+        __syncthreads();
+        const int f = chol_diag_f<TCB, TCT>(P, kb, c.s_scal);
+        if (f) { fail = k0 + f; break; }
+        for (int i = tid; i < kb; i += TCT) c.s_rinv[i] = d2f_trunc(1.0 / f2d_exact(P[i + i * TCLD]));
+        __syncthreads();
+        // Panel solve X_KK^T Y = P[:, kb:], one column per thread (kb = 32 here).
+        for (int j = kb + tid; j < w; j += TCT) {
+            float y[TCB];
+#pragma unroll
+            for (int i = 0; i < TCB; ++i) y[i] = P[i + j * TCLD];
+#pragma unroll
+            for (int i = 0; i < TCB; ++i) {
+                float sacc = y[i];
+#pragma unroll
+                for (int k = 0; k < i; ++k) sacc = fmaf(-P[k + i * TCLD], y[k], sacc);
+                y[i] = sacc * c.s_rinv[i];
+            }
+#pragma unroll
+            for (int i = 0; i < TCB; ++i) P[i + j * TCLD] = y[i];
+        }
+        __syncthreads();
+        for (int e = tid; e < kb * w; e += TCT) {
+            const int r = e % kb, j = e / kb;
+            if (j >= r) W[(k0 + r) + (long)(k0 + j) * n] = P[r + j * TCLD];
+        }
+        const int c0 = k0 + kb;
+        if (c0 >= n) break;
+        // Operand rows r = trailing-matrix indices, K = the panel's 32 rows;
+        // rows outside [c0, n) are zero (rows below k0 already are).
+        const int r0 = K == 0 ? 0 : k0;
+        for (int e = tid; e < (rq - r0) * TCB; e += TCT) {
+            const int r = r0 + e / TCB, k = e % TCB;
+            tc::op_store<KIND>(c.q, r, k, TCB, (r >= c0 && r < n) ? P[k + (r - k0) * TCLD] : 0.0f);
+        }
+        tc::fence_smem_to_async();
+        tc::fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after();
+            if (c0 < 128) {
+                const uint32_t id = tc::idesc<KIND>(128, nr - c0, false);
+#pragma unroll
+                for (int sk = 0; sk < KS; ++sk)
+                    tc::mma<KIND>(base + c0, tc::op_desc<KIND>(c.q, 0, sk, TCB), tc::op_desc<KIND>(c.q, c0, sk, TCB),
+                                  id, true);
+            }
+            if (two) {
+                const int c1 = max(c0, 128);
+                const uint32_t id = tc::idesc<KIND>(128, nr - c1, false);
+#pragma unroll
+                for (int sk = 0; sk < KS; ++sk)
+                    tc::mma<KIND>(base + 256 + (c1 - 128), tc::op_desc<KIND>(c.q, 128, sk, TCB),
+                                  tc::op_desc<KIND>(c.q, c1, sk, TCB), id, true);
+            }
+            tc::commit(c.mbar);
+        }
+        const bool ok = tc::mbar_wait(c.mbar, phase);
+        if (__syncthreads_or(!ok)) {
+            tc::mbar_wait(c.mbar, phase, 1u << 26);
+            fail = -1;
+            break;
+        }
+        phase ^= 1u;
+        tc::fence_after();
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (warp == 0) tc::tmem_dealloc(base, ncols);
+    return fail;
 }
 
 // E = A - X^T X (X: FP64 upper factor), all blocks I <= J, written to W in
@@ -342,21 +522,22 @@ __device__ float chol_correct(int n, double *X, long ldx, const float *Wf, float
     return block_sum_f(ss, s_red);
 }
 
-template <int B, int T, int P, int RS>
-__device__ void chol_mixed_instance(int n, const double *A, long lda, double *X, long ldx, int *info,
-                                    float *W1, float *W2, bool raw, float *sm)
+template <int T>
+__device__ DfScale chol_scale(int n, const double *A, long lda, float *s_red)
 {
-    float *s_red = sm + 5 * FTile<B>::SZ;
     int ea, dummy;
     scan_exp3(ScanOp{A, lda, n, n, 2}, ScanOp{nullptr, 0, 0, 0, 0}, ScanOp{nullptr, 0, 0, 0, 0}, threadIdx.x >> 5, T / 32,
               threadIdx.x & 31, ea, dummy);
     cta_max2(ea, dummy, reinterpret_cast<int *>(s_red));
-    const DfScale sc = DfScale::cholesky(ea);
-    const int f = chol_low<B, T, P>(n, A, lda, W1, sm, sc.op);
-    if (f) {
-        if (threadIdx.x == 0) *info = f;
-        return;
-    }
+    return DfScale::cholesky(ea);
+}
+
+// X = the low-precision factor in W1, then (unless raw) the refinement.
+template <int B, int T, int RS>
+__device__ void chol_refine(int n, const double *A, long lda, double *X, long ldx, int *info, float *W1, float *W2,
+                            bool raw, float *sm, const DfScale &sc)
+{
+    float *s_red = sm + 5 * FTile<B>::SZ;
     float ss = 0.0f;
     for (int e = threadIdx.x; e < n * n; e += T) {
         const int r = e % n, c = e / n;
@@ -378,6 +559,19 @@ __device__ void chol_mixed_instance(int n, const double *A, long lda, double *X,
         prev = nd;
     }
     if (threadIdx.x == 0) *info = conv ? 0 : n + 1;
+}
+
+template <int B, int T, int P, int RS>
+__device__ void chol_mixed_instance(int n, const double *A, long lda, double *X, long ldx, int *info,
+                                    float *W1, float *W2, bool raw, float *sm)
+{
+    const DfScale sc = chol_scale<T>(n, A, lda, sm + 5 * FTile<B>::SZ);
+    const int f = chol_low<B, T, P>(n, A, lda, W1, sm, sc.op);
+    if (f) {
+        if (threadIdx.x == 0) *info = f;
+        return;
+    }
+    chol_refine<B, T, RS>(n, A, lda, X, ldx, info, W1, W2, raw, sm, sc);
 }
 
 template <int B, int T, int P, int RS>
@@ -405,6 +599,92 @@ __global__ void __launch_bounds__(T, 1024 / T) chol_mixed_kernel(Operands o, Sch
         chol_mixed_instance<B, T, P, RS>(n, o.A[b], o.lda[b], o.X[b], o.ldx[b], o.info + b, W1,
                                          W1 + (long)n * n, raw != 0, smf);
     }
+}
+
+// Tensor-memory variant, pass 1: the low-precision factor of every instance
+// into W1 (TF32 or BF16 SYRK updates on the tensor cores for n <= 256, the
+// blocked path above), info = 0 or the failing minor.  Few CTAs per SM fit
+// (TMEM, shared memory), so the refinement runs as pass 2.
+template <int P>
+__global__ void __launch_bounds__(TCT) chol_tc_factor_kernel(Operands o, Sched s, int group, int raw)
+{
+    constexpr int KIND = P == P_TF32 ? tc::K_TF32 : tc::K_BF16;
+    extern __shared__ unsigned char smraw[];
+    __shared__ int s_slot;
+    const TcChol c = tc_chol_carve<KIND>(smraw);
+    const int lo = s.meta[META_RANGE + 2 * group], hi = s.meta[META_RANGE + 2 * group + 1];
+    claim_init(&s_slot);
+    if (threadIdx.x == 0) tc::mbar_init(c.mbar, 1);
+    __syncthreads();
+    uint32_t phase = 0;
+    for (;;) {
+        const int w = lo + claim_slot(s.meta + META_HEAD + group, &s_slot);
+        if (w >= hi) break;
+        const int b = s.perm[w];
+        const int n = o.n[b];
+        if (n == 0) { if (threadIdx.x == 0) o.info[b] = 0; continue; }
+        if (!raw && o.X[b] == o.A[b]) { if (threadIdx.x == 0) o.info[b] = SS_INFO_ALIASED; continue; }
+        const long long off = s.scr[w];
+        if (off + 2ll * n * n > s.scratch_elems) {
+            if (threadIdx.x == 0) o.info[b] = SS_INFO_NO_WORK;
+            continue;
+        }
+        float *W1 = static_cast<float *>(s.scratch) + off;
+        const DfScale sc = chol_scale<TCT>(n, o.A[b], o.lda[b], c.sm);
+        const int f = n <= TCMAXN ? chol_low_tc<KIND>(n, o.A[b], o.lda[b], W1, c, phase, sc.op)
+                                  : chol_low<TCB, TCT, P>(n, o.A[b], o.lda[b], W1, c.sm, sc.op);
+        if (threadIdx.x == 0) o.info[b] = f < 0 ? SS_INFO_TIMEOUT : f;
+        if (f < 0) break;
+    }
+}
+
+// Pass 2: X from W1 and the refinement, for every instance pass 1 left at
+// info = 0 (its own queue: the group's second-pass head).
+template <int P, int RS>
+__global__ void __launch_bounds__(TCT, 1024 / TCT) chol_tc_refine_kernel(Operands o, Sched s, int group, int raw)
+{
+    extern __shared__ __align__(16) float smf[];
+    __shared__ int s_slot;
+    const int lo = s.meta[META_RANGE + 2 * group], hi = s.meta[META_RANGE + 2 * group + 1];
+    claim_init(&s_slot);
+    for (;;) {
+        const int w = lo + claim_slot(s.meta + META_SCL_HEAD + group, &s_slot);
+        if (w >= hi) break;
+        const int b = s.perm[w];
+        const int n = o.n[b];
+        if (n == 0 || o.info[b] != 0) continue;
+        float *W1 = static_cast<float *>(s.scratch) + s.scr[w];
+        const DfScale sc = chol_scale<TCT>(n, o.A[b], o.lda[b], smf + 5 * FTile<TCB>::SZ);
+        chol_refine<TCB, TCT, RS>(n, o.A[b], o.lda[b], o.X[b], o.ldx[b], o.info + b, W1, W1 + (long)n * n,
+                                  raw != 0, smf, sc);
+    }
+}
+
+template <int P, int RS>
+cudaError_t launch_chol_tc(const Operands &o, const Sched &s, const Launch &l, cudaStream_t st, int raw)
+{
+    constexpr int KIND = P == P_TF32 ? tc::K_TF32 : tc::K_BF16;
+    auto k1 = chol_tc_factor_kernel<P>;
+    auto k2 = chol_tc_refine_kernel<P, RS>;
+    const size_t smem1 = tc_chol_smem_bytes<KIND>(), smem2 = chol_smem_bytes<TCB>();
+    cudaError_t e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+    if (e != cudaSuccess) return e;
+    int per1 = 0, per2 = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per1, k1, TCT, smem1);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k2, TCT, smem2);
+    if (e != cudaSuccess) return e;
+    // TMEM: 128 columns per CTA for n <= 128 (512 per SM).
+    per1 = per1 > 4 ? 4 : (per1 < 1 ? 1 : per1);
+    per2 = per2 < 1 ? 1 : per2;
+    long g1 = (long)per1 * sm_count(), g2 = (long)per2 * sm_count();
+    if (g1 > l.batch) g1 = l.batch;
+    if (g2 > l.batch) g2 = l.batch;
+    k1<<<(int)(g1 < 1 ? 1 : g1), TCT, smem1, st>>>(o, s, l.group, raw);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k2<<<(int)(g2 < 1 ? 1 : g2), TCT, smem2, st>>>(o, s, l.group, raw);
+    return cudaGetLastError();
 }
 
 template <int B, int T, int P, int RS>
@@ -445,12 +725,14 @@ cudaError_t launch_mixed_potrf(int prec, int cfg, const Operands &o, const Sched
         case 0: return launch_chol<16, 64, P_TF32, R_DF>(o, s, l, st, raw);
         case 1: return launch_chol<32, 128, P_TF32, R_DF>(o, s, l, st, raw);
         case 2: return launch_chol<32, 128, P_TF32, R_FP64>(o, s, l, st, raw);
+        case 3: return launch_chol_tc<P_TF32, R_DF>(o, s, l, st, raw);
         }
     } else if (prec == P_BF16) {
         switch (cfg) {
         case 0: return launch_chol<16, 64, P_BF16, R_DF>(o, s, l, st, raw);
         case 1: return launch_chol<32, 128, P_BF16, R_DF>(o, s, l, st, raw);
         case 2: return launch_chol<32, 128, P_BF16, R_FP64>(o, s, l, st, raw);
+        case 3: return launch_chol_tc<P_BF16, R_DF>(o, s, l, st, raw);
         }
     }
     return cudaErrorInvalidValue;

@@ -25,6 +25,7 @@ cudaError_t launch_mixed_trlyap(int prec, int cfg, const Operands &o, const Sche
         case 1: return launch_mixed_syl<32, 128, true, P_TF32, R_DF>(o, s, l, st, raw);
         case 2: return launch_mixed_syl<16, 64, true, P_TF32, R_FP64>(o, s, l, st, raw);
         case 3: return launch_mixed_syl<32, 128, true, P_TF32, R_FP64>(o, s, l, st, raw);
+        case 4: return wb::launch_warp_tc<true, P_TF32>(o, s, l, st, raw);
         }
     } else if (prec == P_BF16) {
         switch (cfg) {
@@ -32,6 +33,7 @@ cudaError_t launch_mixed_trlyap(int prec, int cfg, const Operands &o, const Sche
         case 1: return launch_mixed_syl<32, 128, true, P_BF16, R_DF>(o, s, l, st, raw);
         case 2: return launch_mixed_syl<16, 64, true, P_BF16, R_FP64>(o, s, l, st, raw);
         case 3: return launch_mixed_syl<32, 128, true, P_BF16, R_FP64>(o, s, l, st, raw);
+        case 4: return wb::launch_warp_tc<true, P_BF16>(o, s, l, st, raw);
         }
     }
     return cudaErrorInvalidValue;

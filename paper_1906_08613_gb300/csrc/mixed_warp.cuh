@@ -17,9 +17,15 @@
 // L and U are converted to FP32 once per instance into scratch (for the
 // Lyapunov form U = L^T is stored explicitly), as are the FP64 reciprocals
 // 1/(l_ii + u_jj).  Scratch per instance: 4 n^2 floats (D, reciprocals, L, U).
+//
+// Tensor-memory configurations (TF32 / BF16, n <= 128) replace the
+// low-precision solve by a right-looking one whose right-hand side stays in
+// TMEM as the tensor cores' FP32 accumulator (tsolve below); the residual and
+// the correction steps are the same.
 #pragma once
 
 #include "mixed_solver.cuh"
+#include "umma.cuh"
 
 namespace ss {
 namespace mx {
@@ -305,9 +311,206 @@ __device__ void wresidual(int n, const double *L, long ldl, const double *U, lon
     __syncthreads();
 }
 
-template <int WPC, bool LYAP>
-__device__ void warp_instance(int n, const double *L, long ldl, const double *U, long ldu, const double *C,
-                              long ldc, double *X, long ldx, int *info, float *W, bool raw, float *smem)
+// ---- Tensor-memory low-precision solve (n <= 128) -------------------------
+//
+// TMEM holds -R' (rows = lanes, 128 columns), R' the right-hand side less
+// every trailing update applied so far.  Block column K (k0 = 32 K):
+//   * the diagonal block D_KK, then the column chain D_IK (I > K; warp I,
+//     the owner of those lanes): T = R'_IK - sum_{K <= K' < I} L_IK' D_K'K,
+//     solved as L_II D + D U_KK = T by the block wavefront; for Sylvester
+//     also the row chain D_KJ (J > K; warp K): T = R'_KJ - sum D_KK' U_K'J;
+//   * the trailing update of every block (I, J), I, J > K, by the tensor
+//     cores: R' -= L_p D_r + D_c U_r  (Sylvester) or L_p D_c^T + D_c L_p^T
+//     (Lyapunov), with L_p / D_c the block column K of L / D below the
+//     block and D_r / U_r the block row K right of it, as one MMA sequence
+//     [L_p | D_c] [D_r^T | U_r^T]^T of K = 64 into the TMEM columns right of
+//     the block (Lyapunov: one operand buffer, read with its two K halves
+//     swapped for B).
+// The operand buffers overlay the warps' tiles (idle while the MMAs run).
+constexpr int TC_MAXN = 128, TC_THREADS = 128;
+
+// The block (I, J) of the chain of block column K, by the warp owning lanes
+// 32 I .. 32 I + 31.
+template <bool LYAP>
+__device__ void tblock(int n, int I, int J, int K, const float *Lf, const float *Uf, const float *R, float *W,
+                       float *sm, uint32_t tbase)
+{
+    float *sA = sm, *sB = sm + TILE, *sT = sm + 2 * TILE, *sR = sm + 3 * TILE;
+    const int lane = threadIdx.x & 31;
+    const long ldn = n;
+    const int i0 = I * BW, j0 = J * BW;
+    const int mI = min(BW, n - i0), nJ = min(BW, n - j0);
+    const int r0 = lane_r0(), c0 = lane_c0();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        float v[16];
+        tc::ld16(tc::taddr(tbase, I, j0 + 16 * h), v);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) sT[lane + (16 * h + q) * LDN] = -v[q];
+    }
+    __syncwarp();
+    float acc[4][8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = sT[(r0 + i) + (c0 + j) * LDN];
+    if (I > J) {
+        for (int Kp = K; Kp < I; ++Kp) {          // L_IK' D_K'K
+            const int k0 = Kp * BW;
+            __syncwarp();
+            wstage_A<false>(sA, Lf + i0 + (long)k0 * ldn, ldn, mI, BW);
+            wstage_B<false>(sB, W + k0 + (long)j0 * ldn, ldn, BW, nJ);
+            __syncwarp();
+            wmicro_f(acc, sA, sB, BW);
+        }
+    } else if (J > I) {
+        for (int Kp = K; Kp < J; ++Kp) {          // D_KK' U_K'J
+            const int k0 = Kp * BW;
+            __syncwarp();
+            wstage_A<false>(sA, W + i0 + (long)k0 * ldn, ldn, mI, BW);
+            wstage_B<false>(sB, Uf + k0 + (long)j0 * ldn, ldn, BW, nJ);
+            __syncwarp();
+            wmicro_f(acc, sA, sB, BW);
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) sT[(r0 + i) + (c0 + j) * LDN] = acc[i][j];
+#pragma unroll 8
+    for (int y = 0; y < BW; ++y) {
+        const int x = lane;
+        sA[x + y * LDN] = (x < mI && y < mI && x > y) ? Lf[(i0 + x) + (long)(i0 + y) * ldn] : 0.0f;
+        sB[x + y * LDN] = (x < nJ && y < nJ && x < y) ? Uf[(j0 + x) + (long)(j0 + y) * ldn] : 0.0f;
+        sR[x + y * LDN] = (x < mI && y < nJ) ? R[(i0 + x) + (long)(j0 + y) * ldn] : 0.0f;
+    }
+    __syncwarp();
+    for (int d = 0; d <= mI + nJ - 2; ++d) {
+        const int j = lane, i = d - j;
+        if (j < nJ && i >= 0 && i < mI) {
+            float s0 = 0.0f, s1 = 0.0f;
+            int t = 0;
+            for (; t + 1 < d; t += 2) {
+                const bool l0 = t < i, l1 = t + 1 < i;
+                const float a0 = l0 ? sA[i + t * LDN] : sT[i + (t - i) * LDN];
+                const float b0 = l0 ? sT[t + j * LDN] : sB[(t - i) + j * LDN];
+                const float a1 = l1 ? sA[i + (t + 1) * LDN] : sT[i + (t + 1 - i) * LDN];
+                const float b1 = l1 ? sT[t + 1 + j * LDN] : sB[(t + 1 - i) + j * LDN];
+                s0 = fmaf(a0, b0, s0);
+                s1 = fmaf(a1, b1, s1);
+            }
+            if (t < d) {
+                const bool l0 = t < i;
+                const float a0 = l0 ? sA[i + t * LDN] : sT[i + (t - i) * LDN];
+                const float b0 = l0 ? sT[t + j * LDN] : sB[(t - i) + j * LDN];
+                s0 = fmaf(a0, b0, s0);
+            }
+            sT[i + j * LDN] = (sT[i + j * LDN] - (s0 + s1)) * sR[i + j * LDN];
+        }
+        __syncwarp();
+    }
+#pragma unroll 8
+    for (int y = 0; y < nJ; ++y) {
+        const int x = lane;
+        if (x < mI) W[(i0 + x) + (long)(j0 + y) * ldn] = sT[x + y * LDN];
+    }
+    __syncwarp();
+}
+
+struct TcSolve {
+    uint32_t base;       // TMEM columns (128)
+    uint64_t *mbar;
+    uint32_t phase;
+};
+
+// Low-precision solve of L D + D U = W in place (n <= 128) with the
+// right-hand side in TMEM.  `smem` is 1024-byte aligned, the warps' tiles.
+// Returns false if a bounded wait for the tensor cores ran out.
+template <bool LYAP, int KIND>
+__device__ bool tsolve(int n, const float *Lf, const float *Uf, const float *R, float *W, float *smem, TcSolve &t)
+{
+    constexpr int KT = 2 * BW, S = KT / tc::KindTraits<KIND>::KSTEP;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    float *sm = smem + warp * SLOTS * TILE;
+    unsigned char *za = reinterpret_cast<unsigned char *>(smem);
+    unsigned char *zb = za + (size_t)TC_MAXN * KT * tc::KindTraits<KIND>::ES;
+    const int nb = (n + BW - 1) / BW, nr = (n + 15) & ~15;
+    {
+        const int i = 32 * warp + lane;
+        for (int cc = 0; cc < nr; cc += 16) {
+            float v[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int j = cc + q;
+                v[q] = (i < n && j < n) ? -W[i + (long)j * n] : 0.0f;
+            }
+            tc::st16(tc::taddr(t.base, warp, cc), v);
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    for (int K = 0; K < nb; ++K) {
+        const int k0 = K * BW, c0 = k0 + BW;
+        if (warp == K) tblock<LYAP>(n, K, K, K, Lf, Uf, R, W, sm, t.base);
+        __syncthreads();
+        for (int s = 1; K + s < nb; ++s) {
+            if (warp == K + s) tblock<LYAP>(n, K + s, K, K, Lf, Uf, R, W, sm, t.base);
+            if (!LYAP && warp == K) tblock<LYAP>(n, K, K + s, K, Lf, Uf, R, W, sm, t.base);
+            __syncthreads();
+        }
+        if (c0 >= n) break;
+        // Operands: A row r = [L(r, k0..) | D(r, k0..)] for c0 <= r < n;
+        // Sylvester B row r = [D(k0.., r) | U(k0.., r)], Lyapunov B = A with
+        // its K halves swapped.
+        for (int e = tid; e < TC_MAXN * KT; e += TC_THREADS) {
+            const int r = e % TC_MAXN, k = e / TC_MAXN;
+            float v = 0.0f;
+            if (r >= c0 && r < n) v = k < BW ? Lf[r + (long)(k0 + k) * n] : W[r + (long)(k0 + k - BW) * n];
+            tc::op_store<KIND>(za, r, k, KT, v);
+        }
+        if (!LYAP) {
+            for (int e = tid; e < TC_MAXN * KT; e += TC_THREADS) {
+                const int k = e % KT, r = e / KT;
+                float v = 0.0f;
+                if (r >= c0 && r < n) v = k < BW ? W[(k0 + k) + (long)r * n] : Uf[(k0 + k - BW) + (long)r * n];
+                tc::op_store<KIND>(zb, r, k, KT, v);
+            }
+        }
+        tc::fence_smem_to_async();
+        tc::fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after();
+            const uint32_t id = tc::idesc<KIND>(128, nr - c0, false);
+#pragma unroll
+            for (int sk = 0; sk < S; ++sk) {
+                const uint64_t a = tc::op_desc<KIND>(za, 0, sk, KT);
+                const uint64_t b = LYAP ? tc::op_desc<KIND>(za, c0, (sk + S / 2) % S, KT)
+                                        : tc::op_desc<KIND>(zb, c0, sk, KT);
+                tc::mma<KIND>(t.base + c0, a, b, id, true);
+            }
+            tc::commit(t.mbar);
+        }
+        const bool ok = tc::mbar_wait(t.mbar, t.phase);
+        if (__syncthreads_or(!ok)) {
+            tc::mbar_wait(t.mbar, t.phase, 1u << 26);
+            return false;
+        }
+        t.phase ^= 1u;
+        tc::fence_after();
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    return true;
+}
+
+template <int WPC, bool LYAP, int TCK = -1>
+__device__ bool warp_instance(int n, const double *L, long ldl, const double *U, long ldu, const double *C,
+                              long ldc, double *X, long ldx, int *info, float *W, bool raw, float *smem,
+                              TcSolve *ts = nullptr)
 {
     constexpr int T = 32 * WPC;
     const long nn = (long)n * n;
@@ -325,7 +528,17 @@ __device__ void warp_instance(int n, const double *L, long ldl, const double *U,
         W[e] = d2f_trunc_s(c, sc.rhs);
     }
     __syncthreads();
-    wsolve<WPC, LYAP>(n, Lf, Uf, R, W, smem);
+    auto solve = [&]() -> bool {
+        if constexpr (TCK >= 0) {
+            if (n <= TC_MAXN) return tsolve<LYAP, TCK>(n, Lf, Uf, R, W, smem, *ts);
+        }
+        wsolve<WPC, LYAP>(n, Lf, Uf, R, W, smem);
+        return true;
+    };
+    if (!solve()) {
+        if (threadIdx.x == 0) *info = SS_INFO_TIMEOUT;
+        return false;
+    }
     const float nx = sqrtf(update_x<T, LYAP>(n, X, ldx, W, n, true, s_red, sc.x));
     int conv = nx == 0.0f || raw;
     float prev = nx;
@@ -338,13 +551,17 @@ __device__ void warp_instance(int n, const double *L, long ldl, const double *U,
             }
             __syncthreads();
         }
-        wsolve<WPC, LYAP>(n, Lf, Uf, R, W, smem);
+        if (!solve()) {
+            if (threadIdx.x == 0) *info = SS_INFO_TIMEOUT;
+            return false;
+        }
         const float nd = sqrtf(update_x<T, LYAP>(n, X, ldx, W, n, false, s_red, sc.x));
         const float pred = prev > 0.0f ? nd * (nd / prev) : nd;
         conv = (nd <= (float)SS_REFINE_TOL * nx) || (pred <= (float)SS_REFINE_TOL * nx);
         prev = nd;
     }
     if (threadIdx.x == 0) *info = bad ? 1 : (conv ? 0 : n + 1);
+    return true;
 }
 
 template <int WPC, bool LYAP>
@@ -372,6 +589,66 @@ __global__ void __launch_bounds__(32 * WPC) warp_syl_kernel(Operands o, Sched s,
         warp_instance<WPC, LYAP>(n, o.A[b], o.lda[b], LYAP ? nullptr : o.U[b], LYAP ? 0 : o.ldu[b], o.C[b],
                                  o.ldc[b], o.X[b], o.ldx[b], o.info + b, W, raw != 0, smf);
     }
+}
+
+// Tensor-memory configurations: four warps, TMEM (128 columns) held for the
+// whole launch; instances with n > 128 take the warp-block wavefront.
+template <bool LYAP, int P>
+__global__ void __launch_bounds__(TC_THREADS) warp_tc_kernel(Operands o, Sched s, int group, int raw)
+{
+    constexpr int KIND = P == P_TF32 ? tc::K_TF32 : tc::K_BF16;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ int s_slot;
+    __shared__ uint64_t s_mbar;
+    __shared__ uint32_t s_tmem;
+    float *smf = reinterpret_cast<float *>(smraw + ((1024u - (tc::smem_u32(smraw) & 1023u)) & 1023u));
+    const int lo = s.meta[META_RANGE + 2 * group], hi = s.meta[META_RANGE + 2 * group + 1];
+    claim_init(&s_slot);
+    if ((threadIdx.x >> 5) == 0) tc::tmem_alloc(&s_tmem, 128);
+    if (threadIdx.x == 0) tc::mbar_init(&s_mbar, 1);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    TcSolve ts{s_tmem, &s_mbar, 0u};
+    for (;;) {
+        const int w = lo + claim_slot(s.meta + META_HEAD + group, &s_slot);
+        if (w >= hi) break;
+        const int b = s.perm[w];
+        const int n = o.n[b];
+        if (n == 0) { if (threadIdx.x == 0) o.info[b] = 0; continue; }
+        if (!raw && o.X[b] == o.C[b]) { if (threadIdx.x == 0) o.info[b] = SS_INFO_ALIASED; continue; }
+        const long long off = s.scr[w];
+        if (off + 4ll * n * n > s.scratch_elems) {
+            if (threadIdx.x == 0) o.info[b] = SS_INFO_NO_WORK;
+            continue;
+        }
+        float *W = static_cast<float *>(s.scratch) + off;
+        if (!warp_instance<4, LYAP, KIND>(n, o.A[b], o.lda[b], LYAP ? nullptr : o.U[b], LYAP ? 0 : o.ldu[b],
+                                          o.C[b], o.ldc[b], o.X[b], o.ldx[b], o.info + b, W, raw != 0, smf, &ts))
+            break;
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(s_tmem, 128);
+}
+
+template <bool LYAP, int P>
+cudaError_t launch_warp_tc(const Operands &o, const Sched &s, const Launch &l, cudaStream_t st, int raw)
+{
+    auto kern = warp_tc_kernel<LYAP, P>;
+    const size_t smem = smem_bytes(4) + 1024;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem);
+    if (e != cudaSuccess) return e;
+    per_sm = per_sm > 4 ? 4 : (per_sm < 1 ? 1 : per_sm);   // 4 x 128 TMEM columns per SM
+    long grid = (long)per_sm * sm_count();
+    if (grid > l.batch) grid = l.batch;
+    if (grid < 1) grid = 1;
+    kern<<<(int)grid, 128, smem, st>>>(o, s, l.group, raw);
+    return cudaGetLastError();
 }
 
 template <int WPC, bool LYAP>

@@ -33,7 +33,9 @@ struct Operands {
 //                             its range (an instance has info SS_INFO_RANGE)
 //   meta[META_SCL + g]        nonzero if an instance of double-float group g
 //                             needs rescaling (DfInst::pend)
-//   meta[META_SCL_HEAD + g]   work-queue head of that scaled pass
+//   meta[META_SCL_HEAD + g]   work-queue head of that scaled pass (for a
+//                             tensor-memory Cholesky group: of its
+//                             refinement pass)
 //   perm[w]                   instance index at position w (sizes descending)
 //   scr[w]                    element offset of position w's scratch area
 constexpr int META_COUNT = 0;

@@ -292,8 +292,10 @@ WORKLOADS = {
     "trlyap_2048x128": dict(op="trlyap", sizes=lambda s: sizes_fixed(2048, 128)),
     # mixed-size Cholesky, 8192 instances, n log-uniform in [8, 256]
     "potrf_8192xLU8-256": dict(op="potrf", sizes=lambda s: sizes_log_uniform(8192, 8, 256, s)),
-    # quarter-size Sylvester case for detailed profiles (operands still > L2)
+    # quarter-size cases for detailed profiles (operands still > L2)
     "trsyl_1024xU4-128": dict(op="trsyl", sizes=lambda s: sizes_uniform(1024, 4, 128, s)),
+    "trlyap_512x128": dict(op="trlyap", sizes=lambda s: sizes_fixed(512, 128)),
+    "potrf_2048xLU8-256": dict(op="potrf", sizes=lambda s: sizes_log_uniform(2048, 8, 256, s)),
 }
 
 

@@ -50,6 +50,7 @@ SELECTOR_MAX_ROWS = 13 * 5
 INFO_BAD_SIZE = -1
 INFO_ALIASED = -3
 INFO_RANGE = -4
+INFO_TIMEOUT = -5
 INFO_NO_WORK = -2
 MAX_N = 4096
 MLP_IN, MLP_HIDDEN, MLP_OUT = 10, 64, 8
