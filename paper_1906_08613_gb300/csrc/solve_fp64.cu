@@ -570,7 +570,7 @@ cudaError_t launch_syl_fp64(const Operands &o, const Sched &s, const Launch &l, 
 {
     const Config *c = config_get(lyap ? SS_OP_TRLYAP : SS_OP_TRSYL, SS_MODE_FP64, l.cfg);
     if (c == nullptr) return cudaErrorInvalidValue;
-    if (c->variant == 2) return launch_syl_ws(c->block, (c->threads - 32) / 32, lyap, false, o, s, l, st);
+    if (c->variant == 2) return launch_syl_ws(c->block, (c->threads - 32) / 32, lyap, false, o, s, l, st, false);
 #define CASE(B, T, V)                                                                                    \
     if (c->block == B && c->threads == T && c->variant == V)                                             \
         return lyap ? launch_persistent(syl_fp64_kernel<B, T, true, V>, T, smem_bytes<B>(), l.batch, st, o, s, l.group) \

@@ -527,7 +527,11 @@ constexpr size_t ws_smem_bytes() { return (size_t)WsTile<B, DF>::N * WsTile<B, D
 // scale pre-pass (di).  Without SC the shifts are the constant zero of data
 // in DfScale's band, which keeps the pipeline's registers as without
 // rescaling.
-template <int B, int NU, bool LYAP, bool DF, bool SC = false>
+//
+// PD = 2 (configurations for one or two CTAs per SM, where no other CTA
+// hides a global load): the update warps load the operands of step s + 2
+// while computing step s, through two register sets used alternately.
+template <int B, int NU, bool LYAP, bool DF, bool SC = false, int PD = 1>
 __device__ int syl_ws_instance(int m, int n, const double *L, long ldl, const double *U, long ldu,
                                const double *C, long ldc, double *X, long ldx, int *info, double *sm,
                                const DfInst *di)
@@ -705,34 +709,81 @@ __device__ int syl_ws_instance(int m, int n, const double *L, long ldl, const do
                 const int nload = nsteps + (has_last ? 1 : 0);
                 Src sa{}, sb{};
                 bool tb = false, tb_next = false;
-                if (nload > 0) {
-                    if (nsteps > 0) step_src<B, LYAP>(0, P1, I, J, mI, nJ, L, ldl, U, ldu, X, ldx, sa, sb, tb_next, sc);
-                    else last_src_t<B, LYAP>(I, J, mI, nJ, L, ldl, U, ldu, sb, tb_next, sc);
-                    pf.load(sa, sb, nsteps > 0, ut);
-                    if constexpr (DF) pf.template store_df<LD>(df2(sA0), df2(sB0), nsteps > 0, ut, sa.sh, sb.sh);
-                    else pf.store(sA0, sB0, nsteps > 0, ut);
-                    named_sync(kBarUpd, TU);
-                }
-                for (int s = 0; s < nsteps; ++s) {
-                    tb = tb_next;
-                    const int buf = s & 1;
-                    const bool more = s + 1 < nload;
-                    const bool next_bulk = s + 1 < nsteps;
-                    if (more) {
-                        if (next_bulk) step_src<B, LYAP>(s + 1, P1, I, J, mI, nJ, L, ldl, U, ldu, X, ldx, sa, sb, tb_next, sc);
+                if constexpr (PD == 2) {
+                    // Step q's operands live in register set q & 1: loaded at
+                    // step q - 2, stored to tile buffer q & 1 after step q - 1.
+                    Prefetch<B, TU> pf1;
+                    Src sa1{}, sb1{};
+                    bool tb0 = false, tb1 = false;
+                    auto src = [&](int q, Src &a, Src &b, bool &tq) {
+                        if (q < nsteps) step_src<B, LYAP>(q, P1, I, J, mI, nJ, L, ldl, U, ldu, X, ldx, a, b, tq, sc);
+                        else last_src_t<B, LYAP>(I, J, mI, nJ, L, ldl, U, ldu, b, tq, sc);
+                    };
+                    auto store = [&](const Prefetch<B, TU> &p, const Src &a, const Src &b, int q) {
+                        const int bf = q & 1;
+                        if constexpr (DF)
+                            p.template store_df<LD>(df2(sA0 + bf * SZ), df2(sB0 + bf * SZ), q < nsteps, ut, a.sh, b.sh);
+                        else
+                            p.store(sA0 + bf * SZ, sB0 + bf * SZ, q < nsteps, ut);
+                    };
+                    auto iter = [&](int q, Prefetch<B, TU> &pc, Src &ac, Src &bc, bool &tc, const Prefetch<B, TU> &pn,
+                                    const Src &an, const Src &bn) {
+                        const bool tq = tc;
+                        if (q + 2 < nload) {
+                            src(q + 2, ac, bc, tc);
+                            pc.load(ac, bc, q + 2 < nsteps, ut);
+                        }
+                        const int bf = q & 1;
+                        if constexpr (DF) upd_df_rt<B, TU, LD>(tq, ae, ao, om, df2(sA0 + bf * SZ), df2(sB0 + bf * SZ));
+                        else upd_fma_rt<B, TU>(tq, ae, ao, om, sA0 + bf * SZ, sB0 + bf * SZ);
+                        if (q + 1 < nload) store(pn, an, bn, q + 1);
+                        named_sync(kBarUpd, TU);
+                    };
+                    if (nload > 0) {
+                        src(0, sa, sb, tb0);
+                        pf.load(sa, sb, nsteps > 0, ut);
+                        store(pf, sa, sb, 0);
+                    }
+                    if (nload > 1) {
+                        src(1, sa1, sb1, tb1);
+                        pf1.load(sa1, sb1, nsteps > 1, ut);
+                    }
+                    if (nload > 0) named_sync(kBarUpd, TU);
+                    for (int q = 0; q < nsteps; q += 2) {
+                        iter(q, pf, sa, sb, tb0, pf1, sa1, sb1);
+                        if (q + 1 < nsteps) iter(q + 1, pf1, sa1, sb1, tb1, pf, sa, sb);
+                    }
+                    tb_next = (nsteps & 1) ? tb1 : tb0;
+                } else {
+                    if (nload > 0) {
+                        if (nsteps > 0) step_src<B, LYAP>(0, P1, I, J, mI, nJ, L, ldl, U, ldu, X, ldx, sa, sb, tb_next, sc);
                         else last_src_t<B, LYAP>(I, J, mI, nJ, L, ldl, U, ldu, sb, tb_next, sc);
-                        pf.load(sa, sb, next_bulk, ut);
+                        pf.load(sa, sb, nsteps > 0, ut);
+                        if constexpr (DF) pf.template store_df<LD>(df2(sA0), df2(sB0), nsteps > 0, ut, sa.sh, sb.sh);
+                        else pf.store(sA0, sB0, nsteps > 0, ut);
+                        named_sync(kBarUpd, TU);
                     }
-                    if constexpr (DF) {
-                        upd_df_rt<B, TU, LD>(tb, ae, ao, om, df2(sA0 + buf * SZ), df2(sB0 + buf * SZ));
-                        if (more)
-                            pf.template store_df<LD>(df2(sA0 + (buf ^ 1) * SZ), df2(sB0 + (buf ^ 1) * SZ), next_bulk, ut,
-                                                     sa.sh, sb.sh);
-                    } else {
-                        upd_fma_rt<B, TU>(tb, ae, ao, om, sA0 + buf * SZ, sB0 + buf * SZ);
-                        if (more) pf.store(sA0 + (buf ^ 1) * SZ, sB0 + (buf ^ 1) * SZ, next_bulk, ut);
+                    for (int s = 0; s < nsteps; ++s) {
+                        tb = tb_next;
+                        const int buf = s & 1;
+                        const bool more = s + 1 < nload;
+                        const bool next_bulk = s + 1 < nsteps;
+                        if (more) {
+                            if (next_bulk) step_src<B, LYAP>(s + 1, P1, I, J, mI, nJ, L, ldl, U, ldu, X, ldx, sa, sb, tb_next, sc);
+                            else last_src_t<B, LYAP>(I, J, mI, nJ, L, ldl, U, ldu, sb, tb_next, sc);
+                            pf.load(sa, sb, next_bulk, ut);
+                        }
+                        if constexpr (DF) {
+                            upd_df_rt<B, TU, LD>(tb, ae, ao, om, df2(sA0 + buf * SZ), df2(sB0 + buf * SZ));
+                            if (more)
+                                pf.template store_df<LD>(df2(sA0 + (buf ^ 1) * SZ), df2(sB0 + (buf ^ 1) * SZ), next_bulk, ut,
+                                                         sa.sh, sb.sh);
+                        } else {
+                            upd_fma_rt<B, TU>(tb, ae, ao, om, sA0 + buf * SZ, sB0 + buf * SZ);
+                            if (more) pf.store(sA0 + (buf ^ 1) * SZ, sB0 + (buf ^ 1) * SZ, next_bulk, ut);
+                        }
+                        named_sync(kBarUpd, TU);
                     }
-                    named_sync(kBarUpd, TU);
                 }
                 if (t > 0) named_sync(kBarX, TALL);        // X of block t-1 is final
                 if (has_last) {
@@ -1051,8 +1102,9 @@ __global__ void __launch_bounds__(32 * NU + 32, MINB) syl_ws_kernel(Operands o, 
         }
         const double *U = LYAP ? nullptr : o.U[b];
         const int ldu = LYAP ? 0 : o.ldu[b];
-        const int st = syl_ws_instance<B, NU, LYAP, DF, SC>(m, n, o.A[b], o.lda[b], U, ldu, o.C[b], o.ldc[b], o.X[b],
-                                                            o.ldx[b], o.info + b, sm, DF ? s.dfs + b : nullptr);
+        const int st = syl_ws_instance<B, NU, LYAP, DF, SC, MINB <= 2 ? 2 : 1>(m, n, o.A[b], o.lda[b], U, ldu, o.C[b],
+                                                                              o.ldc[b], o.X[b], o.ldx[b], o.info + b,
+                                                                              sm, DF ? s.dfs + b : nullptr);
         // Out of the double-float range: syl_ws_fixup_kernel, launched last,
         // solves the instance again in FP64 (unless X overwrote C).
         if (DF && st != 0 && threadIdx.x == 0) {
@@ -1213,19 +1265,23 @@ cudaError_t launch_syl_df(const Operands &o, const Sched &s, const Launch &l, cu
 }
 
 // Warp-specialised configurations: block B, NU update warps (+1 diagonal warp);
-// df: double-float update warps (plus the scaled pass and the range fix-up pass).
+// df: double-float update warps (plus the scaled pass and the range fix-up pass);
+// few: at most two CTAs per SM and the two-step operand prefetch.
 cudaError_t launch_syl_ws(int block, int nu, bool lyap, bool df, const Operands &o, const Sched &s, const Launch &l,
-                          cudaStream_t st)
+                          cudaStream_t st, bool few)
 {
 #define WS_ONE(BB, NN, MB, LY, D)                                                                          \
     launch_ws(syl_ws_kernel<BB, NN, LY, MB, D, false>, 32 * NN + 32, ws_smem_bytes<BB, D>(), l.batch, st, o, s, l.group)
-#define WS_CASE(BB, NN, MB)                                                                                \
-    if (block == BB && nu == NN)                                                                           \
+#define WS_CASE(BB, NN, MB, FEW)                                                                           \
+    if (block == BB && nu == NN && few == FEW)                                                             \
         return df ? (lyap ? launch_syl_df<BB, NN, MB, true>(o, s, l, st) : launch_syl_df<BB, NN, MB, false>(o, s, l, st)) \
                   : (lyap ? WS_ONE(BB, NN, MB, true, false) : WS_ONE(BB, NN, MB, false, false));
-    WS_CASE(16, 4, 6)
-    WS_CASE(16, 2, 8)
-    WS_CASE(16, 1, 8)
+    WS_CASE(16, 4, 6, false)
+    WS_CASE(16, 2, 8, false)
+    WS_CASE(16, 1, 8, false)
+    WS_CASE(16, 4, 2, true)    // few instances per SM: two-step operand prefetch
+    WS_CASE(16, 8, 1, true)
+    WS_CASE(32, 8, 1, true)
 #undef WS_CASE
 #undef WS_ONE
     return cudaErrorInvalidValue;

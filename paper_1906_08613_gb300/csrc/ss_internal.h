@@ -119,9 +119,10 @@ cudaError_t launch_trlyap(const Operands &o, const Sched &s, const Launch &l, cu
 
 // Sylvester / Lyapunov with warp-specialised CTAs (block B, nu update warps
 // plus one diagonal warp); df: the update warps compute in double-float on the
-// FP32 pipe (SS_MODE_DF), otherwise in FP64.
+// FP32 pipe (SS_MODE_DF), otherwise in FP64; few: the configuration for one
+// or two CTAs per SM (two-step operand prefetch).
 cudaError_t launch_syl_ws(int block, int nu, bool lyap, bool df, const Operands &o, const Sched &s, const Launch &l,
-                          cudaStream_t st);
+                          cudaStream_t st, bool few);
 
 // Cholesky with warp-specialised CTAs (block B, nu update warps plus one
 // diagonal warp); df: double-float update warps (SS_MODE_DF).

@@ -296,6 +296,10 @@ WORKLOADS = {
     "trsyl_1024xU4-128": dict(op="trsyl", sizes=lambda s: sizes_uniform(1024, 4, 128, s)),
     "trlyap_512x128": dict(op="trlyap", sizes=lambda s: sizes_fixed(512, 128)),
     "potrf_2048xLU8-256": dict(op="potrf", sizes=lambda s: sizes_log_uniform(2048, 8, 256, s)),
+    # few large instances (one or two CTAs per SM): n uniform in {257..512}
+    "trsyl_64xU257-512": dict(op="trsyl", sizes=lambda s: sizes_uniform(64, 257, 512, s)),
+    "trsyl_256xU257-512": dict(op="trsyl", sizes=lambda s: sizes_uniform(256, 257, 512, s)),
+    "trlyap_128xU257-512": dict(op="trlyap", sizes=lambda s: sizes_uniform(128, 257, 512, s)),
 }
 
 

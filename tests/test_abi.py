@@ -112,10 +112,13 @@ def test_df_mode_host_side(lib):
     text = open(HEADER).read()
     assert int(re.search(r"#define SS_MODE_DF\s+(\d+)", text).group(1)) == ss.MODE_DF
     assert ss.MODES["df"] == ss.MODE_DF
-    for op, want in ((ss.OP_POTRF, 2), (ss.OP_TRSYL, 3), (ss.OP_TRLYAP, 3)):
+    for op, want in ((ss.OP_POTRF, 2), (ss.OP_TRSYL, 6), (ss.OP_TRLYAP, 6)):
         cnt = ss.ss_config_count(op, ss.MODE_DF)
         assert cnt == want
-        assert all(ss.ss_config_describe(op, ss.MODE_DF, c)[2] == 4 for c in range(cnt))
+        # variant 4: the double-float pipeline; bit 3 (Sylvester / Lyapunov):
+        # its form for one or two CTAs per SM
+        assert all(ss.ss_config_describe(op, ss.MODE_DF, c)[2] & ~8 == 4 for c in range(cnt))
+        assert sum(ss.ss_config_describe(op, ss.MODE_DF, c)[2] == 12 for c in range(cnt)) == (3 if op != ss.OP_POTRF else 0)
         # FP64's workspace plus 24 bytes per instance (the scale pre-pass's
         # exponents and diagonal maximum, the flag that hands an instance to
         # the rescaled pass), 256-byte aligned; no scratch.
@@ -132,7 +135,7 @@ def test_df_mode_host_side(lib):
     with pytest.raises(ss.SmallSolveError):
         ss.ss_set_auto_table(ss.OP_POTRF, [ss.MODE_DF], [2])
     with pytest.raises(ss.SmallSolveError):
-        ss.ss_set_config_table(ss.OP_TRLYAP, ss.MODE_DF, [3])
+        ss.ss_set_config_table(ss.OP_TRLYAP, ss.MODE_DF, [6])
 
 
 def test_config_table_validation(lib):
