@@ -44,14 +44,16 @@ def bin_range(k: int):
 
 
 def default_buckets(max_bin: int = 9):
-    """(op, bin, batch) buckets: two batch sizes per bin up to n = 128; for
-    larger n a small, a medium and a large batch (a mixed stream of n up to 512
+    """(op, bin, batch) buckets: three batch counts per bin, 256 / 1024 / 2048
+    up to n = 128 and 64 / 256 / 1024 above (a mixed stream of n up to 512
     puts several hundred instances in each of those bins, where the kernels
-    move from latency- to throughput-bound)."""
+    move from latency- to throughput-bound).  With three counts per bin a
+    held-out count has a trained one on either side or both, so the selector
+    interpolates in batch where configurations of different occupancy cross."""
     out = []
     for op in OPS:
         for k in range(2, max_bin + 1):
-            batches = (256, 2048) if k <= 7 else (64, 256, 1024)
+            batches = (256, 1024, 2048) if k <= 7 else (64, 256, 1024)
             for b in batches:
                 out.append((op, k, b))
     return out
