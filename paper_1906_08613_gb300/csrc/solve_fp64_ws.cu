@@ -208,8 +208,10 @@ struct OutMap {
     static constexpr int E = B * B / TU;
     int row[E], col[E];
     unsigned valid;
+    bool same_row;    // every output in row row[0] (full blocks)
     __device__ __forceinline__ void set(int m, int nn, int ut)
     {
+        same_row = m == B && TU % B == 0;
         valid = 0u;
 #pragma unroll
         for (int r = 0; r < E; ++r) {
@@ -239,6 +241,7 @@ struct OutMap {
     // diagonal block, whose upper part is the transpose).
     __device__ __forceinline__ void set_lower(int m, int ut)
     {
+        same_row = false;
         valid = 0u;
 #pragma unroll
         for (int r = 0; r < E; ++r) {
@@ -319,6 +322,26 @@ struct Prefetch {
             tB[r + c * LD] = v;
         }
     }
+    // Bulk-step tiles K-contiguous, for upd_dfk: op(A)(row, k) at
+    // tA[k + row * LDT], op(B)(k, col) at tB[k + col * LDT] (tb: op(B) is the
+    // staged tile transposed).
+    template <int LDT>
+    __device__ __forceinline__ void store_dfk(float2 *tA, float2 *tB, bool has_a, bool tb, int ut, int sha,
+                                              int shb) const
+    {
+#pragma unroll
+        for (int q = 0; q < PE; ++q) {
+            const int e = ut + TU * q, r = e % B, c = e / B;
+            float2 v;
+            if (has_a) {
+                split_df_s(a[q], sha, v.x, v.y);
+                tA[c + r * LDT] = v;
+            }
+            split_df_s(b[q], shb, v.x, v.y);
+            if (tb) tB[c + r * LDT] = v;
+            else    tB[r + c * LDT] = v;
+        }
+    }
 };
 
 // acc -= A * op(Bm) over B terms, A(row, k) = A[row + k*LD],
@@ -389,6 +412,31 @@ __device__ __forceinline__ void upd_df(float (&ah)[B * B / TU], float (&al)[B * 
                 const float2 a = A[om.row[r] + k * LDT];
                 const float2 b = TB ? Bm[om.col[r] + k * LDT] : Bm[k + om.col[r] * LDT];
                 df_msub(ah[r], al[r], a.x, a.y, b.x, b.y);
+            }
+        }
+    }
+}
+
+// (ah, al) -= op(A) op(B) over B terms from K-contiguous tiles (store_dfk):
+// each 16-byte load brings two terms, and with om.same_row the A pair is
+// loaded once for all of the thread's outputs.
+template <int B, int TU, int LDT>
+__device__ __forceinline__ void upd_dfk(float (&ah)[B * B / TU], float (&al)[B * B / TU], const OutMap<B, TU> &om,
+                                        const float2 *A, const float2 *Bm)
+{
+    constexpr int E = B * B / TU;
+    static_assert(B % 2 == 0 && LDT % 2 == 0, "16-byte pairs of terms");
+#pragma unroll 1
+    for (int k = 0; k < B; k += 2) {
+        const float4 a0 = *reinterpret_cast<const float4 *>(A + k + om.row[0] * LDT);
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            if (om.ok(r)) {
+                const float4 a = (r == 0 || om.same_row) ? a0
+                                                         : *reinterpret_cast<const float4 *>(A + k + om.row[r] * LDT);
+                const float4 b = *reinterpret_cast<const float4 *>(Bm + k + om.col[r] * LDT);
+                df_msub(ah[r], al[r], a.x, a.y, b.x, b.y);
+                df_msub(ah[r], al[r], a.z, a.w, b.z, b.w);
             }
         }
     }
@@ -719,30 +767,34 @@ __device__ int syl_ws_instance(int m, int n, const double *L, long ldl, const do
                         if (q < nsteps) step_src<B, LYAP>(q, P1, I, J, mI, nJ, L, ldl, U, ldu, X, ldx, a, b, tq, sc);
                         else last_src_t<B, LYAP>(I, J, mI, nJ, L, ldl, U, ldu, b, tq, sc);
                     };
-                    auto store = [&](const Prefetch<B, TU> &p, const Src &a, const Src &b, int q) {
+                    auto store = [&](const Prefetch<B, TU> &p, const Src &a, const Src &b, bool tq, int q) {
                         const int bf = q & 1;
-                        if constexpr (DF)
-                            p.template store_df<LD>(df2(sA0 + bf * SZ), df2(sB0 + bf * SZ), q < nsteps, ut, a.sh, b.sh);
-                        else
+                        if constexpr (DF) {
+                            if (q < nsteps)
+                                p.template store_dfk<LD>(df2(sA0 + bf * SZ), df2(sB0 + bf * SZ), true, tq, ut, a.sh, b.sh);
+                            else
+                                p.template store_df<LD>(df2(sA0 + bf * SZ), df2(sB0 + bf * SZ), false, ut, a.sh, b.sh);
+                        } else {
                             p.store(sA0 + bf * SZ, sB0 + bf * SZ, q < nsteps, ut);
+                        }
                     };
                     auto iter = [&](int q, Prefetch<B, TU> &pc, Src &ac, Src &bc, bool &tc, const Prefetch<B, TU> &pn,
-                                    const Src &an, const Src &bn) {
+                                    const Src &an, const Src &bn, const bool &tn) {
                         const bool tq = tc;
                         if (q + 2 < nload) {
                             src(q + 2, ac, bc, tc);
                             pc.load(ac, bc, q + 2 < nsteps, ut);
                         }
                         const int bf = q & 1;
-                        if constexpr (DF) upd_df_rt<B, TU, LD>(tq, ae, ao, om, df2(sA0 + bf * SZ), df2(sB0 + bf * SZ));
+                        if constexpr (DF) upd_dfk<B, TU, LD>(ae, ao, om, df2(sA0 + bf * SZ), df2(sB0 + bf * SZ));
                         else upd_fma_rt<B, TU>(tq, ae, ao, om, sA0 + bf * SZ, sB0 + bf * SZ);
-                        if (q + 1 < nload) store(pn, an, bn, q + 1);
+                        if (q + 1 < nload) store(pn, an, bn, tn, q + 1);
                         named_sync(kBarUpd, TU);
                     };
                     if (nload > 0) {
                         src(0, sa, sb, tb0);
                         pf.load(sa, sb, nsteps > 0, ut);
-                        store(pf, sa, sb, 0);
+                        store(pf, sa, sb, tb0, 0);
                     }
                     if (nload > 1) {
                         src(1, sa1, sb1, tb1);
@@ -750,8 +802,8 @@ __device__ int syl_ws_instance(int m, int n, const double *L, long ldl, const do
                     }
                     if (nload > 0) named_sync(kBarUpd, TU);
                     for (int q = 0; q < nsteps; q += 2) {
-                        iter(q, pf, sa, sb, tb0, pf1, sa1, sb1);
-                        if (q + 1 < nsteps) iter(q + 1, pf1, sa1, sb1, tb1, pf, sa, sb);
+                        iter(q, pf, sa, sb, tb0, pf1, sa1, sb1, tb1);
+                        if (q + 1 < nsteps) iter(q + 1, pf1, sa1, sb1, tb1, pf, sa, sb, tb0);
                     }
                     tb_next = (nsteps & 1) ? tb1 : tb0;
                 } else {
@@ -759,8 +811,12 @@ __device__ int syl_ws_instance(int m, int n, const double *L, long ldl, const do
                         if (nsteps > 0) step_src<B, LYAP>(0, P1, I, J, mI, nJ, L, ldl, U, ldu, X, ldx, sa, sb, tb_next, sc);
                         else last_src_t<B, LYAP>(I, J, mI, nJ, L, ldl, U, ldu, sb, tb_next, sc);
                         pf.load(sa, sb, nsteps > 0, ut);
-                        if constexpr (DF) pf.template store_df<LD>(df2(sA0), df2(sB0), nsteps > 0, ut, sa.sh, sb.sh);
-                        else pf.store(sA0, sB0, nsteps > 0, ut);
+                        if constexpr (DF) {
+                            if (nsteps > 0) pf.template store_dfk<LD>(df2(sA0), df2(sB0), true, tb_next, ut, sa.sh, sb.sh);
+                            else pf.template store_df<LD>(df2(sA0), df2(sB0), false, ut, sa.sh, sb.sh);
+                        } else {
+                            pf.store(sA0, sB0, nsteps > 0, ut);
+                        }
                         named_sync(kBarUpd, TU);
                     }
                     for (int s = 0; s < nsteps; ++s) {
@@ -774,10 +830,15 @@ __device__ int syl_ws_instance(int m, int n, const double *L, long ldl, const do
                             pf.load(sa, sb, next_bulk, ut);
                         }
                         if constexpr (DF) {
-                            upd_df_rt<B, TU, LD>(tb, ae, ao, om, df2(sA0 + buf * SZ), df2(sB0 + buf * SZ));
-                            if (more)
-                                pf.template store_df<LD>(df2(sA0 + (buf ^ 1) * SZ), df2(sB0 + (buf ^ 1) * SZ), next_bulk, ut,
-                                                         sa.sh, sb.sh);
+                            upd_dfk<B, TU, LD>(ae, ao, om, df2(sA0 + buf * SZ), df2(sB0 + buf * SZ));
+                            if (more) {
+                                if (next_bulk)
+                                    pf.template store_dfk<LD>(df2(sA0 + (buf ^ 1) * SZ), df2(sB0 + (buf ^ 1) * SZ), true,
+                                                              tb_next, ut, sa.sh, sb.sh);
+                                else
+                                    pf.template store_df<LD>(df2(sA0 + (buf ^ 1) * SZ), df2(sB0 + (buf ^ 1) * SZ), false,
+                                                             ut, sa.sh, sb.sh);
+                            }
                         } else {
                             upd_fma_rt<B, TU>(tb, ae, ao, om, sA0 + buf * SZ, sB0 + buf * SZ);
                             if (more) pf.store(sA0 + (buf ^ 1) * SZ, sB0 + (buf ^ 1) * SZ, next_bulk, ut);
