@@ -203,16 +203,21 @@ int sm_count()
     return cache[dev];
 }
 
+// SS_MODE_DF Sylvester / Lyapunov: the pre-split double-float copies of L,
+// U and X (3 pairs per n^2, the bound of m^2 + n^2 + m n for max(m, n) = n).
+static long long df_scratch_per_n2(int op) { return op != SS_OP_POTRF ? 6 : 0; }
+
 static long long scratch_per_n2(int op, int mode)
 {
     if (mode == SS_MODE_AUTO) {
-        long long m = 0;
+        long long m = df_scratch_per_n2(op);
         for (int md = 1; md < SS_NUM_MODES; ++md) {
             const long long v = mixed_scratch_per_n2(op, md);
             if (v > m) m = v;
         }
         return m;
     }
+    if (mode == SS_MODE_DF) return df_scratch_per_n2(op);
     return mode == SS_MODE_FP64 ? 0 : mixed_scratch_per_n2(op, mode);
 }
 

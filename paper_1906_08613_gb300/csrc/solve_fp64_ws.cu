@@ -344,6 +344,63 @@ struct Prefetch {
     }
 };
 
+// Double-float Sylvester / Lyapunov pipeline: the operand tiles come from
+// per-instance copies already split into double-float pairs (L and U when
+// the instance starts, X as the diagonal warp finishes each block; see
+// syl_ws_instance), so staging only copies.  Layout of the copies in the
+// instance's scratch, leading dimensions m, n, m: L (m x m), U (n x n),
+// X (m x n).
+struct SrcF {
+    const float2 *F;
+    long ld;
+    int rows, cols;
+    bool sym;   // the symmetric diagonal block, its lower triangle stored
+};
+
+template <int B, int TU>
+struct PrefetchF {
+    static constexpr int PE = B * B / TU;
+    float2 a[PE], b[PE];
+
+    __device__ __forceinline__ static float2 get(const SrcF &s, int r, int c)
+    {
+        if (r >= s.rows || c >= s.cols) return make_float2(0.f, 0.f);
+        if (s.sym && r < c) return s.F[c + (long)r * s.ld];
+        return s.F[r + (long)c * s.ld];
+    }
+    __device__ __forceinline__ void load(const SrcF &sa, const SrcF &sb, bool has_a, int ut)
+    {
+#pragma unroll
+        for (int q = 0; q < PE; ++q) {
+            const int e = ut + TU * q, r = e % B, c = e / B;
+            a[q] = has_a ? get(sa, r, c) : make_float2(0.f, 0.f);
+            b[q] = get(sb, r, c);
+        }
+    }
+    // Bulk-step tiles, K-contiguous (see upd_dfk).
+    template <int LDT>
+    __device__ __forceinline__ void store_k(float2 *tA, float2 *tB, bool tb, int ut) const
+    {
+#pragma unroll
+        for (int q = 0; q < PE; ++q) {
+            const int e = ut + TU * q, r = e % B, c = e / B;
+            tA[c + r * LDT] = a[q];
+            if (tb) tB[c + r * LDT] = b[q];
+            else    tB[r + c * LDT] = b[q];
+        }
+    }
+    // The last phase's tile, natural layout.
+    template <int LDT>
+    __device__ __forceinline__ void store_b(float2 *tB, int ut) const
+    {
+#pragma unroll
+        for (int q = 0; q < PE; ++q) {
+            const int e = ut + TU * q, r = e % B, c = e / B;
+            tB[r + c * LDT] = b[q];
+        }
+    }
+};
+
 // acc -= A * op(Bm) over B terms, A(row, k) = A[row + k*LD],
 // op(Bm)(k, col) = TB ? Bm[col + k*LD] : Bm[k + col*LD]; even and odd k go to
 // separate accumulators (two independent FMA chains per output).
@@ -538,6 +595,55 @@ __device__ __forceinline__ void last_src_t(int I, int J, int mI, int nJ, const d
     tb = LYAP;
 }
 
+// step_src / last_src_t on the pre-split copies (dfw: L, then U, then X).
+template <int B, bool LYAP>
+__device__ __forceinline__ void step_src_f(int s, int P1, int I, int J, int mI, int nJ, int m, int n,
+                                           const float2 *dfw, SrcF &a, SrcF &b, bool &tb)
+{
+    const int i0 = I * B, j0 = J * B;
+    const float2 *Lf = dfw, *Uf = dfw + (long)m * m, *Xf = Uf + (long)n * n;
+    if (s < P1) {
+        const int k0 = s * B;
+        a = SrcF{Lf + i0 + (long)k0 * m, m, mI, B, false};                 // L_IK
+        if (!LYAP || s > J) {
+            b = SrcF{Xf + k0 + (long)j0 * m, m, B, nJ, false};             // X_KJ
+            tb = false;
+        } else if (s == J) {
+            b = SrcF{Xf + j0 + (long)j0 * m, m, nJ, nJ, true};             // X_JJ (symmetric)
+            tb = false;
+        } else {
+            b = SrcF{Xf + j0 + (long)k0 * m, m, nJ, B, false};             // X_JK, used transposed
+            tb = true;
+        }
+    } else {
+        const int k0 = (s - P1) * B;
+        a = SrcF{Xf + i0 + (long)k0 * m, m, mI, B, false};                 // X_IK
+        if (!LYAP) {
+            b = SrcF{Uf + k0 + (long)j0 * n, n, B, nJ, false};             // U_KJ
+            tb = false;
+        } else {
+            b = SrcF{Lf + j0 + (long)k0 * m, m, nJ, B, false};             // L_JK, used transposed
+            tb = true;
+        }
+    }
+}
+
+template <int B, bool LYAP>
+__device__ __forceinline__ void last_src_f(int I, int J, int mI, int nJ, int m, int n, const float2 *dfw, SrcF &b,
+                                           bool &tb)
+{
+    const int j0 = J * B;
+    const float2 *Lf = dfw, *Uf = dfw + (long)m * m;
+    if (J == 0) {
+        b = SrcF{Lf + I * B + (long)(I - 1) * B * m, m, mI, B, false};
+        tb = false;
+        return;
+    }
+    const int k0 = (J - 1) * B;
+    b = LYAP ? SrcF{Lf + j0 + (long)k0 * m, m, nJ, B, false} : SrcF{Uf + k0 + (long)j0 * n, n, B, nJ, false};
+    tb = LYAP;
+}
+
 // Shared tiles of the warp-specialised kernels: FP64 uses nine tiles of
 // Tile<B>; DF uses ten tiles of B x (B + 2) double-float pairs (an even
 // leading dimension of 8-byte elements puts the entries of an anti-diagonal,
@@ -579,10 +685,13 @@ constexpr size_t ws_smem_bytes() { return (size_t)WsTile<B, DF>::N * WsTile<B, D
 // PD = 2 (configurations for one or two CTAs per SM, where no other CTA
 // hides a global load): the update warps load the operands of step s + 2
 // while computing step s, through two register sets used alternately.
+//
+// DF: dfw, the instance's scratch for the pre-split copies (SrcF), holds
+// m*m + n*n + m*n double-float pairs.
 template <int B, int NU, bool LYAP, bool DF, bool SC = false, int PD = 1>
 __device__ int syl_ws_instance(int m, int n, const double *L, long ldl, const double *U, long ldu,
                                const double *C, long ldc, double *X, long ldx, int *info, double *sm,
-                               const DfInst *di)
+                               const DfInst *di, float2 *dfw = nullptr)
 {
     constexpr int LD = WsTile<B, DF>::LD, SZ = WsTile<B, DF>::SZ;
     constexpr int TU = 32 * NU, TALL = TU + 32;
@@ -607,6 +716,27 @@ __device__ int syl_ws_instance(int m, int n, const double *L, long ldl, const do
         if (threadIdx.x == 0) {
             *s_bad = 0;
             *s_rng = 0;
+        }
+        // L (strict lower triangle) and U (strict upper) split once, scaled;
+        // the diagonal blocks' operands are prepared per block as before.
+        for (long e = threadIdx.x; e < (long)m * m; e += blockDim.x) {
+            const int r = (int)(e % m), c = (int)(e / m);
+            if (r > c) {
+                float2 v;
+                split_df_s(L[r + (long)c * ldl], sc.op, v.x, v.y);
+                dfw[e] = v;
+            }
+        }
+        if (!LYAP) {
+            float2 *Uf = dfw + (long)m * m;
+            for (long e = threadIdx.x; e < (long)n * n; e += blockDim.x) {
+                const int r = (int)(e % n), c = (int)(e / n);
+                if (r < c) {
+                    float2 v;
+                    split_df_s(U[r + (long)c * ldu], sc.op, v.x, v.y);
+                    Uf[e] = v;
+                }
+            }
         }
         __syncthreads();
     } else {
@@ -647,6 +777,8 @@ __device__ int syl_ws_instance(int m, int n, const double *L, long ldl, const do
                             const float2 v = dT[r + c * LD];
                             rng |= df_out_of_range(v.x);          // every entry of X passes here once
                             X[(i0 + r) + (long)(j0 + c) * ldx] = df_to_double_s(v.x, v.y, -sc.x);
+                            // scaled units, for the update warps' staging
+                            dfw[(long)m * m + (long)n * n + (i0 + r) + (long)(j0 + c) * m] = v;
                         }
                     }
                 } else {
@@ -694,7 +826,6 @@ __device__ int syl_ws_instance(int m, int n, const double *L, long ldl, const do
         const int ut = threadIdx.x - 32;
         OutMap<B, TU> om;
         using Acc = typename std::conditional<DF, float, double>::type;
-        Prefetch<B, TU> pf;
         int t = 0;
         for (int I = 0; I < mb; ++I) {
             const int mI = min(B, m - I * B), i0 = I * B;
@@ -755,46 +886,53 @@ __device__ int syl_ws_instance(int m, int n, const double *L, long ldl, const do
                 const bool has_last = J > 0 || lfirst;
                 const int nsteps = P1 + (J > 0 ? J - 1 : 0);
                 const int nload = nsteps + (has_last ? 1 : 0);
-                Src sa{}, sb{};
-                bool tb = false, tb_next = false;
+                using SrcT = typename std::conditional<DF, SrcF, Src>::type;
+                using PfT = typename std::conditional<DF, PrefetchF<B, TU>, Prefetch<B, TU>>::type;
+                // Operands of step q (q == nsteps: the last phase's tile).
+                auto src = [&](int q, SrcT &a, SrcT &b, bool &tq) {
+                    if constexpr (DF) {
+                        if (q < nsteps) step_src_f<B, LYAP>(q, P1, I, J, mI, nJ, m, n, dfw, a, b, tq);
+                        else last_src_f<B, LYAP>(I, J, mI, nJ, m, n, dfw, b, tq);
+                    } else {
+                        if (q < nsteps) step_src<B, LYAP>(q, P1, I, J, mI, nJ, L, ldl, U, ldu, X, ldx, a, b, tq, sc);
+                        else last_src_t<B, LYAP>(I, J, mI, nJ, L, ldl, U, ldu, b, tq, sc);
+                    }
+                };
+                // The tiles of step q into buffer q & 1.
+                auto stage = [&](const PfT &p, bool tq, int q) {
+                    const int bf = q & 1;
+                    if constexpr (DF) {
+                        if (q < nsteps) p.template store_k<LD>(df2(sA0 + bf * SZ), df2(sB0 + bf * SZ), tq, ut);
+                        else p.template store_b<LD>(df2(sB0 + bf * SZ), ut);
+                    } else {
+                        p.store(sA0 + bf * SZ, sB0 + bf * SZ, q < nsteps, ut);
+                    }
+                };
+                auto compute = [&](bool tq, int bf) {
+                    if constexpr (DF) upd_dfk<B, TU, LD>(ae, ao, om, df2(sA0 + bf * SZ), df2(sB0 + bf * SZ));
+                    else upd_fma_rt<B, TU>(tq, ae, ao, om, sA0 + bf * SZ, sB0 + bf * SZ);
+                };
+                bool tb_next = false;
                 if constexpr (PD == 2) {
                     // Step q's operands live in register set q & 1: loaded at
                     // step q - 2, stored to tile buffer q & 1 after step q - 1.
-                    Prefetch<B, TU> pf1;
-                    Src sa1{}, sb1{};
+                    PfT pf0, pf1;
+                    SrcT sa0{}, sb0{}, sa1{}, sb1{};
                     bool tb0 = false, tb1 = false;
-                    auto src = [&](int q, Src &a, Src &b, bool &tq) {
-                        if (q < nsteps) step_src<B, LYAP>(q, P1, I, J, mI, nJ, L, ldl, U, ldu, X, ldx, a, b, tq, sc);
-                        else last_src_t<B, LYAP>(I, J, mI, nJ, L, ldl, U, ldu, b, tq, sc);
-                    };
-                    auto store = [&](const Prefetch<B, TU> &p, const Src &a, const Src &b, bool tq, int q) {
-                        const int bf = q & 1;
-                        if constexpr (DF) {
-                            if (q < nsteps)
-                                p.template store_dfk<LD>(df2(sA0 + bf * SZ), df2(sB0 + bf * SZ), true, tq, ut, a.sh, b.sh);
-                            else
-                                p.template store_df<LD>(df2(sA0 + bf * SZ), df2(sB0 + bf * SZ), false, ut, a.sh, b.sh);
-                        } else {
-                            p.store(sA0 + bf * SZ, sB0 + bf * SZ, q < nsteps, ut);
-                        }
-                    };
-                    auto iter = [&](int q, Prefetch<B, TU> &pc, Src &ac, Src &bc, bool &tc, const Prefetch<B, TU> &pn,
-                                    const Src &an, const Src &bn, const bool &tn) {
+                    auto iter = [&](int q, PfT &pc, SrcT &ac, SrcT &bc, bool &tc, const PfT &pn, const bool &tn) {
                         const bool tq = tc;
                         if (q + 2 < nload) {
                             src(q + 2, ac, bc, tc);
                             pc.load(ac, bc, q + 2 < nsteps, ut);
                         }
-                        const int bf = q & 1;
-                        if constexpr (DF) upd_dfk<B, TU, LD>(ae, ao, om, df2(sA0 + bf * SZ), df2(sB0 + bf * SZ));
-                        else upd_fma_rt<B, TU>(tq, ae, ao, om, sA0 + bf * SZ, sB0 + bf * SZ);
-                        if (q + 1 < nload) store(pn, an, bn, tn, q + 1);
+                        compute(tq, q & 1);
+                        if (q + 1 < nload) stage(pn, tn, q + 1);
                         named_sync(kBarUpd, TU);
                     };
                     if (nload > 0) {
-                        src(0, sa, sb, tb0);
-                        pf.load(sa, sb, nsteps > 0, ut);
-                        store(pf, sa, sb, tb0, 0);
+                        src(0, sa0, sb0, tb0);
+                        pf0.load(sa0, sb0, nsteps > 0, ut);
+                        stage(pf0, tb0, 0);
                     }
                     if (nload > 1) {
                         src(1, sa1, sb1, tb1);
@@ -802,47 +940,28 @@ __device__ int syl_ws_instance(int m, int n, const double *L, long ldl, const do
                     }
                     if (nload > 0) named_sync(kBarUpd, TU);
                     for (int q = 0; q < nsteps; q += 2) {
-                        iter(q, pf, sa, sb, tb0, pf1, sa1, sb1, tb1);
-                        if (q + 1 < nsteps) iter(q + 1, pf1, sa1, sb1, tb1, pf, sa, sb, tb0);
+                        iter(q, pf0, sa0, sb0, tb0, pf1, tb1);
+                        if (q + 1 < nsteps) iter(q + 1, pf1, sa1, sb1, tb1, pf0, tb0);
                     }
                     tb_next = (nsteps & 1) ? tb1 : tb0;
                 } else {
+                    PfT pf;
+                    SrcT sa{}, sb{};
                     if (nload > 0) {
-                        if (nsteps > 0) step_src<B, LYAP>(0, P1, I, J, mI, nJ, L, ldl, U, ldu, X, ldx, sa, sb, tb_next, sc);
-                        else last_src_t<B, LYAP>(I, J, mI, nJ, L, ldl, U, ldu, sb, tb_next, sc);
+                        src(0, sa, sb, tb_next);
                         pf.load(sa, sb, nsteps > 0, ut);
-                        if constexpr (DF) {
-                            if (nsteps > 0) pf.template store_dfk<LD>(df2(sA0), df2(sB0), true, tb_next, ut, sa.sh, sb.sh);
-                            else pf.template store_df<LD>(df2(sA0), df2(sB0), false, ut, sa.sh, sb.sh);
-                        } else {
-                            pf.store(sA0, sB0, nsteps > 0, ut);
-                        }
+                        stage(pf, tb_next, 0);
                         named_sync(kBarUpd, TU);
                     }
-                    for (int s = 0; s < nsteps; ++s) {
-                        tb = tb_next;
-                        const int buf = s & 1;
-                        const bool more = s + 1 < nload;
-                        const bool next_bulk = s + 1 < nsteps;
+                    for (int q = 0; q < nsteps; ++q) {
+                        const bool tq = tb_next;
+                        const bool more = q + 1 < nload;
                         if (more) {
-                            if (next_bulk) step_src<B, LYAP>(s + 1, P1, I, J, mI, nJ, L, ldl, U, ldu, X, ldx, sa, sb, tb_next, sc);
-                            else last_src_t<B, LYAP>(I, J, mI, nJ, L, ldl, U, ldu, sb, tb_next, sc);
-                            pf.load(sa, sb, next_bulk, ut);
+                            src(q + 1, sa, sb, tb_next);
+                            pf.load(sa, sb, q + 1 < nsteps, ut);
                         }
-                        if constexpr (DF) {
-                            upd_dfk<B, TU, LD>(ae, ao, om, df2(sA0 + buf * SZ), df2(sB0 + buf * SZ));
-                            if (more) {
-                                if (next_bulk)
-                                    pf.template store_dfk<LD>(df2(sA0 + (buf ^ 1) * SZ), df2(sB0 + (buf ^ 1) * SZ), true,
-                                                              tb_next, ut, sa.sh, sb.sh);
-                                else
-                                    pf.template store_df<LD>(df2(sA0 + (buf ^ 1) * SZ), df2(sB0 + (buf ^ 1) * SZ), false,
-                                                             ut, sa.sh, sb.sh);
-                            }
-                        } else {
-                            upd_fma_rt<B, TU>(tb, ae, ao, om, sA0 + buf * SZ, sB0 + buf * SZ);
-                            if (more) pf.store(sA0 + (buf ^ 1) * SZ, sB0 + (buf ^ 1) * SZ, next_bulk, ut);
-                        }
+                        compute(tq, q & 1);
+                        if (more) stage(pf, tb_next, q + 1);
                         named_sync(kBarUpd, TU);
                     }
                 }
@@ -1126,12 +1245,13 @@ __device__ int chol_ws_instance(int n, const double *A, long lda, double *X, lon
 }
 
 __device__ __forceinline__ bool next_instance(const Sched &s, int group, int *s_slot, int &b,
-                                              int head = META_HEAD)
+                                              int head = META_HEAD, int *wpos = nullptr)
 {
     const int lo = s.meta[META_RANGE + 2 * group], hi = s.meta[META_RANGE + 2 * group + 1];
     const int w = lo + claim_slot(s.meta + head + group, s_slot);
     if (w >= hi) return false;
     b = s.perm[w];
+    if (wpos) *wpos = w;
     return true;
 }
 
@@ -1148,9 +1268,19 @@ __global__ void __launch_bounds__(32 * NU + 32, MINB) syl_ws_kernel(Operands o, 
 {
     extern __shared__ double sm[];
     __shared__ int s_slot;
-    auto one = [&](int b) {
+    auto one = [&](int b, int w) {
         const int n = o.n[b], m = o.m != nullptr ? o.m[b] : n;
         if (n == 0 || m == 0) { if (threadIdx.x == 0) o.info[b] = 0; return; }
+        // DF: the instance's share of the workspace scratch (pre-split copies).
+        float2 *dfw = nullptr;
+        if constexpr (DF) {
+            const long long need = 2ll * ((long long)m * m + (long long)n * n + (long long)m * n);
+            if (s.scr == nullptr || s.scratch == nullptr || s.scr[w] + need > s.scratch_elems) {
+                if (threadIdx.x == 0) o.info[b] = SS_INFO_NO_WORK;
+                return;
+            }
+            dfw = reinterpret_cast<float2 *>(static_cast<float *>(s.scratch) + s.scr[w]);
+        }
         if constexpr (DF && !SC) {
             const DfInst d = s.dfs[b];                        // the same on every thread
             if (!DfScale::sylvester(d.eo, d.ec).zero()) {
@@ -1165,7 +1295,7 @@ __global__ void __launch_bounds__(32 * NU + 32, MINB) syl_ws_kernel(Operands o, 
         const int ldu = LYAP ? 0 : o.ldu[b];
         const int st = syl_ws_instance<B, NU, LYAP, DF, SC, MINB <= 2 ? 2 : 1>(m, n, o.A[b], o.lda[b], U, ldu, o.C[b],
                                                                               o.ldc[b], o.X[b], o.ldx[b], o.info + b,
-                                                                              sm, DF ? s.dfs + b : nullptr);
+                                                                              sm, DF ? s.dfs + b : nullptr, dfw);
         // Out of the double-float range: syl_ws_fixup_kernel, launched last,
         // solves the instance again in FP64 (unless X overwrote C).
         if (DF && st != 0 && threadIdx.x == 0) {
@@ -1173,14 +1303,14 @@ __global__ void __launch_bounds__(32 * NU + 32, MINB) syl_ws_kernel(Operands o, 
             s.meta[META_RNG + group] = 1;
         }
     };
-    int b;
+    int b, w = 0;
     claim_init(&s_slot);
     if constexpr (SC) {
         if (s.meta[META_SCL + group] == 0) return;            // the same on every thread
-        while (next_instance(s, group, &s_slot, b, META_SCL_HEAD))
-            if (s.dfs[b].pend != 0) one(b);                   // the same on every thread
+        while (next_instance(s, group, &s_slot, b, META_SCL_HEAD, &w))
+            if (s.dfs[b].pend != 0) one(b, w);                // the same on every thread
     } else {
-        while (next_instance(s, group, &s_slot, b)) one(b);
+        while (next_instance(s, group, &s_slot, b, META_HEAD, &w)) one(b, w);
     }
 }
 

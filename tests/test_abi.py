@@ -121,9 +121,13 @@ def test_df_mode_host_side(lib):
         assert sum(ss.ss_config_describe(op, ss.MODE_DF, c)[2] == 12 for c in range(cnt)) == (3 if op != ss.OP_POTRF else 0)
         # FP64's workspace plus 24 bytes per instance (the scale pre-pass's
         # exponents and diagonal maximum, the flag that hands an instance to
-        # the rescaled pass), 256-byte aligned; no scratch.
+        # the rescaled pass), 256-byte aligned; for Sylvester / Lyapunov also
+        # the pre-split double-float copies of L, U and X (scratch offsets, and
+        # 3 pairs = 24 bytes per max_n^2 per instance).
+        al = lambda x: (x + 255) // 256 * 256
         extra = ss.ss_workspace_size(op, 1000, 128, ss.MODE_DF) - ss.ss_workspace_size(op, 1000, 128, ss.MODE_FP64)
-        assert extra == (1000 * 24 + 255) // 256 * 256
+        want = al(1000 * 24) + (0 if op == ss.OP_POTRF else al(1000 * 8) + al(1000 * 128 * 128 * 24))
+        assert extra == want
     # Argument checks of the DF forms run before any launch.
     assert ss.potrf_upper(1, 4, 1, 1, 1, 1, 1, 1, mode=ss.MODE_DF, cfg=2, check=False) == -10
     assert ss.posv_upper(1, 4, 4, *([1] * 11), mode=ss.MODE_DF, cfg=2, check=False) == -16
