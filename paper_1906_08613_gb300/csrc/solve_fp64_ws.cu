@@ -1434,7 +1434,7 @@ cudaError_t launch_potrf_ws(int block, int nu, bool df, const Operands &o, const
                   : launch_ws(chol_ws_kernel<BB, NN, MB, false, false>, 32 * NN + 32, ws_smem_bytes<BB>(), l.batch, \
                               st, o, s, l.group);
     CWS_CASE(16, 2, 8)
-    CWS_CASE(16, 4, 6)
+    CWS_CASE(16, 4, 7)
 #undef CWS_CASE
     return cudaErrorInvalidValue;
 }
