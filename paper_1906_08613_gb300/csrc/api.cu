@@ -16,7 +16,7 @@ cudaError_t launch_syl_fp64(const Operands &o, const Sched &s, const Launch &l, 
 cudaError_t launch_syl_ws(int block, int nu, bool lyap, bool df, const Operands &o, const Sched &s, const Launch &l,
                           cudaStream_t st, bool few);
 cudaError_t launch_potrf_ws(int block, int nu, bool df, const Operands &o, const Sched &s, const Launch &l,
-                            cudaStream_t st);
+                            cudaStream_t st, bool few);
 cudaError_t launch_mixed(int op, const Operands &o, const Sched &s, const Launch &l, cudaStream_t st);
 int mixed_config_count(int op, int mode);
 const Config *mixed_config_get(int op, int mode, int cfg);
@@ -45,10 +45,10 @@ constexpr int kNumFp64Syl = sizeof(kFp64Syl) / sizeof(kFp64Syl[0]);
 // SS_MODE_DF: variant 4, the warp-specialised pipeline with double-float
 // update warps (Sylvester / Lyapunov: double-float diagonal blocks too;
 // Cholesky: FP64 diagonal warp).
-// Variant bit 3: for one or two CTAs per SM (few, large instances), with the
-// two-step operand prefetch.
+// Variant bit 3: for one or two CTAs per SM (few, large instances): all of
+// the registers, and for Sylvester / Lyapunov the two-step operand prefetch.
 const Config kDfSyl[] = {{16, 64, 4}, {16, 96, 4}, {16, 160, 4}, {16, 160, 12}, {16, 288, 12}, {32, 288, 12}};
-const Config kDfPotrf[] = {{16, 96, 4}, {16, 160, 4}};
+const Config kDfPotrf[] = {{16, 96, 4}, {16, 160, 4}, {16, 160, 12}};
 constexpr int kNumDfSyl = sizeof(kDfSyl) / sizeof(kDfSyl[0]);
 constexpr int kNumDfPotrf = sizeof(kDfPotrf) / sizeof(kDfPotrf[0]);
 // Mode ids 0..SS_MODE_DF index the per-mode tables (SS_MODE_AUTO's slot unused).
@@ -371,7 +371,8 @@ int run(int op, int batch, int max_n, const Operands &o, int mode, int cfg, void
         } else if (l.mode == SS_MODE_DF) {
             const Config *c = config_get(op, SS_MODE_DF, l.cfg);
             if (!c) e = cudaErrorInvalidValue;
-            else if (op == SS_OP_POTRF) e = launch_potrf_ws(c->block, (c->threads - 32) / 32, true, o, s, l, gs);
+            else if (op == SS_OP_POTRF) e = launch_potrf_ws(c->block, (c->threads - 32) / 32, true, o, s, l, gs,
+                                                            (c->variant & 8) != 0);
             else e = launch_syl_ws(c->block, (c->threads - 32) / 32, op == SS_OP_TRLYAP, true, o, s, l, gs,
                                    (c->variant & 8) != 0);
         } else {

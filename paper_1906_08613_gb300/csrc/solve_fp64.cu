@@ -552,7 +552,7 @@ cudaError_t launch_potrf_fp64(const Operands &o, const Sched &s, const Launch &l
 {
     const Config *c = config_get(SS_OP_POTRF, SS_MODE_FP64, l.cfg);
     if (c == nullptr) return cudaErrorInvalidValue;
-    if (c->variant == 2) return launch_potrf_ws(c->block, (c->threads - 32) / 32, false, o, s, l, st);
+    if (c->variant == 2) return launch_potrf_ws(c->block, (c->threads - 32) / 32, false, o, s, l, st, false);
     if (c->variant == 3 && c->block == 64 && c->threads == 128) {
         constexpr size_t rl = (size_t)64 * 65 * sizeof(double);
         const size_t smem = rl > smem_bytes<16>() ? rl : smem_bytes<16>();

@@ -1426,15 +1426,16 @@ cudaError_t launch_chol_df(const Operands &o, const Sched &s, const Launch &l, c
 }
 
 cudaError_t launch_potrf_ws(int block, int nu, bool df, const Operands &o, const Sched &s, const Launch &l,
-                            cudaStream_t st)
+                            cudaStream_t st, bool few)
 {
-#define CWS_CASE(BB, NN, MB)                                                                              \
-    if (block == BB && nu == NN)                                                                          \
+#define CWS_CASE(BB, NN, MB, FEW)                                                                         \
+    if (block == BB && nu == NN && few == FEW)                                                            \
         return df ? launch_chol_df<BB, NN, MB>(o, s, l, st)                                               \
                   : launch_ws(chol_ws_kernel<BB, NN, MB, false, false>, 32 * NN + 32, ws_smem_bytes<BB>(), l.batch, \
                               st, o, s, l.group);
-    CWS_CASE(16, 2, 8)
-    CWS_CASE(16, 4, 7)
+    CWS_CASE(16, 2, 8, false)
+    CWS_CASE(16, 4, 7, false)
+    CWS_CASE(16, 4, 2, true)     // few instances per SM: all of the registers
 #undef CWS_CASE
     return cudaErrorInvalidValue;
 }

@@ -127,7 +127,7 @@ cudaError_t launch_syl_ws(int block, int nu, bool lyap, bool df, const Operands 
 // Cholesky with warp-specialised CTAs (block B, nu update warps plus one
 // diagonal warp); df: double-float update warps (SS_MODE_DF).
 cudaError_t launch_potrf_ws(int block, int nu, bool df, const Operands &o, const Sched &s, const Launch &l,
-                            cudaStream_t st);
+                            cudaStream_t st, bool few);
 
 // Solve stage of the SPD solve (R^T Y = B, R X = Y) over the valid instances
 // of a binning pass, on queue head `group`; df: double-float block updates

@@ -112,13 +112,13 @@ def test_df_mode_host_side(lib):
     text = open(HEADER).read()
     assert int(re.search(r"#define SS_MODE_DF\s+(\d+)", text).group(1)) == ss.MODE_DF
     assert ss.MODES["df"] == ss.MODE_DF
-    for op, want in ((ss.OP_POTRF, 2), (ss.OP_TRSYL, 6), (ss.OP_TRLYAP, 6)):
+    for op, want in ((ss.OP_POTRF, 3), (ss.OP_TRSYL, 6), (ss.OP_TRLYAP, 6)):
         cnt = ss.ss_config_count(op, ss.MODE_DF)
         assert cnt == want
         # variant 4: the double-float pipeline; bit 3 (Sylvester / Lyapunov):
         # its form for one or two CTAs per SM
         assert all(ss.ss_config_describe(op, ss.MODE_DF, c)[2] & ~8 == 4 for c in range(cnt))
-        assert sum(ss.ss_config_describe(op, ss.MODE_DF, c)[2] == 12 for c in range(cnt)) == (3 if op != ss.OP_POTRF else 0)
+        assert sum(ss.ss_config_describe(op, ss.MODE_DF, c)[2] == 12 for c in range(cnt)) == (3 if op != ss.OP_POTRF else 1)
         # FP64's workspace plus 24 bytes per instance (the scale pre-pass's
         # exponents and diagonal maximum, the flag that hands an instance to
         # the rescaled pass), 256-byte aligned; for Sylvester / Lyapunov also
@@ -129,15 +129,15 @@ def test_df_mode_host_side(lib):
         want = al(1000 * 24) + (0 if op == ss.OP_POTRF else al(1000 * 8) + al(1000 * 128 * 128 * 24))
         assert extra == want
     # Argument checks of the DF forms run before any launch.
-    assert ss.potrf_upper(1, 4, 1, 1, 1, 1, 1, 1, mode=ss.MODE_DF, cfg=2, check=False) == -10
-    assert ss.posv_upper(1, 4, 4, *([1] * 11), mode=ss.MODE_DF, cfg=2, check=False) == -16
+    assert ss.potrf_upper(1, 4, 1, 1, 1, 1, 1, 1, mode=ss.MODE_DF, cfg=3, check=False) == -10
+    assert ss.posv_upper(1, 4, 4, *([1] * 11), mode=ss.MODE_DF, cfg=3, check=False) == -16
     assert ss.posv_upper(1, 4, 4, *([1] * 11), mode=ss.MODE_FP32_REFINED, check=False) == -15
     ss.ss_set_auto_table(ss.OP_TRSYL, [ss.MODE_DF, ss.MODE_FP64], [2, 0])
     ss.ss_set_auto_table(ss.OP_POTRF, [ss.MODE_DF], [1])
     ss.ss_set_auto_table(ss.OP_TRSYL, [], [])
     ss.ss_set_auto_table(ss.OP_POTRF, [], [])
     with pytest.raises(ss.SmallSolveError):
-        ss.ss_set_auto_table(ss.OP_POTRF, [ss.MODE_DF], [2])
+        ss.ss_set_auto_table(ss.OP_POTRF, [ss.MODE_DF], [3])
     with pytest.raises(ss.SmallSolveError):
         ss.ss_set_config_table(ss.OP_TRLYAP, ss.MODE_DF, [6])
 

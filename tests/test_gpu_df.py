@@ -176,7 +176,7 @@ def test_df_error_against_fp64_on_the_same_batch():
 
 # ------------------------------------------------------------------ Cholesky
 
-@pytest.mark.parametrize("cfg", [0, 1])
+@pytest.mark.parametrize("cfg", [0, 1, 2])
 def test_df_potrf_every_config_edge_sizes(cfg):
     n = np.array(EDGE_SIZES, dtype=np.int32)
     pk = inputs.make_batch("potrf", n, seed=120 + cfg)
@@ -187,7 +187,7 @@ def test_df_potrf_every_config_edge_sizes(cfg):
     assert errs.max() <= DF_TOL, f"max rel err {errs.max():.3e}"
 
 
-@pytest.mark.parametrize("cfg", [0, 1])
+@pytest.mark.parametrize("cfg", [0, 1, 2])
 def test_df_potrf_queue_in_place_and_failures(cfg):
     n = inputs.sizes_uniform(1100, 1, 160, seed=121)
     pk = inputs.make_batch("potrf", n, seed=122)
