@@ -327,7 +327,11 @@ __device__ void wresidual(int n, const double *L, long ldl, const double *U, lon
 //     the block (Lyapunov: one operand buffer, read with its two K halves
 //     swapped for B).
 // The operand buffers overlay the warps' tiles (idle while the MMAs run).
-constexpr int TC_MAXN = 128, TC_THREADS = 128;
+// The kernel runs one CTA per SM (TMEM); it has TC_WARPS warps so that the
+// double-float residual and the other CTA-wide phases fill the SM, while the
+// TMEM traffic and the block chains stay on warps 0..3 (warp w reaches lane
+// quarter w % 4 only).
+constexpr int TC_MAXN = 128, TC_WARPS = 12, TC_THREADS = 32 * TC_WARPS;
 
 // The block (I, J) of the chain of block column K, by the warp owning lanes
 // 32 I .. 32 I + 31.
@@ -436,7 +440,7 @@ __device__ bool tsolve(int n, const float *Lf, const float *Uf, const float *R, 
     unsigned char *za = reinterpret_cast<unsigned char *>(smem);
     unsigned char *zb = za + (size_t)TC_MAXN * KT * tc::KindTraits<KIND>::ES;
     const int nb = (n + BW - 1) / BW, nr = (n + 15) & ~15;
-    {
+    if (warp < 4) {
         const int i = 32 * warp + lane;
         for (int cc = 0; cc < nr; cc += 16) {
             float v[16];
@@ -623,7 +627,7 @@ __global__ void __launch_bounds__(TC_THREADS) warp_tc_kernel(Operands o, Sched s
             continue;
         }
         float *W = static_cast<float *>(s.scratch) + off;
-        if (!warp_instance<4, LYAP, KIND>(n, o.A[b], o.lda[b], LYAP ? nullptr : o.U[b], LYAP ? 0 : o.ldu[b],
+        if (!warp_instance<TC_WARPS, LYAP, KIND>(n, o.A[b], o.lda[b], LYAP ? nullptr : o.U[b], LYAP ? 0 : o.ldu[b],
                                           o.C[b], o.ldc[b], o.X[b], o.ldx[b], o.info + b, W, raw != 0, smf, &ts))
             break;
     }
@@ -637,17 +641,17 @@ template <bool LYAP, int P>
 cudaError_t launch_warp_tc(const Operands &o, const Sched &s, const Launch &l, cudaStream_t st, int raw)
 {
     auto kern = warp_tc_kernel<LYAP, P>;
-    const size_t smem = smem_bytes(4) + 1024;
+    const size_t smem = smem_bytes(TC_WARPS) + 1024;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TC_THREADS, smem);
     if (e != cudaSuccess) return e;
     per_sm = per_sm > 4 ? 4 : (per_sm < 1 ? 1 : per_sm);   // 4 x 128 TMEM columns per SM
     long grid = (long)per_sm * sm_count();
     if (grid > l.batch) grid = l.batch;
     if (grid < 1) grid = 1;
-    kern<<<(int)grid, 128, smem, st>>>(o, s, l.group, raw);
+    kern<<<(int)grid, TC_THREADS, smem, st>>>(o, s, l.group, raw);
     return cudaGetLastError();
 }
 
