@@ -71,8 +71,9 @@
  * FP64 magnitude is thus solved to the same accuracy; entries more than
  * 2^126 below the largest of their operand count as zero (a perturbation
  * below 2^-126 of the operand's norm).  In SS_MODE_DF the largest entries of
- * a Sylvester / Lyapunov instance come from a pre-pass over the batch (one
- * launch more, reading the operands once); a Cholesky A is checked as the
+ * a Sylvester / Lyapunov instance are found by the solve's first pass over
+ * it (which also splits L and U) and an instance outside the band is solved
+ * by a second, rescaled launch; a Cholesky A is checked as the
  * factorisation reads it, and an instance outside the band is factored again
  * rescaled (as is, after a scan, every instance factored in place, X == A).
  * A Sylvester / Lyapunov instance whose rescaled solution reaches 2^60 (a

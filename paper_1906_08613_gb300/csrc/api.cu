@@ -328,24 +328,16 @@ int run(int op, int batch, int max_n, const Operands &o, int mode, int cfg, void
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = launch_binning(batch, max_n, o.n, o.info, s, group_of_bin, ngroups, per, st, o.m, max_m);
     if (e != cudaSuccess) return SS_ERR_CUDA;
-    // A double-float group is the unscaled pipeline and the rescaled pass; for
-    // Sylvester / Lyapunov also the range fix-up pass, and the call gets the
-    // scale pre-pass.
+    // A double-float group is the zero-shift pipeline and the rescaled pass;
+    // for Sylvester / Lyapunov also the range fix-up pass.
     int nlaunch = 1 + ngroups;
-    bool any_df = false;
     for (int g = 0; g < ngroups; ++g) {
         if (group_mode[g] == SS_MODE_DF) {
             if (s.dfs == nullptr) return SS_ERR_CUDA;
-            any_df = true;
             nlaunch += op != SS_OP_POTRF ? 2 : 1;
         } else if (group_mode[g] != SS_MODE_FP64) {
             nlaunch += mixed_launches(op, group_mode[g], group_cfg[g]) - 1;
         }
-    }
-    if (any_df && op != SS_OP_POTRF) {
-        e = launch_df_scale(op, batch, o, s, st);
-        if (e != cudaSuccess) return SS_ERR_CUDA;
-        ++nlaunch;
     }
     g_launches.fetch_add(nlaunch, std::memory_order_relaxed);
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;

@@ -154,97 +154,7 @@ bin_kernel(int batch, int max_key, const int *d_n, const int *d_m, int max_n_in,
     }
 }
 
-// Scale pre-pass of the double-float Sylvester / Lyapunov pipelines (see
-// DfScale).  CTA c takes the instances at positions c, c + grid, ... of the
-// binning pass's longest-first order; its warps read the exponents of the
-// triangles the solve reads (the high word of each FP64 value: the same memory
-// sectors at half the registers of the whole value), warp w the columns
-// 2w, 2w + 1, 2w + 8, ..., lanes over rows, two columns per round trip to
-// memory, and the diagonal entries.  Reading each instance once more costs a
-// few per cent of a solve; done inside the solve it cost more, since every
-// solve CTA then waited for its own loads before it could start.  The pass is
-// bound by the latency of those loads, so it keeps the registers low enough
-// for 12 CTAs per SM.
-constexpr int SCALE_WARPS = 4;
-constexpr int SCALE_CPT = 2;      // columns per round trip
-
-// Biased exponent of an FP64 value from its high word; Inf / NaN -> 0.
-__device__ __forceinline__ int exp_of_hi(unsigned h)
-{
-    const int e = (int)((h >> 20) & 0x7FF);
-    return e == 0x7FF ? 0 : e;
-}
-
-__global__ void __launch_bounds__(32 * SCALE_WARPS, 12) df_scale_kernel(bool lyap, const int *meta, const int *perm,
-                                                                        Operands o, DfInst *dfs)
-{
-    __shared__ int s_buf[2 * SCALE_WARPS];
-    __shared__ double s_md[SCALE_WARPS];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int count = meta[META_COUNT];
-    for (int pos = blockIdx.x; pos < count; pos += gridDim.x) {
-        const int b = perm[pos];
-        const int n = o.n[b], m = o.m != nullptr ? o.m[b] : n;
-        const double *A = o.A[b], *U = lyap ? nullptr : o.U[b], *C = o.C[b];
-        const long lda = o.lda[b], ldu = lyap ? 0 : o.ldu[b], ldc = o.ldc[b];
-        const int cols = max(m, n);
-        const unsigned *hA = reinterpret_cast<const unsigned *>(A) + 1;   // high words
-        const unsigned *hU = reinterpret_cast<const unsigned *>(U) + 1;
-        const unsigned *hC = reinterpret_cast<const unsigned *>(C) + 1;
-        int m0 = 0, m1 = 0;
-        for (int j0 = w * SCALE_CPT; j0 < cols; j0 += SCALE_WARPS * SCALE_CPT) {
-            for (int r0 = 0; r0 < cols; r0 += 128) {
-                unsigned va[SCALE_CPT][4], vu[SCALE_CPT][4], vc[SCALE_CPT][4];
-#pragma unroll
-                for (int jj = 0; jj < SCALE_CPT; ++jj) {
-                    const int j = j0 + jj;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int i = r0 + lane + 32 * q;
-                        const bool ka = i >= j && i < m && j < m;                     // L lower, m x m
-                        const bool ku = !lyap && i <= j && j < n;                     // U upper, n x n
-                        const bool kc = i < m && j < n && (!lyap || i >= j);          // C m x n (S lower)
-                        va[jj][q] = ka ? __ldg(hA + 2 * (i + (long)j * lda)) : 0u;
-                        vu[jj][q] = ku ? __ldg(hU + 2 * (i + (long)j * ldu)) : 0u;
-                        vc[jj][q] = kc ? __ldg(hC + 2 * (i + (long)j * ldc)) : 0u;
-                    }
-                }
-#pragma unroll
-                for (int jj = 0; jj < SCALE_CPT; ++jj)
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        m0 = max(m0, max(exp_of_hi(va[jj][q]), exp_of_hi(vu[jj][q])));
-                        m1 = max(m1, exp_of_hi(vc[jj][q]));
-                    }
-            }
-        }
-        // Diagonal magnitudes of L (and U): the divisor threshold.
-        double md = 0.0;                                 // fmax drops NaN, as the FP64 solves' maximum does
-        for (int d = threadIdx.x; d < m; d += 32 * SCALE_WARPS) md = fmax(md, fabs(A[d + (long)d * lda]));
-        if (!lyap)
-            for (int d = threadIdx.x; d < n; d += 32 * SCALE_WARPS) md = fmax(md, fabs(U[d + (long)d * ldu]));
-        for (int k = 16; k > 0; k >>= 1) md = fmax(md, __shfl_xor_sync(0xffffffffu, md, k));
-        if (lane == 0) s_md[w] = md;
-        cta_max2(m0, m1, s_buf);                         // also orders s_md
-        if (threadIdx.x == 0) {
-            double mdd = 0.0;
-            for (int k = 0; k < SCALE_WARPS; ++k) mdd = fmax(mdd, s_md[k]);
-            dfs[b] = DfInst{m0, m1, 0, 0, (unsigned long long)__double_as_longlong(mdd)};
-        }
-    }
-}
-
 }  // namespace
-
-cudaError_t launch_df_scale(int op, int batch, const Operands &o, const Sched &s, cudaStream_t st)
-{
-    int grid = 12 * sm_count();
-    if (grid > batch) grid = batch;
-    if (grid < 1) grid = 1;
-    df_scale_kernel<<<grid, 32 * SCALE_WARPS, 0, st>>>(op == SS_OP_TRLYAP, s.meta, s.perm, o,
-                                                        const_cast<DfInst *>(s.dfs));
-    return cudaGetLastError();
-}
 
 cudaError_t launch_binning(int batch, int max_n, const int *d_n, int *d_info, const Sched &s,
                            const int *group_of_bin, int ngroups, long long scratch_per_n2,

@@ -677,10 +677,12 @@ constexpr size_t ws_smem_bytes() { return (size_t)WsTile<B, DF>::N * WsTile<B, D
 // NaN), in which case X is not reliable and the caller solves the instance
 // again in FP64; else 0.  The FP64 form always returns 0.
 //
-// DF reads the divisor threshold and, with SC, the rescaling shifts from the
-// scale pre-pass (di).  Without SC the shifts are the constant zero of data
-// in DfScale's band, which keeps the pipeline's registers as without
-// rescaling.
+// DF without SC finds, in its first pass over the instance (the one that
+// splits L and U), the largest exponents and diagonal magnitudes: data in
+// DfScale's band is solved with the constant zero shifts, which keeps the
+// pipeline's registers as without rescaling; other data returns 4 after
+// writing its record (di) for the SC pass, which reads the shifts and the
+// divisor threshold from there.
 //
 // PD = 2 (configurations for one or two CTAs per SM, where no other CTA
 // hides a global load): the update warps load the operands of step s + 2
@@ -691,7 +693,7 @@ constexpr size_t ws_smem_bytes() { return (size_t)WsTile<B, DF>::N * WsTile<B, D
 template <int B, int NU, bool LYAP, bool DF, bool SC = false, int PD = 1>
 __device__ int syl_ws_instance(int m, int n, const double *L, long ldl, const double *U, long ldu,
                                const double *C, long ldc, double *X, long ldx, int *info, double *sm,
-                               const DfInst *di, float2 *dfw = nullptr)
+                               DfInst *di, float2 *dfw = nullptr)
 {
     constexpr int LD = WsTile<B, DF>::LD, SZ = WsTile<B, DF>::SZ;
     constexpr int TU = 32 * NU, TALL = TU + 32;
@@ -710,33 +712,77 @@ __device__ int syl_ws_instance(int m, int n, const double *L, long ldl, const do
     double delta;
     DfScale sc{0, 0, 0};
     if constexpr (DF) {
-        const DfInst d = *di;
-        if constexpr (SC) sc = DfScale::sylvester(d.eo, d.ec);
-        delta = divisor_delta(max(m, n), __longlong_as_double((long long)d.maxdiag));
         if (threadIdx.x == 0) {
             *s_bad = 0;
             *s_rng = 0;
         }
-        // L (strict lower triangle) and U (strict upper) split once, scaled;
-        // the diagonal blocks' operands are prepared per block as before.
+        if constexpr (SC) {
+            const DfInst d = *di;
+            sc = DfScale::sylvester(d.eo, d.ec);
+            delta = divisor_delta(max(m, n), __longlong_as_double((long long)d.maxdiag));
+        }
+        // One pass over L and U: split the strict triangles once (scaled;
+        // the diagonal blocks' operands are prepared per block as before)
+        // and, in the zero-shift pass, the largest exponents and diagonal
+        // magnitudes that decide whether the instance needs rescaling
+        // (Inf / NaN exponents are left to the range check, as in DfScale).
+        int eo = 0, ec = 0;
+        double md = 0.0;                                 // fmax drops NaN, as the FP64 solves' maximum does
         for (long e = threadIdx.x; e < (long)m * m; e += blockDim.x) {
             const int r = (int)(e % m), c = (int)(e / m);
-            if (r > c) {
-                float2 v;
-                split_df_s(L[r + (long)c * ldl], sc.op, v.x, v.y);
-                dfw[e] = v;
+            if (r >= c) {
+                const double x = L[r + (long)c * ldl];
+                if constexpr (!SC) {
+                    const int ex = exp_bits(x);
+                    eo = max(eo, ex == 0x7FF ? 0 : ex);
+                    if (r == c) md = fmax(md, fabs(x));
+                }
+                if (r > c) {
+                    float2 v;
+                    split_df_s(x, sc.op, v.x, v.y);
+                    dfw[e] = v;
+                }
             }
         }
         if (!LYAP) {
             float2 *Uf = dfw + (long)m * m;
             for (long e = threadIdx.x; e < (long)n * n; e += blockDim.x) {
                 const int r = (int)(e % n), c = (int)(e / n);
-                if (r < c) {
-                    float2 v;
-                    split_df_s(U[r + (long)c * ldu], sc.op, v.x, v.y);
-                    Uf[e] = v;
+                if (r <= c) {
+                    const double x = U[r + (long)c * ldu];
+                    if constexpr (!SC) {
+                        const int ex = exp_bits(x);
+                        eo = max(eo, ex == 0x7FF ? 0 : ex);
+                        if (r == c) md = fmax(md, fabs(x));
+                    }
+                    if (r < c) {
+                        float2 v;
+                        split_df_s(x, sc.op, v.x, v.y);
+                        Uf[e] = v;
+                    }
                 }
             }
+        }
+        if constexpr (!SC) {
+            const unsigned *hC = reinterpret_cast<const unsigned *>(C) + 1;   // high words
+            for (long e = threadIdx.x; e < (long)m * n; e += blockDim.x) {
+                const int r = (int)(e % m), c = (int)(e / m);
+                if (LYAP && r < c) continue;                 // S: lower triangle
+                const int ex = (int)((hC[2 * (r + (long)c * ldc)] >> 20) & 0x7FFu);
+                ec = max(ec, ex == 0x7FF ? 0 : ex);
+            }
+            // CTA maxima: the exponents through s_red[0 .. 2 * warps) as ints,
+            // the warps' md at s_red + 12; cta_max2's barriers also order the
+            // split copies before the update warps read them.
+            for (int k = 16; k > 0; k >>= 1) md = fmax(md, __shfl_xor_sync(0xffffffffu, md, k));
+            if ((threadIdx.x & 31) == 0) s_red[12 + (threadIdx.x >> 5)] = md;
+            cta_max2(eo, ec, reinterpret_cast<int *>(s_red));
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k) md = fmax(md, s_red[12 + k]);
+            if (!DfScale::sylvester(eo, ec).zero()) {
+                if (threadIdx.x == 0) *di = DfInst{eo, ec, 1, 0, (unsigned long long)__double_as_longlong(md)};
+                return 4;                                // to the rescaled pass (the same on every thread)
+            }
+            delta = divisor_delta(max(m, n), md);
         }
         __syncthreads();
     } else {
@@ -1258,9 +1304,9 @@ __device__ __forceinline__ bool next_instance(const Sched &s, int group, int *s_
 // MINB: CTAs per SM the register allocation must allow (the two roles share
 // one register budget, set by the larger of them).
 // DF without SC: the persistent queue over the group, solving with zero
-// shifts the instances whose data the scale pre-pass found in DfScale's
-// band; the others are left to the SC pass (DfInst::pend and the group's
-// META_SCL flag).  DF with SC: only those instances, solved with their
+// shifts the instances whose data lies in DfScale's band (found by the
+// solve's first pass); the others are left to the SC pass (DfInst::pend and
+// the group's META_SCL flag).  DF with SC: only those instances, solved with their
 // shifts, from a second queue over the group's positions (longest first, as
 // the first); it returns at once when the group's flag is clear.
 template <int B, int NU, bool LYAP, int MINB, bool DF, bool SC>
@@ -1281,21 +1327,18 @@ __global__ void __launch_bounds__(32 * NU + 32, MINB) syl_ws_kernel(Operands o, 
             }
             dfw = reinterpret_cast<float2 *>(static_cast<float *>(s.scratch) + s.scr[w]);
         }
-        if constexpr (DF && !SC) {
-            const DfInst d = s.dfs[b];                        // the same on every thread
-            if (!DfScale::sylvester(d.eo, d.ec).zero()) {
-                if (threadIdx.x == 0) {
-                    const_cast<DfInst *>(s.dfs)[b].pend = 1;
-                    s.meta[META_SCL + group] = 1;
-                }
-                return;
-            }
-        }
         const double *U = LYAP ? nullptr : o.U[b];
         const int ldu = LYAP ? 0 : o.ldu[b];
         const int st = syl_ws_instance<B, NU, LYAP, DF, SC, MINB <= 2 ? 2 : 1>(m, n, o.A[b], o.lda[b], U, ldu, o.C[b],
                                                                               o.ldc[b], o.X[b], o.ldx[b], o.info + b,
-                                                                              sm, DF ? s.dfs + b : nullptr, dfw);
+                                                                              sm, DF ? const_cast<DfInst *>(s.dfs) + b : nullptr,
+                                                                              dfw);
+        // Zero-shift pass: the instance's data is outside DfScale's band; its
+        // record (written by the instance) hands it to the rescaled pass.
+        if (DF && !SC && st == 4) {
+            if (threadIdx.x == 0) s.meta[META_SCL + group] = 1;
+            return;
+        }
         // Out of the double-float range: syl_ws_fixup_kernel, launched last,
         // solves the instance again in FP64 (unless X overwrote C).
         if (DF && st != 0 && threadIdx.x == 0) {

@@ -51,9 +51,10 @@ constexpr int META_INTS = 144;
 constexpr int NUM_BINS = SS_NUM_BINS;   // bin(n) = ceil(log2(max(n,1))), n <= 4096
 
 // Per-instance state of the double-float pipelines.  Sylvester / Lyapunov:
-// the scale pre-pass writes the largest biased FP64 exponents of the
-// operator (L and U) and of the right-hand side, and the largest diagonal
-// magnitude of L and U (the singular-divisor threshold).  pend: set by the
+// for an instance out of DfScale's band, the zero-shift pass writes the
+// largest biased FP64 exponents of the operator (L and U) and of the
+// right-hand side, and the largest diagonal magnitude of L and U (the
+// singular-divisor threshold), for the rescaled pass.  pend: set by the
 // unscaled pipeline when the instance needs the rescaled one (Cholesky:
 // found out of DfScale's band while the solve read A).  The binning pre-pass
 // zeroes every entry.
@@ -96,11 +97,6 @@ void carve_workspace(void *d_work, size_t work_bytes, int op, int batch, int max
 cudaError_t launch_binning(int batch, int max_n, const int *d_n, int *d_info, const Sched &s,
                            const int *group_of_bin, int ngroups, long long scratch_per_n2,
                            cudaStream_t st, const int *d_m = nullptr, int max_m = 0);
-
-// Scale pre-pass of the double-float Sylvester / Lyapunov pipelines: s.dfs[b]
-// for every instance in the binning pass's order (one CTA per instance at a
-// time, all in parallel).  Runs after the binning pre-pass.
-cudaError_t launch_df_scale(int op, int batch, const Operands &o, const Sched &s, cudaStream_t st);
 
 // Configuration tables.
 struct Config {
