@@ -54,10 +54,11 @@
  * posv_upper (factor stage): T = A - sum X^T X in double-float; the diagonal
  * blocks (square roots, pivots, panel solves) stay FP64; posv_upper's
  * triangular solves likewise.  No refinement.  Workspace: FP64's plus 24
- * bytes per instance, and for trsyl_lu, trlyap_l and trsyl_rect the
- * double-float copies of L, U and X that the update warps stage from (split
- * once per instance; 24 bytes per max_n^2 per instance in the
- * ss_workspace_size bound); an instance without room gets SS_INFO_NO_WORK.
+ * bytes per instance, and the double-float copies the update warps stage
+ * from (split once per instance): for trsyl_lu, trlyap_l and trsyl_rect of
+ * L, U and X (24 bytes per max_n^2 per instance in the ss_workspace_size
+ * bound), for potrf_upper and posv_upper of X (8 bytes per max_n^2); an
+ * instance without room gets SS_INFO_NO_WORK.
  * Accuracy is that of FP64 up to the split's 2^-47 relative representation
  * error per operand.
  *

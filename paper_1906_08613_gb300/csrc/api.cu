@@ -203,9 +203,10 @@ int sm_count()
     return cache[dev];
 }
 
-// SS_MODE_DF Sylvester / Lyapunov: the pre-split double-float copies of L,
-// U and X (3 pairs per n^2, the bound of m^2 + n^2 + m n for max(m, n) = n).
-static long long df_scratch_per_n2(int op) { return op != SS_OP_POTRF ? 6 : 0; }
+// SS_MODE_DF scratch: Sylvester / Lyapunov the pre-split double-float copies
+// of L, U and X (3 pairs per n^2, the bound of m^2 + n^2 + m n for
+// max(m, n) = n); Cholesky X as pairs (1 pair per n^2).
+static long long df_scratch_per_n2(int op) { return op != SS_OP_POTRF ? 6 : 2; }
 
 static long long scratch_per_n2(int op, int mode)
 {

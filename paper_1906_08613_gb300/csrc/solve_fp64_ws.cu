@@ -389,6 +389,17 @@ struct PrefetchF {
             else    tB[r + c * LDT] = b[q];
         }
     }
+    // Both tiles in natural layout (the Cholesky pipeline's X_KI^T X_KJ).
+    template <int LDT>
+    __device__ __forceinline__ void store_nat(float2 *tA, float2 *tB, bool has_a, int ut) const
+    {
+#pragma unroll
+        for (int q = 0; q < PE; ++q) {
+            const int e = ut + TU * q, r = e % B, c = e / B;
+            if (has_a) tA[r + c * LDT] = a[q];
+            tB[r + c * LDT] = b[q];
+        }
+    }
     // The last phase's tile, natural layout.
     template <int LDT>
     __device__ __forceinline__ void store_b(float2 *tB, int ut) const
@@ -1116,9 +1127,13 @@ __device__ void warp_trsm_ut(const double *sD, const double *sR, double *sT, int
 //
 // SC, the band check without SC and the status (valid on thread 0): as for
 // syl_ws_instance (the check covers every entry of A, each staged once).
+//
+// DF: dfx, the instance's scratch, receives X (scaled) as double-float pairs
+// (ld n) as the diagonal warp finishes each block; the update warps stage
+// X_KI and X_KJ from there without splitting.
 template <int B, int NU, bool DF, bool SC = false>
 __device__ int chol_ws_instance(int n, const double *A, long lda, double *X, long ldx, int *info, double *sm,
-                                const DfScale &scin)
+                                const DfScale &scin, float2 *dfx = nullptr)
 {
     constexpr bool VAL = DF && !SC;
     constexpr int W = DfScale::BAND_CHOL;
@@ -1166,8 +1181,20 @@ __device__ int chol_ws_instance(int n, const double *A, long lda, double *X, lon
                     // diagonal block: upper part; after a failing pivot only
                     // the rows above it are final.
                     if (I < J || (r <= c && (!f || r < f - 1))) {
-                        if constexpr (DF) X[(i0 + r) + (long)(j0 + c) * ldx] = sT[r + c * LD] * pow2d(-sc.x);
-                        else X[(i0 + r) + (long)(j0 + c) * ldx] = sT[r + c * LD];
+                        if constexpr (DF) {
+                            const double v = sT[r + c * LD];
+                            X[(i0 + r) + (long)(j0 + c) * ldx] = v * pow2d(-sc.x);
+                            // Pairs (scaled) for the update warps: only block rows
+                            // that later blocks stage (K <= I - 2 in the bulk steps,
+                            // I - 1 <= J - 2 in the last phase), i.e. I <= nb - 3.
+                            if (I + 3 <= nb) {
+                                float2 p;
+                                split_df_s(v, 0, p.x, p.y);
+                                dfx[(i0 + r) + (long)(j0 + c) * n] = p;
+                            }
+                        } else {
+                            X[(i0 + r) + (long)(j0 + c) * ldx] = sT[r + c * LD];
+                        }
                     }
                 }
                 named_arrive(kBarX, TALL);                 // X of block t is final
@@ -1185,7 +1212,6 @@ __device__ int chol_ws_instance(int n, const double *A, long lda, double *X, lon
         constexpr int E = B * B / TU;
         const int ut = threadIdx.x - 32;
         OutMap<B, TU> om;
-        Prefetch<B, TU> pf;
         using Acc = typename std::conditional<DF, float, double>::type;
         unsigned chk = 0;                                  // band bits (VAL)
         int t = 0;
@@ -1201,22 +1227,39 @@ __device__ int chol_ws_instance(int n, const double *A, long lda, double *X, lon
                 const int nsteps = I > 1 ? I - 1 : 0;
                 const bool has_last = I >= 1;
                 const int nload = nsteps + (has_last && !diag ? 1 : 0);
-                auto bulk_src = [&](int K, Src &sa, Src &sb) {
-                    const int k0 = K * B;
-                    sa = Src{X + k0 + (long)i0 * ldx, ldx, B, mI, false, sc.x};   // X_KI (used transposed)
-                    sb = Src{X + k0 + (long)j0 * ldx, ldx, B, nJ, false, sc.x};   // X_KJ
-                };
-                Src sa{}, sb{};
-                if (nload > 0) {
-                    if (nsteps > 0) {
-                        bulk_src(0, sa, sb);
-                        pf.load(sa, sb, true, ut);
+                using SrcT = typename std::conditional<DF, SrcF, Src>::type;
+                using PfT = typename std::conditional<DF, PrefetchF<B, TU>, Prefetch<B, TU>>::type;
+                // Operands of step q: X_KI (used transposed) and X_KJ for K = q;
+                // q == nsteps: the last phase's X_{I-1,I}.
+                auto src = [&](int q, SrcT &sa, SrcT &sb) {
+                    if constexpr (DF) {
+                        if (q < nsteps) {
+                            sa = SrcF{dfx + q * B + (long)i0 * n, n, B, mI, false};
+                            sb = SrcF{dfx + q * B + (long)j0 * n, n, B, nJ, false};
+                        } else {
+                            sb = SrcF{dfx + (long)(I - 1) * B + (long)i0 * n, n, B, mI, false};
+                        }
                     } else {
-                        sb = Src{X + (long)(I - 1) * B + (long)i0 * ldx, ldx, B, mI, false, sc.x};   // X_{I-1,I}
-                        pf.load(sa, sb, false, ut);
+                        if (q < nsteps) {
+                            const int k0 = q * B;
+                            sa = Src{X + k0 + (long)i0 * ldx, ldx, B, mI, false, sc.x};
+                            sb = Src{X + k0 + (long)j0 * ldx, ldx, B, nJ, false, sc.x};
+                        } else {
+                            sb = Src{X + (long)(I - 1) * B + (long)i0 * ldx, ldx, B, mI, false, sc.x};
+                        }
                     }
-                    if constexpr (DF) pf.template store_df<LD>(df2(sA0), df2(sB0), nsteps > 0, ut, sa.sh, sb.sh);
-                    else pf.store(sA0, sB0, nsteps > 0, ut);
+                };
+                auto stage = [&](const PfT &p, int q) {           // step q's tiles into buffer q & 1
+                    const int bf = q & 1;
+                    if constexpr (DF) p.template store_nat<LD>(df2(sA0 + bf * SZ), df2(sB0 + bf * SZ), q < nsteps, ut);
+                    else p.store(sA0 + bf * SZ, sB0 + bf * SZ, q < nsteps, ut);
+                };
+                PfT pf;
+                SrcT sa{}, sb{};
+                if (nload > 0) {
+                    src(0, sa, sb);
+                    pf.load(sa, sb, nsteps > 0, ut);
+                    stage(pf, 0);
                     named_sync(kBarUpd, TU);
                 }
                 // FP64: even / odd terms; DF: hi / lo of one double-float sum.
@@ -1232,23 +1275,16 @@ __device__ int chol_ws_instance(int n, const double *A, long lda, double *X, lon
                         if constexpr (VAL) chk |= band_bits<W>(a, BAND_OP);
                     }
                 }
-                for (int s = 0; s < nsteps; ++s) {
-                    const int buf = s & 1;
-                    const bool more = s + 1 < nload, next_bulk = s + 1 < nsteps;
+                for (int q = 0; q < nsteps; ++q) {
+                    const int buf = q & 1;
+                    const bool more = q + 1 < nload;
                     if (more) {
-                        if (next_bulk) bulk_src(s + 1, sa, sb);
-                        else sb = Src{X + (long)(I - 1) * B + (long)i0 * ldx, ldx, B, mI, false, sc.x};
-                        pf.load(sa, sb, next_bulk, ut);
+                        src(q + 1, sa, sb);
+                        pf.load(sa, sb, q + 1 < nsteps, ut);
                     }
-                    if constexpr (DF) {
-                        upd_df_ta<B, TU, LD>(ae, ao, om, df2(sA0 + buf * SZ), df2(sB0 + buf * SZ));
-                        if (more)
-                            pf.template store_df<LD>(df2(sA0 + (buf ^ 1) * SZ), df2(sB0 + (buf ^ 1) * SZ), next_bulk, ut,
-                                                     sa.sh, sb.sh);
-                    } else {
-                        upd_fma_ta<B, TU>(ae, ao, om, sA0 + buf * SZ, sB0 + buf * SZ);
-                        if (more) pf.store(sA0 + (buf ^ 1) * SZ, sB0 + (buf ^ 1) * SZ, next_bulk, ut);
-                    }
+                    if constexpr (DF) upd_df_ta<B, TU, LD>(ae, ao, om, df2(sA0 + buf * SZ), df2(sB0 + buf * SZ));
+                    else upd_fma_ta<B, TU>(ae, ao, om, sA0 + buf * SZ, sB0 + buf * SZ);
+                    if (more) stage(pf, q + 1);
                     named_sync(kBarUpd, TU);
                 }
                 if (t > 0) named_sync(kBarX, TALL);        // X of block t-1 is final
@@ -1427,9 +1463,18 @@ __global__ void __launch_bounds__(32 * NU + 32, MINB) chol_ws_kernel(Operands o,
             s.meta[META_SCL + group] = 1;
         }
     };
-    auto one = [&](int b) {
+    auto one = [&](int b, int w) {
         const int n = o.n[b];
         if (n == 0) { if (threadIdx.x == 0) o.info[b] = 0; return; }
+        // DF: the instance's share of the workspace scratch (X as pairs).
+        float2 *dfx = nullptr;
+        if constexpr (DF) {
+            if (s.scr == nullptr || s.scratch == nullptr || s.scr[w] + 2ll * n * n > s.scratch_elems) {
+                if (threadIdx.x == 0) o.info[b] = SS_INFO_NO_WORK;
+                return;
+            }
+            dfx = reinterpret_cast<float2 *>(static_cast<float *>(s.scratch) + s.scr[w]);
+        }
         DfScale sc{0, 0, 0};
         if constexpr (DF && !SC) {
             if (o.X[b] == o.A[b]) { pend(b); return; }           // in place: scanned first by the SC pass
@@ -1441,17 +1486,17 @@ __global__ void __launch_bounds__(32 * NU + 32, MINB) chol_ws_kernel(Operands o,
             cta_max2(ea, unused, s_scan);
             sc = DfScale::cholesky(ea);
         }
-        const int st = chol_ws_instance<B, NU, DF, SC>(n, o.A[b], o.lda[b], o.X[b], o.ldx[b], o.info + b, sm, sc);
+        const int st = chol_ws_instance<B, NU, DF, SC>(n, o.A[b], o.lda[b], o.X[b], o.ldx[b], o.info + b, sm, sc, dfx);
         if (DF && (st & 2)) pend(b);                            // out of the band: solve again rescaled
     };
-    int b;
+    int b, w = 0;
     claim_init(&s_slot);
     if constexpr (SC) {
         if (s.meta[META_SCL + group] == 0) return;              // the same on every thread
-        while (next_instance(s, group, &s_slot, b, META_SCL_HEAD))
-            if (s.dfs[b].pend != 0) one(b);                     // the same on every thread
+        while (next_instance(s, group, &s_slot, b, META_SCL_HEAD, &w))
+            if (s.dfs[b].pend != 0) one(b, w);                  // the same on every thread
     } else {
-        while (next_instance(s, group, &s_slot, b)) one(b);
+        while (next_instance(s, group, &s_slot, b, META_HEAD, &w)) one(b, w);
     }
 }
 

@@ -126,7 +126,8 @@ def test_df_mode_host_side(lib):
         # 3 pairs = 24 bytes per max_n^2 per instance).
         al = lambda x: (x + 255) // 256 * 256
         extra = ss.ss_workspace_size(op, 1000, 128, ss.MODE_DF) - ss.ss_workspace_size(op, 1000, 128, ss.MODE_FP64)
-        want = al(1000 * 24) + (0 if op == ss.OP_POTRF else al(1000 * 8) + al(1000 * 128 * 128 * 24))
+        # (Cholesky: X as pairs, 8 bytes per max_n^2 per instance).
+        want = al(1000 * 24) + al(1000 * 8) + al(1000 * 128 * 128 * (8 if op == ss.OP_POTRF else 24))
         assert extra == want
     # Argument checks of the DF forms run before any launch.
     assert ss.potrf_upper(1, 4, 1, 1, 1, 1, 1, 1, mode=ss.MODE_DF, cfg=3, check=False) == -10
