@@ -170,20 +170,38 @@ __device__ void warp_diag_solve_df(const float2 *sLU, float2 *sT, const float2 *
                 l0 = tv.y;
             }
             int t = part;
-            for (; t + split < d; t += 2 * split) {
-                const int t1 = t + split;
-                const float2 a0 = t < i ? sLU[i + t * LDT] : sT[i + (t - i) * LDT];
-                const float2 b0 = t < i ? (SYM && t < j ? sT[j + t * LDT] : sT[t + j * LDT]) : sLU[(t - i) + j * LDT];
-                const float2 a1 = t1 < i ? sLU[i + t1 * LDT] : sT[i + (t1 - i) * LDT];
-                const float2 b1 = t1 < i ? (SYM && t1 < j ? sT[j + t1 * LDT] : sT[t1 + j * LDT])
-                                         : sLU[(t1 - i) + j * LDT];
-                df_msub(h0, l0, a0.x, a0.y, b0.x, b0.y);
-                df_msub(h1, l1, a1.x, a1.y, b1.x, b1.y);
-            }
-            if (t < d) {
-                const float2 a0 = t < i ? sLU[i + t * LDT] : sT[i + (t - i) * LDT];
-                const float2 b0 = t < i ? (SYM && t < j ? sT[j + t * LDT] : sT[t + j * LDT]) : sLU[(t - i) + j * LDT];
-                df_msub(h0, l0, a0.x, a0.y, b0.x, b0.y);
+            if constexpr (!SYM) {
+                // Offsets from sT: term t reads L_it (sLU) and Y_tj (sT) for
+                // t < i, Y_i,t-i (sT) and U_t-i,j (sLU) from t = i on, that
+                // is base + t * LDT and base + t with the bases of its part.
+                const int dlu = (int)(sLU - sT);
+                const int aL = dlu + i, aU = i - i * LDT, bL = j * LDT, bU = dlu - i + j * LDT;
+                for (; t + split < d; t += 2 * split) {
+                    const int t1 = t + split;
+                    const float2 a0 = sT[(t < i ? aL : aU) + t * LDT], b0 = sT[(t < i ? bL : bU) + t];
+                    const float2 a1 = sT[(t1 < i ? aL : aU) + t1 * LDT], b1 = sT[(t1 < i ? bL : bU) + t1];
+                    df_msub(h0, l0, a0.x, a0.y, b0.x, b0.y);
+                    df_msub(h1, l1, a1.x, a1.y, b1.x, b1.y);
+                }
+                if (t < d) {
+                    const float2 a0 = sT[(t < i ? aL : aU) + t * LDT], b0 = sT[(t < i ? bL : bU) + t];
+                    df_msub(h0, l0, a0.x, a0.y, b0.x, b0.y);
+                }
+            } else {
+                for (; t + split < d; t += 2 * split) {
+                    const int t1 = t + split;
+                    const float2 a0 = t < i ? sLU[i + t * LDT] : sT[i + (t - i) * LDT];
+                    const float2 b0 = t < i ? (t < j ? sT[j + t * LDT] : sT[t + j * LDT]) : sLU[(t - i) + j * LDT];
+                    const float2 a1 = t1 < i ? sLU[i + t1 * LDT] : sT[i + (t1 - i) * LDT];
+                    const float2 b1 = t1 < i ? (t1 < j ? sT[j + t1 * LDT] : sT[t1 + j * LDT]) : sLU[(t1 - i) + j * LDT];
+                    df_msub(h0, l0, a0.x, a0.y, b0.x, b0.y);
+                    df_msub(h1, l1, a1.x, a1.y, b1.x, b1.y);
+                }
+                if (t < d) {
+                    const float2 a0 = t < i ? sLU[i + t * LDT] : sT[i + (t - i) * LDT];
+                    const float2 b0 = t < i ? (t < j ? sT[j + t * LDT] : sT[t + j * LDT]) : sLU[(t - i) + j * LDT];
+                    df_msub(h0, l0, a0.x, a0.y, b0.x, b0.y);
+                }
             }
         }
         df_add(h0, l0, h1, l1);
