@@ -846,14 +846,23 @@ __device__ int syl_ws_instance(int m, int n, const double *L, long ldl, const do
                     } else {
                         warp_diag_solve_df<B, LD, false>(dLU, dT, dR, mI, nJ, lane);
                     }
+                    // The pairs in scaled units first, for the update warps'
+                    // staging of later blocks; then "X final" (the update
+                    // warps read this block from shared memory); then X
+                    // rounded to FP64 and its range check, while the update
+                    // warps finish the next block's T.
+                    float2 *dX = dfw + (long)m * m + (long)n * n + i0 + (long)j0 * m;
+                    for (int e = lane; e < mI * nJ; e += 32) {
+                        const int r = e % mI, c = e / mI;
+                        if (!LYAP || I != J || r >= c) dX[r + (long)c * m] = dT[r + c * LD];
+                    }
+                    named_arrive(kBarX, TALL);             // X of block t is final
                     for (int e = lane; e < mI * nJ; e += 32) {
                         const int r = e % mI, c = e / mI;
                         if (!LYAP || I != J || r >= c) {
                             const float2 v = dT[r + c * LD];
                             rng |= df_out_of_range(v.x);          // every entry of X passes here once
                             X[(i0 + r) + (long)(j0 + c) * ldx] = df_to_double_s(v.x, v.y, -sc.x);
-                            // scaled units, for the update warps' staging
-                            dfw[(long)m * m + (long)n * n + (i0 + r) + (long)(j0 + c) * m] = v;
                         }
                     }
                 } else {
@@ -884,8 +893,8 @@ __device__ int syl_ws_instance(int m, int n, const double *L, long ldl, const do
                         const int r = e % mI, c = e / mI;
                         if (!LYAP || I != J || r >= c) X[(i0 + r) + (long)(j0 + c) * ldx] = sT[r + c * LD];
                     }
+                    named_arrive(kBarX, TALL);             // X of block t is final
                 }
-                named_arrive(kBarX, TALL);                 // X of block t is final
             }
         }
         // DF: the update warps set s_bad and s_rng before their last "T ready"
