@@ -23,6 +23,11 @@ Two properties are checked for square, rectangular and Lyapunov shapes:
   earlier (its copy in memory is complete before the "X final" arrival the
   update warps waited for at the end of the block before), and the last phase
   reads only the block solved just before, from shared memory.
+
+The diagonal warp's double-float wavefront is modelled the same way: its lane
+split gives every entry of every block shape all its terms exactly once, and
+the per-part base offsets of the non-symmetric form address the same
+shared-memory elements as the per-term operand selects they replace.
 """
 import numpy as np
 import pytest
@@ -165,3 +170,70 @@ def test_the_special_cases_are_needed():
     assert bulk_reads_previous(4, 4, True)           # X_{I,I-1} in the diagonal block's first sum
     assert bulk_reads_previous(4, 1, False)          # X_{I-1,0} with a single block column
     assert not bulk_reads_previous(4, 4, False)
+
+
+# ---- the diagonal warp's wavefront (warp_diag_solve_df) ----------------------
+
+def wf_step(d, m, nn, sym):
+    """Per-step constants: first row, entry count and lanes per entry (a
+    power of two: at most 32 / entries rounded down to a power of two, at most
+    the largest power of two <= d)."""
+    ilo = max((d + 1) // 2, d - nn + 1) if sym else max(0, d - nn + 1)
+    cnt = min(d, m - 1) - ilo + 1
+    by_cnt = 1 if cnt >= 32 else 32 >> (0 if cnt <= 1 else (cnt - 1).bit_length())
+    by_len = 1 << (max(d, 1).bit_length() - 1)
+    return ilo, cnt, min(by_cnt, by_len)
+
+
+@pytest.mark.parametrize("B,LDT", [(16, 18), (32, 34)])
+@pytest.mark.parametrize("sym", [False, True])
+def test_wavefront_lanes_cover_each_entry_once(B, LDT, sym):
+    for m in range(1, B + 1):
+        for nn in ([m] if sym else range(1, B + 1)):
+            seen = set()
+            for d in range(m + nn - 1):
+                ilo, cnt, split = wf_step(d, m, nn, sym)
+                assert cnt * split <= 32 and split & (split - 1) == 0
+                lg = split.bit_length() - 1
+                terms = {}
+                for lane in range(32):
+                    idx, part = lane >> lg, lane & (split - 1)
+                    if idx >= cnt:
+                        continue
+                    i = ilo + idx
+                    j = d - i
+                    assert 0 <= i < m and 0 <= j < nn and (not sym or i >= j)
+                    terms.setdefault((i, j), []).extend(range(part, d, split))
+                for e, ts in terms.items():
+                    assert sorted(ts) == list(range(d)), (m, nn, d, e)
+                    seen.add(e)
+            want = {(i, j) for i in range(m) for j in range(nn) if not sym or i >= j}
+            assert seen == want
+
+
+@pytest.mark.parametrize("B,LDT", [(16, 18), (32, 34)])
+def test_wavefront_base_offsets_match_the_operand_selects(B, LDT):
+    """Non-symmetric blocks: term t of entry (i, j) reads sLU[i + t LDT] and
+    sT[t + j LDT] for t < i, sT[i + (t - i) LDT] and sLU[(t - i) + j LDT]
+    from t = i on; the kernel forms both as offsets from sT with bases that
+    switch at t = i.  Same elements, all inside the two tiles."""
+    dlu = -3 * B * LDT                      # sLU - sT in elements (any offset)
+    for m in range(1, B + 1):
+        for nn in range(1, B + 1):
+            for d in range(m + nn - 1):
+                ilo, cnt, split = wf_step(d, m, nn, False)
+                for idx in range(cnt):
+                    i = ilo + idx
+                    j = d - i
+                    aL, aU, bL, bU = dlu + i, i - i * LDT, j * LDT, dlu - i + j * LDT
+                    for t in range(d):
+                        a = (aL if t < i else aU) + t * LDT
+                        b = (bL if t < i else bU) + t
+                        ea = dlu + i + t * LDT if t < i else i + (t - i) * LDT
+                        eb = t + j * LDT if t < i else dlu + (t - i) + j * LDT
+                        assert (a, b) == (ea, eb)
+                        for off in (a, b):
+                            base = dlu if dlu <= off < dlu + B * LDT else 0
+                            assert 0 <= off - base < B * LDT
+                            r, c = (off - base) % LDT, (off - base) // LDT
+                            assert r < B and c < B
