@@ -145,8 +145,10 @@ __device__ void warp_diag_solve(const double *sL, const double *sU, double *sT, 
 // the strict lower triangle of Lt and the strict upper triangle of Ut in one
 // tile sLU, reciprocal divisors in sR, all as (hi, lo) float pairs with
 // leading dimension LDT.  The lane that finishes entry (i, j) starts its sum at
-// t_ij; x_ij = (t_ij - sum) * r_ij is a normalised double-float product.  Only
-// the FP32 pipe is used.
+// t_ij; x_ij = (t_ij - sum) * r_ij is a normalised double-float product.  One
+// accumulator per lane: the loop-carried chain of a double-float term is one
+// addition on each half, so a second one would only add the merge.  Only the
+// FP32 pipe is used.
 template <int B, int LDT, bool SYM>
 __device__ void warp_diag_solve_df(const float2 *sLU, float2 *sT, const float2 *sR, int m, int nn, int lane)
 {
@@ -162,7 +164,7 @@ __device__ void warp_diag_solve_df(const float2 *sLU, float2 *sT, const float2 *
         const int idx = lane >> lg, part = lane & (split - 1);
         const bool act = idx < cnt;
         const int i = ilo + (act ? idx : 0), j = d - i;
-        float h0 = 0.f, l0 = 0.f, h1 = 0.f, l1 = 0.f;
+        float h0 = 0.f, l0 = 0.f;
         if (act) {
             if (part == 0) {
                 const float2 tv = sT[i + j * LDT];
@@ -181,7 +183,7 @@ __device__ void warp_diag_solve_df(const float2 *sLU, float2 *sT, const float2 *
                     const float2 a0 = sT[(t < i ? aL : aU) + t * LDT], b0 = sT[(t < i ? bL : bU) + t];
                     const float2 a1 = sT[(t1 < i ? aL : aU) + t1 * LDT], b1 = sT[(t1 < i ? bL : bU) + t1];
                     df_msub(h0, l0, a0.x, a0.y, b0.x, b0.y);
-                    df_msub(h1, l1, a1.x, a1.y, b1.x, b1.y);
+                    df_msub(h0, l0, a1.x, a1.y, b1.x, b1.y);
                 }
                 if (t < d) {
                     const float2 a0 = sT[(t < i ? aL : aU) + t * LDT], b0 = sT[(t < i ? bL : bU) + t];
@@ -195,7 +197,7 @@ __device__ void warp_diag_solve_df(const float2 *sLU, float2 *sT, const float2 *
                     const float2 a1 = t1 < i ? sLU[i + t1 * LDT] : sT[i + (t1 - i) * LDT];
                     const float2 b1 = t1 < i ? (t1 < j ? sT[j + t1 * LDT] : sT[t1 + j * LDT]) : sLU[(t1 - i) + j * LDT];
                     df_msub(h0, l0, a0.x, a0.y, b0.x, b0.y);
-                    df_msub(h1, l1, a1.x, a1.y, b1.x, b1.y);
+                    df_msub(h0, l0, a1.x, a1.y, b1.x, b1.y);
                 }
                 if (t < d) {
                     const float2 a0 = t < i ? sLU[i + t * LDT] : sT[i + (t - i) * LDT];
@@ -204,7 +206,6 @@ __device__ void warp_diag_solve_df(const float2 *sLU, float2 *sT, const float2 *
                 }
             }
         }
-        df_add(h0, l0, h1, l1);
         df_group_sum(h0, l0, split);
         if (act && part == 0) {
             df_norm(h0, l0);
